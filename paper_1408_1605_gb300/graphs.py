@@ -1,0 +1,165 @@
+"""Seeded synthetic graph inputs and the symmetric CSR builder (host side).
+
+Input preparation only: shared by the CPU oracle tests and the GPU path, and holding none
+of the BFS arithmetic. The heavy lifting is in ``csrc/graphgen.cpp`` (multithreaded,
+counter-based randomness, so the result does not depend on the thread count).
+
+Workloads (stand-ins for the paper's Graph500 R-MAT inputs, Sec. 4; the Graph500 generator
+itself is not available, so byte parity with it is not claimed):
+  * ``rmat(scale, edge_factor)``: edge_factor * 2^scale generated pairs, quadrant
+    probabilities A/B/C/D = .57/.19/.19/.05, seeded vertex permutation, self-loops and
+    duplicates removed, symmetrized.
+  * ``uniform(n, m)``: G(n, m) pairs with both endpoints uniform, same cleaning.
+  * ``grid3d(X, Y, Z)``: non-periodic 6-neighbour grid, id = x + X * (y + Y * z).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+_P64 = ctypes.POINTER(ctypes.c_int64)
+_P32 = ctypes.POINTER(ctypes.c_int32)
+
+# Seeds: graph seed = GRAPH_SEED_BASE + workload index; root seed = graph seed ^ 0x5EED.
+GRAPH_SEED_BASE = 20140806
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.LIB_GEN
+        if not os.path.exists(path):
+            _build.build_graphgen()
+        lib = ctypes.CDLL(path)
+        lib.gg_rmat_edges.restype = ctypes.c_int
+        lib.gg_rmat_edges.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_int, _P32, _P32, ctypes.c_int]
+        lib.gg_uniform_edges.restype = ctypes.c_int
+        lib.gg_uniform_edges.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, _P32, _P32, ctypes.c_int]
+        lib.gg_grid3d_edge_count.restype = ctypes.c_int64
+        lib.gg_grid3d_edge_count.argtypes = [ctypes.c_int64] * 3
+        lib.gg_grid3d_edges.restype = ctypes.c_int
+        lib.gg_grid3d_edges.argtypes = [ctypes.c_int64] * 3 + [_P32, _P32, ctypes.c_int]
+        lib.gg_build_csr.restype = ctypes.c_int64
+        lib.gg_build_csr.argtypes = [ctypes.c_int64, ctypes.c_int64, _P32, _P32, _P64, _P32, ctypes.c_int]
+        lib.gg_pick_roots.restype = ctypes.c_int64
+        lib.gg_pick_roots.argtypes = [ctypes.c_int64, _P64, ctypes.c_int64, ctypes.c_uint64, _P32]
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class CSRGraph:
+    """Symmetric CSR: ``offsets`` int64[n + 1], ``cols`` int32[nnz], rows sorted."""
+
+    n: int
+    offsets: np.ndarray
+    cols: np.ndarray
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.offsets[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+    def offsets32(self) -> np.ndarray:
+        if self.nnz > np.iinfo(np.int32).max:
+            raise OverflowError("graph has more than 2^31 - 1 CSR entries; int64 offsets needed")
+        return self.offsets.astype(np.int32)
+
+
+def _p(a, typ):
+    return a.ctypes.data_as(typ)
+
+
+def rmat_edges(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+               seed: int = GRAPH_SEED_BASE, permute: bool = True, threads: int = 0):
+    m = int(edge_factor) << int(scale)
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    r = _load().gg_rmat_edges(int(scale), m, a, b, c, int(seed) & (2**64 - 1), int(bool(permute)),
+                              _p(src, _P32), _p(dst, _P32), int(threads))
+    if r != 0:
+        raise ValueError("gg_rmat_edges: bad arguments")
+    return src, dst
+
+
+def uniform_edges(n: int, m: int, seed: int, threads: int = 0):
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    if _load().gg_uniform_edges(int(n), int(m), int(seed) & (2**64 - 1), _p(src, _P32), _p(dst, _P32),
+                                int(threads)) != 0:
+        raise ValueError("gg_uniform_edges: bad arguments")
+    return src, dst
+
+
+def grid3d_edges(X: int, Y: int, Z: int, threads: int = 0):
+    m = int(_load().gg_grid3d_edge_count(X, Y, Z))
+    if m < 0:
+        raise ValueError("grid dimensions must be >= 1")
+    src = np.empty(max(m, 1), dtype=np.int32)
+    dst = np.empty(max(m, 1), dtype=np.int32)
+    if _load().gg_grid3d_edges(X, Y, Z, _p(src, _P32), _p(dst, _P32), int(threads)) != 0:
+        raise ValueError("gg_grid3d_edges: bad arguments")
+    return src[:m], dst[:m]
+
+
+def from_edges(n: int, src, dst, threads: int = 0, name: str = "") -> CSRGraph:
+    """Symmetric, loop-free, duplicate-free CSR with sorted rows from an edge list."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    if src.shape != dst.shape:
+        raise ValueError("src/dst length mismatch")
+    m = src.size
+    offsets = np.empty(n + 1, dtype=np.int64)
+    cols = np.empty(max(2 * m, 1), dtype=np.int32)
+    sp = src if m else np.zeros(1, dtype=np.int32)
+    dp = dst if m else np.zeros(1, dtype=np.int32)
+    nnz = _load().gg_build_csr(int(n), m, _p(sp, _P32), _p(dp, _P32), _p(offsets, _P64), _p(cols, _P32),
+                               int(threads))
+    if nnz == -3:
+        raise ValueError("edge endpoint out of range")
+    if nnz < 0:
+        raise MemoryError("gg_build_csr failed") if nnz == -2 else ValueError("gg_build_csr: bad arguments")
+    if nnz < cols.size // 2:
+        cols = cols[:nnz].copy()
+    else:
+        cols = cols[:nnz]
+    return CSRGraph(int(n), offsets, cols, name)
+
+
+def rmat(scale: int, edge_factor: int = 16, seed: int = GRAPH_SEED_BASE, threads: int = 0, **kw) -> CSRGraph:
+    src, dst = rmat_edges(scale, edge_factor, seed=seed, threads=threads, **kw)
+    g = from_edges(1 << scale, src, dst, threads=threads, name=f"rmat-s{scale}-ef{edge_factor}")
+    return g
+
+
+def uniform(n: int, m: int, seed: int, threads: int = 0) -> CSRGraph:
+    src, dst = uniform_edges(n, m, seed, threads)
+    return from_edges(n, src, dst, threads=threads, name=f"uniform-n{n}-m{m}")
+
+
+def grid3d(X: int, Y: int, Z: int, threads: int = 0) -> CSRGraph:
+    src, dst = grid3d_edges(X, Y, Z, threads)
+    return from_edges(X * Y * Z, src, dst, threads=threads, name=f"grid3d-{X}x{Y}x{Z}")
+
+
+def pick_roots(g: CSRGraph, k: int, seed: int) -> np.ndarray:
+    """k distinct roots with degree > 0, drawn from a seeded counter-based stream."""
+    out = np.empty(max(k, 1), dtype=np.int32)
+    got = _load().gg_pick_roots(g.n, _p(g.offsets, _P64), int(k), int(seed) & (2**64 - 1), _p(out, _P32))
+    if got < 0:
+        raise ValueError("gg_pick_roots: bad arguments")
+    return out[:got].copy()
+
+
+def root_seed(graph_seed: int) -> int:
+    return graph_seed ^ 0x5EED
