@@ -1,0 +1,132 @@
+/*
+ * gbfs: single-GPU level-synchronous BFS for GB300 (sm_103a), C ABI.
+ *
+ * Method: Bisson, Bernaschi, Mastrostefano, "Parallel Distributed Breadth First Search
+ * on the Kepler Architecture" (arXiv 1408.1605), in its one-processor form (processor
+ * grid R = C = 1, Sec. 3.2 Algorithm 2 with the exchanges reduced to identities): per
+ * level, an exclusive scan of the frontier's degrees (Sec. 3.4), a binary search that
+ * maps each thread to child edges (Sec. 3.4, Fig. 2; Sec. 3.4.1), a visited-bitmap claim
+ * with atomicOr (Sec. 3.4, Algorithm 3), level / predecessor writes, and appends to the
+ * next frontier.
+ *
+ * Conventions shared by every entry point:
+ *  - Graphs are undirected and given as a symmetric CSR (the paper's CSC `col` offsets /
+ *    `row` indices pair, Sec. 3.1; for a symmetric matrix CSR and CSC coincide):
+ *    row_offsets[n_vertices + 1] (int32 or int64, see flags) and cols int32[n_entries]
+ *    holding neighbour ids in [0, n_vertices). Rows need not be sorted. Self-loops and
+ *    repeated entries are harmless. A non-symmetric CSR is searched along its stored
+ *    (out-)edges.
+ *  - Outputs (Sec. 3.1; Algorithm 2 lines 1-10): level[v] = hop distance from the root,
+ *    pred[v] = a neighbour of v one level closer to the root, level[root] = 0 and
+ *    pred[root] = root; vertices not reached get level = pred = -1. When several parents
+ *    are valid, which one is written depends on which atomic wins (Sec. 3.4).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is enqueued on
+ *    it; see each call for when it returns.
+ *  - Every call returns a bfs_status; on failure bfs_last_error() describes the cause
+ *    (thread-local). Outputs are unspecified after a failure.
+ *  - The library owns the device copy of a graph and its work buffers; the caller owns
+ *    every array it passes in and keeps ownership after the call.
+ *  - Calls that use the same graph handle are serialized by a lock in the handle.
+ */
+#ifndef GBFS_H
+#define GBFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GBFS_API __attribute__((visibility("default")))
+#else
+#define GBFS_API
+#endif
+
+typedef enum bfs_status {
+  BFS_OK = 0,
+  BFS_ERR_INVALID_ARG = 1,   /* NULL pointer, root out of range, bad flags or sizes */
+  BFS_ERR_INVALID_GRAPH = 2, /* malformed CSR (see bfs_graph_create) */
+  BFS_ERR_OOM = 3,           /* a device or host allocation failed */
+  BFS_ERR_CUDA = 4,          /* a CUDA runtime call failed; message in bfs_last_error() */
+  BFS_ERR_TIMEOUT = 5,       /* a bounded wait expired */
+  BFS_ERR_BUSY = 6,          /* a queue is full; retry later */
+  BFS_ERR_CANCELLED = 7,     /* the request was cancelled */
+  BFS_ERR_NOT_FOUND = 8      /* unknown ticket / graph id */
+} bfs_status;
+
+typedef struct bfs_graph_s *bfs_graph_t;
+
+/* bfs_graph_create flags */
+#define BFS_HOST_PTRS 0x1u     /* row_offsets / cols are host pointers (default) */
+#define BFS_DEVICE_PTRS 0x2u   /* row_offsets / cols are device pointers */
+#define BFS_OFFSETS_INT32 0x4u /* row_offsets is int32[n_vertices + 1] (default) */
+#define BFS_OFFSETS_INT64 0x8u /* row_offsets is int64[n_vertices + 1] */
+#define BFS_VALIDATE 0x10u     /* also check every column id and the symmetry (O(n_entries)) */
+
+/* Per-search statistics. edges_traversed is m_c, the TEPS numerator of Sec. 4: the
+ * number of undirected input edges inside the traversed component, i.e. half the degree
+ * sum over reached vertices. */
+typedef struct bfs_stats {
+  int32_t depth;            /* number of non-empty levels, i.e. max level + 1 */
+  int32_t reserved;
+  int64_t vertices_reached; /* including the root */
+  int64_t edges_traversed;  /* m_c */
+  double device_ms;         /* device time of the whole search, CUDA events on `stream` */
+} bfs_stats;
+
+/* Copies a CSR graph into library-owned device memory on the current CUDA device.
+ *   row_offsets: int32 or int64 [n_vertices + 1] per BFS_OFFSETS_*; host or device per
+ *                BFS_*_PTRS. cols: int32 [n_entries]. n_vertices in [1, 2^31 - 1].
+ *   Checked always: row_offsets[0] == 0, non-decreasing, row_offsets[n] == n_entries.
+ *   Checked with BFS_VALIDATE: every column id in range and the CSR symmetric.
+ *   Failures: BFS_ERR_INVALID_ARG (NULL / sizes / flags), BFS_ERR_INVALID_GRAPH (checks
+ *   above), BFS_ERR_OOM, BFS_ERR_CUDA. The call is synchronous on `stream`. */
+GBFS_API bfs_status bfs_graph_create(const void *row_offsets, const int32_t *cols, int64_t n_vertices,
+                                     int64_t n_entries, uint32_t flags, void *stream, bfs_graph_t *out);
+
+/* Releases the graph's device memory and work buffers. Waits for the graph's pending
+ * work. NULL is accepted (no-op). */
+GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
+
+/* Vertex and CSR-entry counts of a graph. */
+GBFS_API bfs_status bfs_graph_info(bfs_graph_t g, int64_t *n_vertices, int64_t *n_entries);
+
+/* One single-source BFS from `root` (Algorithm 2 with R = C = 1; kernel per level as in
+ * Algorithm 3). levels / parents: int32[n_vertices] each, device memory or host memory
+ * (pinned or pageable; detected with cudaPointerGetAttributes, results are then copied
+ * back before return). The level loop runs on the device; the call returns once the
+ * search has finished when stats != NULL or the outputs are host memory, else as soon as
+ * the work is enqueued. Failures: BFS_ERR_INVALID_ARG (root outside [0, n), NULL
+ * outputs), BFS_ERR_INVALID_GRAPH (a column id out of range was met during the search),
+ * BFS_ERR_OOM, BFS_ERR_CUDA. */
+GBFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *levels, int32_t *parents, void *stream,
+                            bfs_stats *stats);
+
+/* One top-down level on caller-held state: the frontier expansion routine of Algorithm 2
+ * line 14 (Algorithm 3) with R = C = 1, including the degree gather and exclusive scan
+ * (Sec. 3.4). All pointers are device memory:
+ *   frontier int32[n_frontier]: the current frontier (any order, repeats and
+ *     zero-degree vertices allowed);
+ *   bitmap uint32[ceil(n/32)]: visited bits, bit v % 32 of word v / 32 (Sec. 3.1);
+ *   levels, parents int32[n]: written for each newly claimed vertex v as
+ *     levels[v] = level, parents[v] = the frontier vertex whose edge claimed v;
+ *   next int32[n]: receives the newly claimed vertices, each once, in unspecified order;
+ *   next_count int64 (device): receives their number.
+ * `level` must be >= 1. The call returns once the work is enqueued. Failures:
+ * BFS_ERR_INVALID_ARG, BFS_ERR_OOM, BFS_ERR_CUDA. */
+GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n_frontier, int32_t level,
+                               uint32_t *bitmap, int32_t *levels, int32_t *parents, int32_t *next,
+                               int64_t *next_count, void *stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+GBFS_API const char *bfs_last_error(void);
+
+/* Library version string. */
+GBFS_API const char *bfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFS_H */

@@ -1,0 +1,155 @@
+"""Thin ctypes binding of the gbfs C ABI (``include/gbfs.h``): same names, argument
+marshalling only. Every step of a search runs in the CUDA library; nothing here computes.
+
+Arrays may be torch tensors (device or host) or numpy arrays (host); they are passed as raw
+pointers. Streams default to torch's current CUDA stream when torch is importable.
+If the shared library has not been built, every call raises ``RuntimeError``: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import _build
+
+BFS_OK = 0
+STATUS_NAMES = {
+    0: "BFS_OK", 1: "BFS_ERR_INVALID_ARG", 2: "BFS_ERR_INVALID_GRAPH", 3: "BFS_ERR_OOM", 4: "BFS_ERR_CUDA",
+    5: "BFS_ERR_TIMEOUT", 6: "BFS_ERR_BUSY", 7: "BFS_ERR_CANCELLED", 8: "BFS_ERR_NOT_FOUND",
+}
+BFS_HOST_PTRS = 0x1
+BFS_DEVICE_PTRS = 0x2
+BFS_OFFSETS_INT32 = 0x4
+BFS_OFFSETS_INT64 = 0x8
+BFS_VALIDATE = 0x10
+
+_P = ctypes.c_void_p
+_lib = None
+
+
+class BfsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class bfs_stats(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("reserved", ctypes.c_int32), ("vertices_reached", ctypes.c_int64),
+                ("edges_traversed", ctypes.c_int64), ("device_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+def library_path() -> str:
+    return _build.LIB_BFS
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions ``include/gbfs.h`` declares."""
+    with open(os.path.join(_build.INCLUDE, "gbfs.h")) as f:
+        text = f.read()
+    return re.findall(r"GBFS_API\s+[\w\s\*]+?\b(bfs_\w+)\s*\(", text)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"gbfs CUDA library not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        i64, i32, u32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        sig = {
+            "bfs_graph_create": [_P, _P, i64, i64, u32, _P, ctypes.POINTER(_P)],
+            "bfs_graph_destroy": [_P],
+            "bfs_graph_info": [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+            "bfs_run": [_P, i32, _P, _P, _P, ctypes.POINTER(bfs_stats)],
+            "bfs_expand": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.bfs_last_error.restype = ctypes.c_char_p
+        L.bfs_version.restype = ctypes.c_char_p
+        _lib = L
+        _extend(L)
+    return _lib
+
+
+_extensions = []
+
+
+def _extend(L):
+    for f in _extensions:
+        f(L)
+
+
+def check(status: int) -> None:
+    if status != BFS_OK:
+        raise BfsError(status, lib().bfs_last_error().decode())
+
+
+def ptr(a) -> int:
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        return a.ctypes.data
+    return int(a)
+
+
+def stream_handle(stream=None) -> int:
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+def bfs_graph_create(row_offsets, cols, n_vertices: int, n_entries: int, flags: int = 0, stream=None) -> int:
+    out = _P()
+    check(lib().bfs_graph_create(ptr(row_offsets), ptr(cols), int(n_vertices), int(n_entries), int(flags),
+                                 stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def bfs_graph_destroy(graph: int) -> None:
+    check(lib().bfs_graph_destroy(graph))
+
+
+def bfs_graph_info(graph: int) -> tuple[int, int]:
+    n, m = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().bfs_graph_info(graph, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def bfs_run(graph: int, root: int, levels, parents, stream=None, want_stats: bool = False):
+    st = bfs_stats()
+    check(lib().bfs_run(graph, int(root), ptr(levels), ptr(parents), stream_handle(stream),
+                        ctypes.byref(st) if want_stats else None))
+    return st if want_stats else None
+
+
+def bfs_expand(graph: int, frontier, n_frontier: int, level: int, bitmap, levels, parents, next_, next_count,
+               stream=None) -> None:
+    check(lib().bfs_expand(graph, ptr(frontier), int(n_frontier), int(level), ptr(bitmap), ptr(levels), ptr(parents),
+                           ptr(next_), ptr(next_count), stream_handle(stream)))
+
+
+def bfs_last_error() -> str:
+    return lib().bfs_last_error().decode()
+
+
+def bfs_version() -> str:
+    return lib().bfs_version().decode()

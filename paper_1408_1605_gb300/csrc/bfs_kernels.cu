@@ -1,0 +1,498 @@
+// Single-source BFS kernels for sm_103a: output init, the standalone degree scan, and
+// the fused frontier-expansion kernel (Sec. 3.4, Algorithm 3, with the optimizations of
+// Sec. 3.4.1).
+//
+// Level structure (Algorithm 2 with R = C = 1). The frontier of a level is held as
+// (v[k], cum[k], base[k]) plus a chunk index: chunk[c] = max{k : cum[k] <= c * kChunk},
+// the binary-search answer (Algorithm 3 line 2) for every kChunk-th edge, written when
+// the frontier is built. One expansion launch per level processes the level's edge space
+// [0, r) in tiles of T = BLOCK * E edges:
+//   1. tile bounds from chunk[] (the per-tile binary search, precomputed);
+//   2. stage the tile's frontier entries (cum relative to the tile, base, vertex) in
+//      shared memory;
+//   3. each warp takes 32 * E consecutive edges, lane l edges l, l + 32, ... (coalesced
+//      column reads); one shared-memory binary search for the first, then the linear walk
+//      of Sec. 3.4.1 (advance k while e >= cum[k + 1]) for the rest;
+//   4. all E column loads are issued before any is used (the interleaving of Sec. 3.4.1);
+//   5. bitmap pre-check, then atomicOr claim (Algorithm 3 lines 5-8); the winner writes
+//      level and parent (lines 15, 17) and reads the claimed vertex's degree;
+//   6. claimed vertices are appended to a shared-memory buffer with one shared atomic per
+//      warp (ballot / popc); the buffer is flushed with ONE global 64-bit atomicAdd that
+//      reserves both the queue slots and the edge range (the exclusive scan of the next
+//      frontier's degrees, Sec. 3.4, fused into the append of lines 9-14).
+// The last CTA to finish closes the level (no spin-waits anywhere).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gbfs {
+
+// ---------------------------------------------------------------------------------------
+// Frontier construction helpers
+
+// Writes chunk[c] = k for every chunk start c * kChunk inside [cum, cum + deg).
+template <typename OffT>
+__device__ __forceinline__ void write_chunks(int32_t* chunk, OffT cum, OffT deg, int32_t k) {
+  if (deg <= 0) return;
+  OffT c = (cum + kChunk - 1) / kChunk;
+  const OffT end = cum + deg;
+  for (; c * kChunk < end; ++c) chunk[c] = k;
+}
+
+template <typename OffT>
+__global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t root, int32_t* levels,
+                              int32_t* parents, uint32_t* bitmap, FrontierBuf<OffT> f0, int32_t* chunk0,
+                              Ctl* ctl, Packed pk) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n; i += stride) {
+    const bool is_root = i == root;
+    levels[i] = is_root ? 0 : -1;
+    parents[i] = is_root ? root : -1;
+  }
+  const int64_t nw = (n + 31) / 32;
+  for (int64_t w = tid; w < nw; w += stride) bitmap[w] = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
+  const OffT o0 = off[root], deg = off[root + 1] - o0;
+  // chunk starts of the root's row, spread over the grid (a hub root spans many chunks)
+  const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
+  for (int64_t c = tid; c < nchunks; c += stride) chunk0[c] = 0;
+  if (tid == 0) {
+    f0.v[0] = root;
+    f0.cum[0] = 0;
+    f0.base[0] = o0;
+    ctl->counter[0] = pk.make(1, (long long)deg);
+    ctl->counter[1] = 0;
+    ctl->done[0] = ctl->done[1] = 0;
+    ctl->level = 1;
+    ctl->depth = 1;
+    ctl->reached = 1;
+    ctl->edges2 = 0;
+    ctl->error = 0;
+    ctl->cont = deg > 0;
+    ctl->levels = levels;
+    ctl->parents = parents;
+  }
+}
+
+// Degree gather + exclusive scan of a caller-given frontier list (Sec. 3.4: the degrees
+// of the frontier vertices are scanned into the cumulative degree array). Reduce-then-scan
+// over a fixed grid: per-CTA partial sums, a one-CTA scan of the partials, then a
+// per-CTA rescan that writes (v, cum, base) and the chunk index.
+template <typename OffT>
+__device__ __forceinline__ OffT frontier_degree(const OffT* off, int64_t n, int32_t v, Ctl* ctl) {
+  if ((uint32_t)v >= (uint64_t)n) {
+    atomicOr(&ctl->error, kErrFrontierRange);
+    return 0;
+  }
+  return off[v + 1] - off[v];
+}
+
+template <typename OffT>
+__device__ OffT block_exclusive_scan(OffT x, OffT* s_warp, OffT* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  OffT inc = warp_inclusive_scan(x);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    OffT t = lane < nw ? s_warp[lane] : 0;
+    OffT ti = warp_inclusive_scan(t);
+    if (lane < nw) s_warp[lane] = ti - t;
+    if (lane == nw - 1) s_warp[32] = ti;
+  }
+  __syncthreads();
+  OffT ex = s_warp[w] + inc - x;
+  *total = s_warp[32];
+  __syncthreads();
+  return ex;
+}
+
+template <typename OffT>
+__global__ void k_scan_partials(const OffT* __restrict__ off, int64_t n, const int32_t* __restrict__ front,
+                                int64_t nf, OffT* partial, Ctl* ctl) {
+  __shared__ OffT s_warp[33];
+  const int64_t per = (nf + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = min(nf, per * blockIdx.x), hi = min(nf, lo + per);
+  OffT sum = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) sum += frontier_degree(off, n, front[i], ctl);
+  OffT total;
+  block_exclusive_scan(sum, s_warp, &total);
+  if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+template <typename OffT>
+__global__ void k_scan_top(OffT* partial, int nparts, int64_t nf, Ctl* ctl, Packed pk, int32_t level,
+                           int32_t* levels, int32_t* parents, long long max_edges) {
+  __shared__ OffT s_warp[33];
+  __shared__ OffT s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nparts; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const OffT x = i < nparts ? partial[i] : 0;
+    OffT total;
+    const OffT ex = block_exclusive_scan(x, s_warp, &total);
+    if (i < nparts) partial[i] = s_carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // A caller frontier with repeated hubs can exceed the chunk index / counter capacity:
+    // report it and expand nothing.
+    const bool over = (long long)s_carry > max_edges;
+    if (over) atomicOr(&ctl->error, kErrCounterOverflow);
+    const int cur = (level - 1) & 1;
+    ctl->counter[cur] = over ? 0ull : pk.make(nf, (long long)s_carry);
+    ctl->counter[cur ^ 1] = 0;
+    ctl->done[0] = ctl->done[1] = 0;
+    ctl->level = level;
+    ctl->depth = 0;
+    ctl->reached = 0;
+    ctl->edges2 = 0;
+    ctl->cont = 1;
+    ctl->levels = levels;
+    ctl->parents = parents;
+  }
+}
+
+template <typename OffT>
+__global__ void k_scan_final(const OffT* __restrict__ off, int64_t n, const int32_t* __restrict__ front,
+                             int64_t nf, const OffT* partial, FrontierBuf<OffT> f, int32_t* chunk,
+                             const Ctl* ctl) {
+  __shared__ OffT s_warp[33];
+  if (ctl->error & kErrCounterOverflow) return;  // reported by k_scan_top; nothing to expand
+  const int64_t per = (nf + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = min(nf, per * blockIdx.x), hi = min(nf, lo + per);
+  OffT carry = partial[blockIdx.x];
+  for (int64_t b = lo; b < hi; b += blockDim.x) {
+    const int64_t i = b + threadIdx.x;
+    int32_t v = 0;
+    OffT d = 0, o = 0;
+    if (i < hi) {
+      v = front[i];
+      if ((uint32_t)v < (uint64_t)n) {
+        o = off[v];
+        d = off[v + 1] - o;
+      }
+    }
+    OffT total;
+    const OffT ex = block_exclusive_scan(d, s_warp, &total);
+    if (i < hi) {
+      const OffT c = carry + ex;
+      f.v[i] = v;
+      f.cum[i] = c;
+      f.base[i] = o - c;
+      write_chunks(chunk, c, d, (int32_t)i);
+    }
+    carry += total;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Frontier expansion
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+struct ExpandSmem {
+  static constexpr int T = BLOCK * E;
+  static constexpr int CAP = T + 1;  // staged frontier entries per tile (fast path)
+  // layout: base[CAP] (OffT) | rel[CAP + 1] (int32) | u[CAP] (int32) | claim[CLAIM] (int2)
+  static constexpr size_t off_base = 0;
+  static constexpr size_t off_rel = off_base + sizeof(OffT) * CAP;
+  static constexpr size_t off_u = off_rel + sizeof(int32_t) * (CAP + 1);
+  static constexpr size_t off_claim = ((off_u + sizeof(int32_t) * CAP) + 15) & ~size_t(15);
+  static constexpr size_t bytes = off_claim + sizeof(int2) * CLAIM;
+};
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+__device__ __forceinline__ void flush_claims(const ExpandArgs<OffT>& a, const FrontierBuf<OffT>& out,
+                                             int32_t* chunk_out, int nxt, int2* s_claim, int nc, OffT* s_warp,
+                                             unsigned long long* s_resv) {
+  // Thread t owns the consecutive buffer items [t * P, t * P + P).
+  constexpr int P = (CLAIM + BLOCK - 1) / BLOCK;
+  const int lo = min(nc, (int)threadIdx.x * P), hi = min(nc, lo + P);
+  OffT mine = 0;
+  for (int i = lo; i < hi; ++i) mine += (OffT)s_claim[i].y;
+  OffT total;
+  OffT run = block_exclusive_scan(mine, s_warp, &total);
+  if (threadIdx.x == 0) *s_resv = atomicAdd(&a.ctl->counter[nxt], a.pk.make(nc, (long long)total));
+  __syncthreads();
+  const unsigned long long resv = *s_resv;
+  const long long slot0 = a.pk.count(resv);
+  run += (OffT)a.pk.edges(resv);
+  for (int i = lo; i < hi; ++i) {
+    const int32_t v = s_claim[i].x;
+    const OffT d = (OffT)s_claim[i].y;
+    const int32_t slot = (int32_t)(slot0 + i);
+    out.v[slot] = v;
+    out.cum[slot] = run;
+    out.base[slot] = a.off[v] - run;
+    write_chunks(chunk_out, run, d, slot);
+    run += d;
+  }
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+__global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
+  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  constexpr int T = S::T;
+  constexpr int CAP = S::CAP;
+  static_assert(CLAIM >= T, "claim buffer must hold one full tile");
+  extern __shared__ __align__(16) unsigned char smem[];
+  OffT* s_base = reinterpret_cast<OffT*>(smem + S::off_base);
+  int32_t* s_rel = reinterpret_cast<int32_t*>(smem + S::off_rel);
+  int32_t* s_u = reinterpret_cast<int32_t*>(smem + S::off_u);
+  int2* s_claim = reinterpret_cast<int2*>(smem + S::off_claim);
+  __shared__ OffT s_warp[33];
+  __shared__ unsigned long long s_resv;
+  __shared__ int s_nclaim;
+  __shared__ int s_klo, s_kend;
+
+  Ctl* ctl = a.ctl;
+  const int L = *(volatile int*)&ctl->level;
+  const int cur = (L - 1) & 1, nxt = cur ^ 1;
+  const unsigned long long pc = *(volatile unsigned long long*)&ctl->counter[cur];
+  const int64_t nf = a.pk.count(pc);
+  const OffT r = (OffT)a.pk.edges(pc);
+  int32_t* const levels = *(int32_t* volatile*)&ctl->levels;
+  int32_t* const parents = *(int32_t* volatile*)&ctl->parents;
+  const FrontierBuf<OffT> in = a.fr[cur], out = a.fr[nxt];
+  const int32_t* chunk_in = a.chunk[cur];
+  int32_t* chunk_out = a.chunk[nxt];
+  const int64_t ntiles = ((int64_t)r + T - 1) / T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) s_nclaim = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const OffT e0 = (OffT)(tile * T);
+    const int cnt = (int)min((OffT)T, r - e0);
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    if (threadIdx.x == 0) {
+      s_klo = chunk_in[e0 / kChunk];
+      s_kend = (e0 + cnt < r) ? chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+    }
+    __syncthreads();
+    const int klo = s_klo;
+    const int s = s_kend - klo + 1;
+    const bool fast = s <= CAP;
+    if (fast) {
+      for (int i = threadIdx.x; i < s; i += BLOCK) {
+        const OffT c = in.cum[klo + i];
+        s_rel[i] = (int32_t)max(c - e0, (OffT)0);
+        s_base[i] = in.base[klo + i];
+        s_u[i] = in.v[klo + i];
+      }
+      if (threadIdx.x == 0) s_rel[s] = 0x7fffffff;  // sentinel
+      __syncthreads();
+    }
+
+    // Thread -> edge mapping. Warp w owns tile edges [w * 32E, (w + 1) * 32E).
+    int32_t vv[E], uu[E];
+    OffT col[E];
+    bool ok[E];
+    {
+      const int er0 = warp * 32 * E + lane;
+      int k = 0;
+      if (fast && er0 < cnt) k = binsearch_maxle(s_rel, 0, s, er0);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int er = er0 + 32 * j;
+        ok[j] = er < cnt;
+        uu[j] = 0;
+        col[j] = 0;
+        if (ok[j]) {
+          if (fast) {
+            // linear walk (Sec. 3.4.1), with a bounded number of steps before a search
+            int steps = 0;
+            while (s_rel[k + 1] <= er && steps < 4) { ++k; ++steps; }
+            if (s_rel[k + 1] <= er) k = binsearch_maxle(s_rel, k, s, er);
+            col[j] = s_base[k] + e0 + er;
+            uu[j] = s_u[k];
+          } else {
+            // many zero-degree frontier entries: search the global scan directly
+            const OffT e = e0 + er;
+            const int32_t kk = binsearch_maxle(in.cum, (int64_t)klo, (int64_t)s_kend + 1, e);
+            col[j] = in.base[kk] + e;
+            uu[j] = in.v[kk];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) vv[j] = ok[j] ? ld_nc(a.cols + col[j]) : 0;
+    uint32_t bits[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (ok[j] && (uint32_t)vv[j] >= (uint64_t)a.n) {
+        atomicOr(&ctl->error, kErrColumnRange);
+        ok[j] = false;
+      }
+      bits[j] = ok[j] ? a.bitmap[vv[j] >> 5] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int32_t v = vv[j];
+      const uint32_t m = 1u << (v & 31);
+      bool claimed = false;
+      if (!(bits[j] & m)) claimed = !(atomicOr(a.bitmap + (v >> 5), m) & m);
+      int32_t deg = 0;
+      if (claimed) {
+        levels[v] = L;
+        parents[v] = uu[j];
+        deg = (int32_t)(a.off[v + 1] - a.off[v]);
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, claimed);
+      if (ball) {
+        const int leader = __ffs(ball) - 1;
+        int pos = 0;
+        if (lane == leader) pos = atomicAdd(&s_nclaim, __popc(ball));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (claimed) s_claim[pos + __popc(ball & lanemask_lt())] = make_int2(v, deg);
+      }
+    }
+    __syncthreads();
+    const int nc = s_nclaim;
+    if (nc > CLAIM - T) {
+      flush_claims<OffT, BLOCK, E, CLAIM>(a, out, chunk_out, nxt, s_claim, nc, s_warp, &s_resv);
+      __syncthreads();
+      if (threadIdx.x == 0) s_nclaim = 0;
+    }
+  }
+  __syncthreads();
+  const int nc = s_nclaim;
+  if (nc > 0) flush_claims<OffT, BLOCK, E, CLAIM>(a, out, chunk_out, nxt, s_claim, nc, s_warp, &s_resv);
+
+  // Level epilogue by the last CTA to finish: close the level and prepare the next.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->done[cur], 1u);
+    if (t == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long pn = atomicAdd(&ctl->counter[nxt], 0ull);
+      const long long nn = a.pk.count(pn);
+      ctl->edges2 += (long long)r;
+      if (nn > 0) {
+        ctl->depth += 1;
+        ctl->reached += nn;
+      }
+      ctl->counter[cur] = 0;
+      ctl->done[cur] = 0;
+      ctl->level = L + 1;
+      ctl->cont = nn > 0;
+      if (a.use_cond) cudaGraphSetConditional(a.cond, nn > 0 ? 1u : 0u);
+    }
+  }
+}
+
+__global__ void k_write_count(const Ctl* ctl, Packed pk, int64_t* out) {
+  // after an expansion the next frontier's counter sits at parity 1 (level-1 parity 0)
+  const int nxt = ((ctl->level - 2) & 1) ^ 1;
+  *out = pk.count(ctl->counter[nxt]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers
+
+void launch_write_count(Ctl* ctl, Packed pk, int64_t* out, cudaStream_t st) {
+  k_write_count<<<1, 1, 0, st>>>(ctl, pk, out);
+}
+
+template <typename OffT>
+void launch_init_single(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
+                        cudaStream_t st) {
+  const int block = 256;
+  const int grid = g.num_sms * 8;
+  k_init_single<OffT><<<grid, block, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, levels, parents,
+                                               ws.bitmap, ws.fr<OffT>(0), ws.chunk[0], ws.ctl, g.pk);
+}
+
+template <typename OffT>
+void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, int32_t level, int32_t* levels,
+                          int32_t* parents, SingleWs& ws, cudaStream_t st) {
+  const OffT* off = reinterpret_cast<const OffT*>(g.off);
+  const int cur = (level - 1) & 1;  // the expansion of `level` reads buffer parity cur
+  cudaMemsetAsync(&ws.ctl->error, 0, sizeof(unsigned), st);
+  const int parts = ws.scan_parts;
+  OffT* partial = reinterpret_cast<OffT*>(ws.scan_partial);
+  k_scan_partials<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.ctl);
+  const long long max_edges = std::min<long long>((long long)g.pk.mask, (ws.chunk_cap - 1) * (long long)kChunk);
+  k_scan_top<OffT><<<1, 1024, 0, st>>>(partial, parts, nf, ws.ctl, g.pk, level, levels, parents, max_edges);
+  k_scan_final<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.fr<OffT>(cur), ws.chunk[cur], ws.ctl);
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+static cudaError_t launch_expand_t(const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
+  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  auto kern = k_expand<OffT, BLOCK, E, CLAIM>;
+  static bool attr_set = false;  // per template instance; set once per process
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  kern<<<grid, BLOCK, S::bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+static int occupancy_t(int num_sms) {
+  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  auto kern = k_expand<OffT, BLOCK, E, CLAIM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
+  return std::max(1, per_sm) * num_sms;
+}
+
+// Table of compiled shapes (BLOCK, E, CLAIM); the autotuner chooses among them.
+#define GBFS_EXPAND_SHAPES(X) \
+  X(0, 256, 4, 2048)          \
+  X(1, 256, 8, 4096)          \
+  X(2, 512, 4, 4096)          \
+  X(3, 128, 8, 2048)          \
+  X(4, 256, 2, 2048)          \
+  X(5, 256, 16, 8192)
+
+const ExpandShape kExpandShapes[] = {
+#define X(id, b, e, c) {id, b, e, c},
+    GBFS_EXPAND_SHAPES(X)
+#undef X
+};
+const int kNumExpandShapes = sizeof(kExpandShapes) / sizeof(kExpandShapes[0]);
+
+template <typename OffT>
+cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
+  switch (shape) {
+#define X(id, b, e, c) \
+  case id: return launch_expand_t<OffT, b, e, c>(a, grid, st);
+    GBFS_EXPAND_SHAPES(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename OffT>
+int expand_grid(int shape, int num_sms) {
+  switch (shape) {
+#define X(id, b, e, c) \
+  case id: return occupancy_t<OffT, b, e, c>(num_sms);
+    GBFS_EXPAND_SHAPES(X)
+#undef X
+  }
+  return num_sms;
+}
+
+template void launch_init_single<int32_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
+template void launch_init_single<int64_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
+template void launch_scan_frontier<int32_t>(const GraphDev&, const int32_t*, int64_t, int32_t, int32_t*,
+                                            int32_t*, SingleWs&, cudaStream_t);
+template void launch_scan_frontier<int64_t>(const GraphDev&, const int32_t*, int64_t, int32_t, int32_t*,
+                                            int32_t*, SingleWs&, cudaStream_t);
+template cudaError_t launch_expand<int32_t>(int, const ExpandArgs<int32_t>&, int, cudaStream_t);
+template cudaError_t launch_expand<int64_t>(int, const ExpandArgs<int64_t>&, int, cudaStream_t);
+template int expand_grid<int32_t>(int, int);
+template int expand_grid<int64_t>(int, int);
+
+}  // namespace gbfs

@@ -1,0 +1,85 @@
+// Shared device-side definitions for the gbfs library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace gbfs {
+
+// Device error bits, OR-ed into Ctl::error by kernels and read by the host after a search.
+enum : unsigned { kErrColumnRange = 1u, kErrFrontierRange = 2u, kErrCounterOverflow = 4u };
+
+// The next frontier's size and edge total are reserved together by one 64-bit atomicAdd
+// on a packed word (count << shift) | edges, so the slot order and the exclusive degree
+// scan agree (the scan of Sec. 3.4, fused into the append of Algorithm 3 lines 9-14).
+struct Packed {
+  int shift;                 // bits for the edge total
+  unsigned long long mask;   // (1 << shift) - 1
+  __host__ __device__ long long count(unsigned long long p) const { return (long long)(p >> shift); }
+  __host__ __device__ long long edges(unsigned long long p) const { return (long long)(p & mask); }
+  __host__ __device__ unsigned long long make(long long c, long long e) const {
+    return ((unsigned long long)c << shift) | (unsigned long long)e;
+  }
+};
+
+// Frontier in the form the expansion consumes: vertex ids, the exclusive scan of their
+// degrees (cum[k] = sum of deg(v[j]) for j < k) and base[k] = off[v[k]] - cum[k], so edge
+// e of the level's edge space (cum[k] <= e < cum[k + 1]) is column entry base[k] + e.
+template <typename OffT>
+struct FrontierBuf {
+  int32_t* v;
+  OffT* cum;
+  OffT* base;
+};
+
+// Per-search control block in device memory. Two counters alternate by level parity:
+// counter[cur] describes the frontier being expanded, counter[nxt] collects the next one.
+struct Ctl {
+  unsigned long long counter[2];
+  unsigned int done[2];      // CTAs finished per parity (last-CTA detection, no spinning)
+  int level;                 // level assigned to vertices claimed by the running expansion
+  int depth;                 // non-empty frontiers so far (root included)
+  long long reached;         // vertices reached so far (root included)
+  long long edges2;          // sum of frontier degree sums = 2 m_c at the end
+  unsigned int error;        // kErr* bits
+  int cont;                  // 1 while the next frontier is non-empty
+  int32_t* levels;           // output arrays of the running search
+  int32_t* parents;
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Read-only, non-coherent load of a column id (the const __restrict__ read-only path the
+// paper uses for the CSC arrays, Sec. 3.4.1).
+__device__ __forceinline__ int32_t ld_nc(const int32_t* p) { return __ldg(p); }
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if ((int)lane_id() >= d) x += y;
+  }
+  return x;
+}
+
+// Largest k in [lo, hi) with a[k] <= x, given a[lo] <= x (binsearch_maxle of Algorithm 3
+// line 2). a is non-decreasing.
+template <typename T, typename I>
+__device__ __forceinline__ I binsearch_maxle(const T* a, I lo, I hi, T x) {
+  while (hi - lo > 1) {
+    I mid = lo + (hi - lo) / 2;
+    if (a[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace gbfs

@@ -1,0 +1,81 @@
+// Internal declarations shared by the gbfs translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gbfs {
+
+// Granularity of the precomputed per-tile binary-search answers (chunk index). Every
+// expansion tile size is a multiple of it.
+constexpr int kChunk = 256;
+
+// Device copy of a graph: offsets are int32 when the entry count allows, else int64.
+struct GraphDev {
+  int device = 0;
+  int num_sms = 0;
+  int64_t n = 0;
+  int64_t nnz = 0;
+  bool off64 = false;
+  void* off = nullptr;      // OffT[n + 1]
+  int32_t* cols = nullptr;  // int32[nnz]
+  Packed pk{};
+};
+
+// Work buffers of single-source searches on one graph (reused across calls).
+struct SingleWs {
+  bool ready = false;
+  uint32_t* bitmap = nullptr;  // ceil(n / 32) words
+  int32_t* v[2] = {nullptr, nullptr};
+  void* cum[2] = {nullptr, nullptr};
+  void* base[2] = {nullptr, nullptr};
+  int32_t* chunk[2] = {nullptr, nullptr};
+  int64_t chunk_cap = 0;       // entries per chunk array
+  Ctl* ctl = nullptr;
+  void* scan_partial = nullptr;
+  int scan_parts = 0;
+  int32_t* host_levels = nullptr;   // device staging when the caller passes host outputs
+  int32_t* host_parents = nullptr;
+  Ctl* ctl_host = nullptr;          // pinned mirror of ctl
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  template <typename OffT>
+  FrontierBuf<OffT> fr(int i) const {
+    return FrontierBuf<OffT>{v[i], reinterpret_cast<OffT*>(cum[i]), reinterpret_cast<OffT*>(base[i])};
+  }
+};
+
+template <typename OffT>
+struct ExpandArgs {
+  const OffT* off;
+  const int32_t* cols;
+  uint32_t* bitmap;
+  int64_t n;
+  FrontierBuf<OffT> fr[2];
+  int32_t* chunk[2];
+  Ctl* ctl;
+  Packed pk;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
+struct ExpandShape {
+  int id, block, e, claim;
+};
+extern const ExpandShape kExpandShapes[];
+extern const int kNumExpandShapes;
+
+template <typename OffT>
+void launch_init_single(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
+                        cudaStream_t st);
+template <typename OffT>
+void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, int32_t level, int32_t* levels,
+                          int32_t* parents, SingleWs& ws, cudaStream_t st);
+template <typename OffT>
+cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaStream_t st);
+template <typename OffT>
+int expand_grid(int shape, int num_sms);
+
+}  // namespace gbfs

@@ -1,0 +1,80 @@
+"""The C-ABI library builds for sm_103a, loads, exports every function include/gbfs.h
+declares, and rejects bad arguments on the host before touching a GPU (CPU only)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1408_1605_gb300 import _build, capi
+
+    _build.build_bfs()
+    return capi
+
+
+def test_exports_every_declared_symbol(capi):
+    names = capi.declared_functions()
+    assert "bfs_graph_create" in names and "bfs_run" in names and "bfs_expand" in names
+    L = ctypes.CDLL(capi.library_path())
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_version(capi):
+    assert "sm_103a" in capi.bfs_version()
+
+
+def _create(capi, off, cols, n, nnz, flags):
+    out = ctypes.c_void_p()
+    s = capi.lib().bfs_graph_create(capi.ptr(off), capi.ptr(cols), n, nnz, flags, 0, ctypes.byref(out))
+    return s, out.value
+
+
+def test_create_rejects_bad_arguments(capi):
+    off = np.array([0, 1, 2], dtype=np.int32)
+    cols = np.array([1, 0], dtype=np.int32)
+    L = capi.lib()
+    assert L.bfs_graph_create(capi.ptr(off), capi.ptr(cols), 2, 2, 0, 0, None) == 1  # out NULL
+    assert _create(capi, None, cols, 2, 2, 0)[0] == 1
+    assert _create(capi, off, None, 2, 2, 0)[0] == 1
+    assert _create(capi, off, cols, 0, 2, 0)[0] == 1
+    assert _create(capi, off, cols, 2, -1, 0)[0] == 1
+    assert _create(capi, off, cols, 2, 2, 0x1000)[0] == 1
+    assert _create(capi, off, cols, 2, 2, capi.BFS_HOST_PTRS | capi.BFS_DEVICE_PTRS)[0] == 1
+    assert _create(capi, off, cols, 2, 2, capi.BFS_OFFSETS_INT32 | capi.BFS_OFFSETS_INT64)[0] == 1
+    assert "both set" in capi.bfs_last_error()
+
+
+def test_create_rejects_malformed_csr(capi):
+    cols = np.array([1, 0], dtype=np.int32)
+    for off in ([1, 1, 2], [0, 2, 1], [0, 1, 3]):
+        s, _ = _create(capi, np.array(off, dtype=np.int32), cols, 2, 2, 0)
+        assert s == 2, off
+    s, _ = _create(capi, np.array([0, 1, 2], dtype=np.int64), cols, 2, 2, capi.BFS_OFFSETS_INT64)
+    assert s != 2  # well-formed: fails later only for want of a GPU, or succeeds on one
+    bad_cols = np.array([1, 5], dtype=np.int32)
+    s, _ = _create(capi, np.array([0, 1, 2], dtype=np.int32), bad_cols, 2, 2, capi.BFS_VALIDATE)
+    assert s == 2 and "out of range" in capi.bfs_last_error()
+    asym = np.array([1, 1], dtype=np.int32)  # 0->1, 1->1 : not symmetric
+    s, _ = _create(capi, np.array([0, 1, 2], dtype=np.int32), asym, 2, 2, capi.BFS_VALIDATE)
+    assert s == 2 and "symmetric" in capi.bfs_last_error()
+
+
+def test_calls_reject_null_graph(capi):
+    L = capi.lib()
+    lv = np.zeros(4, dtype=np.int32)
+    assert L.bfs_run(None, 0, capi.ptr(lv), capi.ptr(lv), None, None) == 1
+    assert L.bfs_expand(None, None, 0, 1, None, None, None, None, None, None) == 1
+    assert L.bfs_graph_info(None, None, None) == 1
+    assert L.bfs_graph_destroy(None) == 0
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1408_1605_gb300 import _build, capi
+
+    monkeypatch.setattr(_build, "LIB_BFS", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.lib()
