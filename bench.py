@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: harmonic-mean GTEPS of single-source BFS on one GB300, with the achieved
+fraction of the HBM roofline, an end-to-end figure through the C ABI with host buffers,
+and the CPU oracle timed as a baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A step is one complete search from one root (init, every level's expansion, level loop
+on the device). K steps use K distinct seeded roots. TEPS per root = m_c / device time,
+m_c = undirected input edges in the traversed component (Sec. 4 of the paper); the value
+is the harmonic mean over roots (Sec. 4: 64 roots, harmonic mean). With --gpus N > 1
+(torchrun, one process per GPU) every rank runs its own replica of the graph on its own
+roots (no collective on the data path) and the value is the sum of per-rank harmonic
+means. Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "harmonic-mean GTEPS over roots (single-source BFS); % of HBM peak"
+UNIT = "GTEPS"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def harmonic_mean(xs):
+    xs = [x for x in xs]
+    return len(xs) / sum(1.0 / x for x in xs) if xs and all(x > 0 for x in xs) else 0.0
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("bfs_kernels.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1408_1605_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """Per-launch DRAM bytes of the expansion kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(PROFILES, "k_expand_traffic.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m_hash or m_hash.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_per_launch\[{re.escape(workload)}\]:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled with nvidia-smi while the timed region runs
+
+class ClockSampler:
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        inside = [s for t, s in self.samples if t0 <= t <= t1 + 0.15]
+        used = inside if inside else [s for _, s in self.samples]
+        sm, mx, reasons = [], [], set()
+        for s in used:
+            try:
+                sm.append(float(s[1]))
+                mx.append(float(s[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(self.REASONS, s[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples_in_window": len(inside), "samples": len(used)}
+
+
+def gpu_smi_id():
+    try:
+        import torch
+
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def alg_bytes_expand(m_c: int, n_c: int, off_bytes: int) -> int:
+    """Algorithmic HBM bytes of one search's expansion launches: every reached vertex's
+    row is read once (2 m_c column ids of 4 B), and per reached vertex its offsets pair,
+    its queue entry written and read (id 4 B + scan value), and its level and parent."""
+    per_vertex = 2 * off_bytes + (4 + off_bytes) * 2 + 8
+    return 8 * m_c + per_vertex * n_c
+
+
+def run_reference(args, wl, g, roots, rank):
+    """The reference arm: the CPU oracle as it stands, one thread, on the same graph and
+    roots; steps are bounded by a wall-clock budget so the run ends within minutes."""
+    import oracle
+
+    if rank != 0:
+        return 0
+    t0 = time.perf_counter()
+    _ = int(g.cols[:: 1 << 12].sum())  # touch the arrays once (warm-up)
+    warm_s = time.perf_counter() - t0
+    teps, times, used = [], [], 0
+    budget = float(os.environ.get("GBFS_REFERENCE_BUDGET_S", "150"))
+    t_start = time.perf_counter()
+    for r in roots[: args.steps]:
+        t = time.perf_counter()
+        lv, _ = oracle.bfs(g.offsets, g.cols, int(r))
+        dt = time.perf_counter() - t
+        m_c = oracle.component_edges(g.offsets, lv)
+        teps.append(m_c / dt / 1e9)
+        times.append(dt)
+        used += 1
+        if time.perf_counter() - t_start > budget:
+            break
+    hm = harmonic_mean(teps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(hm, 4), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": used, "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(times) / max(used, 1), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+        "config": config_for(wl, g, args),
+        "cpu_baseline": {"value": round(hm, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{used} of {args.steps} requested roots (wall-clock budget {budget:.0f} s); "
+                                   f"warm-up = one strided pass over the CSR ({warm_s:.1f} s)"},
+        "e2e": {"value": round(hm, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_for(wl, g, args) -> dict:
+    return {"workload": wl.name, "description": wl.description, "n_vertices": g.n, "csr_entries": g.nnz,
+            "offsets": "int64" if g.nnz > 2**31 - 1 else "int32", "roots": args.steps,
+            "l2_flush": "inputs larger than L2 (column array and per-root outputs exceed the 129 MB L2)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat-s26-ef16")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=16)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+
+    from paper_1408_1605_gb300.workloads import WORKLOADS
+
+    wl = WORKLOADS[args.workload]
+    rank, world, local_rank = dist_env()
+    t = time.perf_counter()
+    g = wl.make()
+    log(f"[bench] {wl.name}: n={g.n} nnz={g.nnz} generated in {time.perf_counter() - t:.1f}s")
+    pool = wl.pick_roots(g, max(64, (args.warmup + args.steps) * world))
+    if pool.size == 0:
+        raise SystemExit("graph has no vertex with degree > 0")
+    import numpy as np
+
+    need = (args.warmup + args.steps) * world
+    pool = np.resize(pool, need) if pool.size < need else pool[:need]
+    if args.impl == "reference":
+        timed_roots = pool[args.warmup * world:][rank::world]
+        return run_reference(args, wl, g, timed_roots, rank)
+
+    import torch
+
+    from paper_1408_1605_gb300 import capi
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    warm_roots = pool[: args.warmup * world][rank::world]
+    timed_roots = pool[args.warmup * world:][rank::world]
+
+    t = time.perf_counter()
+    h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
+    log(f"[bench] upload {time.perf_counter() - t:.1f}s")
+    off_bytes = 8 if g.nnz > 2**31 - 1 else 4
+    lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for r in warm_roots:
+        capi.bfs_run(h, int(r), lv, pr, want_stats=True)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_smi_id())
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    w0 = time.time()
+    ev0.record()
+    for r in timed_roots:
+        st = capi.bfs_run(h, int(r), lv, pr, want_stats=True)
+        stats.append(st.as_dict())
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    w1 = time.time()
+    time.sleep(0.2)
+    sampler.stop()
+    clocks = sampler.summary(w0, w1)
+    elapsed_ms = ev0.elapsed_time(ev1)
+
+    teps = [s["edges_traversed"] / (s["device_ms"] * 1e-3) / 1e9 for s in stats]
+    hm = harmonic_mean(teps)
+    total_bytes = sum(alg_bytes_expand(s["edges_traversed"], s["vertices_reached"], off_bytes) for s in stats)
+    expand_ms = sum(s["expand_ms"] for s in stats)
+    launches_expand = sum(s["depth"] for s in stats)
+    launches = sum(s["depth"] + 1 for s in stats)
+    achieved = total_bytes / (expand_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host (pinned) outputs: device->host copy of the
+    # levels and parents inside the timed region, the root passed in as the step's input
+    e2e_roots = timed_roots[: max(1, min(args.e2e_steps, len(timed_roots)))]
+    hl = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    hp = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    capi.bfs_run(h, int(e2e_roots[0]), hl, hp)
+    e2e_teps = []
+    for r in e2e_roots:
+        t = time.perf_counter()
+        st = capi.bfs_run(h, int(r), hl, hp, want_stats=True)
+        dt = time.perf_counter() - t
+        e2e_teps.append(st.edges_traversed / dt / 1e9)
+    e2e_hm = harmonic_mean(e2e_teps)
+
+    # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks
+    value, ms_step = hm, elapsed_ms / max(len(stats), 1)
+    if world > 1:
+        t_hm = torch.tensor([hm, e2e_hm, ms_step], dtype=torch.float64, device="cuda")
+        gathered = [torch.zeros_like(t_hm) for _ in range(world)]
+        torch.distributed.all_gather(gathered, t_hm)
+        value = float(sum(x[0] for x in gathered))
+        e2e_hm = float(sum(x[1] for x in gathered))
+        ms_step = float(max(x[2] for x in gathered))
+
+    parity, cpu_baseline = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        parity, cpu_baseline = cpu_leg(args, g, h, timed_roots, lv, pr)
+
+    if rank == 0:
+        peaks = load_peaks()
+        traffic = profiled_traffic(wl.name)
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": len(stats),
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+            "config": config_for(wl, g, args),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                         "kernel": "k_expand", "launches": launches_expand,
+                         "peak_source": peaks["source"],
+                         "alg_bytes_per_launch": round(total_bytes / max(launches_expand, 1))},
+            "e2e": {"value": round(e2e_hm, 3), "unit": UNIT, "h2d_bytes_per_step": 4,
+                    "d2h_bytes_per_step": 8 * g.n + 72, "steps": len(e2e_roots)},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "detail": {"mean_device_ms": round(sum(s["device_ms"] for s in stats) / len(stats), 4),
+                       "mean_expand_ms": round(expand_ms / len(stats), 4),
+                       "mean_depth": round(launches_expand / len(stats), 2),
+                       "mean_m_c": round(sum(s["edges_traversed"] for s in stats) / len(stats)),
+                       "min_gteps": round(min(teps), 3), "max_gteps": round(max(teps), 3)},
+        }
+        if parity is not None:
+            line["parity"] = parity
+        if cpu_baseline is not None:
+            line["cpu_baseline"] = cpu_baseline
+        print(json.dumps(line), flush=True)
+    capi.bfs_graph_destroy(h)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if parity is not None and not parity["ok"]:
+        return 1
+    return 0
+
+
+def cpu_leg(args, g, h, roots, lv, pr):
+    """Oracle timed single-threaded on a bounded sample of the timed roots; the GPU result
+    for the same roots is checked against it (levels exact, parents valid)."""
+    import numpy as np
+
+    import oracle
+    from paper_1408_1605_gb300 import capi
+
+    teps, checked, exact_all, valid_all, used = [], 0, True, True, 0
+    t_all = time.perf_counter()
+    for r in roots:
+        t = time.perf_counter()
+        ref, _ = oracle.bfs(g.offsets, g.cols, int(r))
+        dt = time.perf_counter() - t
+        m_c = oracle.component_edges(g.offsets, ref)
+        teps.append(m_c / dt / 1e9)
+        used += 1
+        capi.bfs_run(h, int(r), lv, pr, want_stats=True)
+        got_l, got_p = lv.cpu().numpy(), pr.cpu().numpy()
+        exact_all &= bool(np.array_equal(got_l, ref))
+        code, _ = oracle.check_tree(g.offsets, g.cols, int(r), ref, got_l, got_p)
+        valid_all &= code == 0
+        checked += 1
+        if time.perf_counter() - t_all > args.cpu_budget_s:
+            break
+    parity = {"roots_checked": checked, "levels_exact": exact_all, "parents_valid": valid_all,
+              "ok": exact_all and valid_all}
+    cpu = {"value": round(harmonic_mean(teps), 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{used} of the {len(roots)} timed roots, full searches on the same graph"}
+    return parity, cpu
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -73,6 +73,7 @@ typedef struct bfs_stats {
   int64_t vertices_reached; /* including the root */
   int64_t edges_traversed;  /* m_c */
   double device_ms;         /* device time of the whole search, CUDA events on `stream` */
+  double expand_ms;         /* the level loop alone (all expansion launches), CUDA events */
 } bfs_stats;
 
 /* Copies a CSR graph into library-owned device memory on the current CUDA device.
@@ -113,8 +114,11 @@ GBFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *levels, int32_
  *     levels[v] = level, parents[v] = the frontier vertex whose edge claimed v;
  *   next int32[n]: receives the newly claimed vertices, each once, in unspecified order;
  *   next_count int64 (device): receives their number.
- * `level` must be >= 1. The call returns once the work is enqueued. Failures:
- * BFS_ERR_INVALID_ARG, BFS_ERR_OOM, BFS_ERR_CUDA. */
+ * `level` must be >= 1. The call synchronizes `stream` and returns after the level has
+ * completed, so that range errors can be reported. Failures: BFS_ERR_INVALID_ARG (a
+ * frontier vertex outside [0, n), or a frontier whose edge total exceeds the graph's
+ * entry count), BFS_ERR_INVALID_GRAPH (a column id out of range), BFS_ERR_OOM,
+ * BFS_ERR_CUDA. */
 GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n_frontier, int32_t level,
                                uint32_t *bitmap, int32_t *levels, int32_t *parents, int32_t *next,
                                int64_t *next_count, void *stream);

@@ -37,7 +37,7 @@ class BfsError(RuntimeError):
 
 class bfs_stats(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("reserved", ctypes.c_int32), ("vertices_reached", ctypes.c_int64),
-                ("edges_traversed", ctypes.c_int64), ("device_ms", ctypes.c_double)]
+                ("edges_traversed", ctypes.c_int64), ("device_ms", ctypes.c_double), ("expand_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -64,6 +64,7 @@ static void free_single_ws(SingleWs& ws) {
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);
   if (ws.ev0) cudaEventDestroy(ws.ev0);
   if (ws.ev1) cudaEventDestroy(ws.ev1);
+  if (ws.ev_mid) cudaEventDestroy(ws.ev_mid);
   ws = SingleWs{};
 }
 
@@ -91,7 +92,8 @@ bfs_status ensure_single_ws(bfs_graph_s* G) {
       s = cuda_fail(e, "pinned control mirror");
       goto bad;
     }
-    if ((e = cudaEventCreate(&ws.ev0)) != cudaSuccess || (e = cudaEventCreate(&ws.ev1)) != cudaSuccess) {
+    if ((e = cudaEventCreate(&ws.ev0)) != cudaSuccess || (e = cudaEventCreate(&ws.ev1)) != cudaSuccess ||
+        (e = cudaEventCreate(&ws.ev_mid)) != cudaSuccess) {
       s = cuda_fail(e, "events");
       goto bad;
     }
@@ -214,6 +216,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
   if ((e = cudaEventRecord(ws.ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   launch_init_single<OffT>(G->g, root, dl, dp, ws, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "init kernel");
+  if ((e = cudaEventRecord(ws.ev_mid, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if (G->host_loop) {
     ExpandArgs<OffT> a = make_args<OffT>(G, ws.bitmap);
     for (int64_t it = 0; it <= G->g.n; ++it) {
@@ -249,13 +252,15 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     const Ctl& c = *ws.ctl_host;
     if (c.error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
     if (stats) {
-      float ms = 0.f;
+      float ms = 0.f, loop_ms = 0.f;
       cudaEventElapsedTime(&ms, ws.ev0, ws.ev1);
+      cudaEventElapsedTime(&loop_ms, ws.ev_mid, ws.ev1);
       stats->depth = c.depth;
       stats->reserved = 0;
       stats->vertices_reached = c.reached;
       stats->edges_traversed = c.edges2 / 2;
       stats->device_ms = ms;
+      stats->expand_ms = loop_ms;
     }
   }
   return BFS_OK;

@@ -14,7 +14,7 @@ namespace gbfs {
 struct BatchState;  // multi-source work buffers, see bfs_batch.cu
 
 // Expansion shape used unless the autotuner or GBFS_SHAPE picks another.
-constexpr int kDefaultShape = 1;
+constexpr int kDefaultShape = 0;
 
 bfs_status fail(bfs_status s, const std::string& msg);
 bfs_status cuda_fail(cudaError_t e, const char* what);

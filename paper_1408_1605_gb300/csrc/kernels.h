@@ -39,7 +39,7 @@ struct SingleWs {
   int32_t* host_levels = nullptr;   // device staging when the caller passes host outputs
   int32_t* host_parents = nullptr;
   Ctl* ctl_host = nullptr;          // pinned mirror of ctl
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_mid = nullptr;
 
   template <typename OffT>
   FrontierBuf<OffT> fr(int i) const {

@@ -1,0 +1,61 @@
+"""Named synthetic workloads (graph family, size, seeds) used by the tests and the bench.
+
+Seeds: graph seed = GRAPH_SEED_BASE + index of the workload group below; root seed =
+graph seed ^ 0x5EED. The R-MAT graphs stand in for the paper's Graph500 R-MAT inputs
+(Sec. 4, Table 1: scale per GPU, edge factor 16, 64 random roots per measurement)."""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+from . import graphs
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    kind: str            # rmat | uniform | grid3d
+    scale: int = 0       # rmat / uniform: n = 2^scale
+    edge_factor: int = 16
+    dims: tuple = ()
+    group: int = 0       # seed group
+    roots: int = 64
+    description: str = ""
+
+    @property
+    def graph_seed(self) -> int:
+        return graphs.GRAPH_SEED_BASE + self.group + (100 if self.kind == "uniform" else 0)
+
+    @property
+    def root_seed(self) -> int:
+        return graphs.root_seed(self.graph_seed)
+
+    def make(self, threads: int = 0) -> graphs.CSRGraph:
+        if self.kind == "rmat":
+            return graphs.rmat(self.scale, self.edge_factor, seed=self.graph_seed, threads=threads)
+        if self.kind == "uniform":
+            n = 1 << self.scale
+            return graphs.uniform(n, self.edge_factor * n, seed=self.graph_seed, threads=threads)
+        if self.kind == "grid3d":
+            return graphs.grid3d(*self.dims, threads=threads)
+        raise ValueError(self.kind)
+
+    def pick_roots(self, g: graphs.CSRGraph, k: int):
+        return graphs.pick_roots(g, k, self.root_seed)
+
+
+WORKLOADS = {w.name: w for w in [
+    Workload("rmat-s16-ef16", "rmat", 16, group=0, roots=16,
+             description="R-MAT scale 16, edge factor 16, 16 roots (small parity case)"),
+    Workload("rmat-s22-ef16", "rmat", 22, group=1, roots=64, description="R-MAT scale 22, edge factor 16, 64 roots"),
+    Workload("grid3d-256", "grid3d", dims=(256, 256, 256), group=1, roots=64,
+             description="3D 6-neighbour grid 256^3, non-periodic, 64 roots"),
+    Workload("rmat-s26-ef16", "rmat", 26, group=2, roots=64,
+             description="R-MAT scale 26, edge factor 16, 64 roots (int64 offsets in; the library narrows them to int32 when the cleaned entry count fits)"),
+    Workload("uniform-s26-ef16", "uniform", 26, group=2, roots=64,
+             description="uniform G(n, m), n = 2^26, m = 16 n, 64 roots"),
+    Workload("rmat-s24-ef16", "rmat", 24, group=4, roots=64, description="R-MAT scale 24, edge factor 16"),
+    Workload("rmat-s20-ef16", "rmat", 20, group=4, roots=64, description="R-MAT scale 20, edge factor 16"),
+    Workload("grid3d-192", "grid3d", dims=(192, 192, 192), group=4, roots=64, description="3D grid 192^3"),
+    Workload("uniform-n8M-deg8", "uniform", 23, edge_factor=4, group=4, roots=64,
+             description="uniform G(n, m), n = 2^23, mean degree 8"),
+]}
