@@ -123,6 +123,28 @@ GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n
                                uint32_t *bitmap, int32_t *levels, int32_t *parents, int32_t *next,
                                int64_t *next_count, void *stream);
 
+/* Single-source BFS that allocates nothing, for callers that may not allocate device
+ * memory at call time: code whose framework allocator owns all device memory, loops in
+ * which cudaMalloc / cudaFree would synchronize the device, services that must not fail
+ * with out-of-memory mid-request. The paper has no counterpart; the search is the same
+ * as bfs_run's, with every work buffer in one static device array (about 6.3 MB, held by
+ * every GPU that loads the library until the process exits).
+ *   row_offsets int32[n_vertices + 1], cols int32[n_entries]: device memory, a symmetric
+ *     CSR as for bfs_graph_create (the offsets are checked on the device; column ids are
+ *     range-checked during the search).
+ *   levels, parents int32[n_vertices]: device memory, written as by bfs_run.
+ * Limits: 1 <= n_vertices <= 262144 and 0 <= n_entries <= 4194304; larger sizes are
+ * rejected with BFS_ERR_INVALID_ARG before any GPU work. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture. Every call on a device shares the array and
+ * re-initializes what must start cleared; two searches using it at the same time on the
+ * GPU would race, so the call holds a process-wide lock and returns only after its search
+ * has finished on `stream`. Failures: BFS_ERR_INVALID_ARG, BFS_ERR_INVALID_GRAPH,
+ * BFS_ERR_CUDA. */
+GBFS_API bfs_status bfs_run_noalloc(const int32_t *row_offsets, const int32_t *cols, int64_t n_vertices,
+                                    int64_t n_entries, int32_t root, int32_t *levels, int32_t *parents,
+                                    void *stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 GBFS_API const char *bfs_last_error(void);
 

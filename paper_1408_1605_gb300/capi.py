@@ -68,6 +68,7 @@ def lib():
             "bfs_graph_info": [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
             "bfs_run": [_P, i32, _P, _P, _P, ctypes.POINTER(bfs_stats)],
             "bfs_expand": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P],
+            "bfs_run_noalloc": [_P, _P, i64, i64, i32, _P, _P, _P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -145,6 +146,12 @@ def bfs_expand(graph: int, frontier, n_frontier: int, level: int, bitmap, levels
                stream=None) -> None:
     check(lib().bfs_expand(graph, ptr(frontier), int(n_frontier), int(level), ptr(bitmap), ptr(levels), ptr(parents),
                            ptr(next_), ptr(next_count), stream_handle(stream)))
+
+
+def bfs_run_noalloc(row_offsets, cols, n_vertices: int, n_entries: int, root: int, levels, parents,
+                    stream=None) -> None:
+    check(lib().bfs_run_noalloc(ptr(row_offsets), ptr(cols), int(n_vertices), int(n_entries), int(root),
+                                ptr(levels), ptr(parents), stream_handle(stream)))
 
 
 def bfs_last_error() -> str:
