@@ -104,6 +104,21 @@ GBFS_API bfs_status bfs_graph_info(bfs_graph_t g, int64_t *n_vertices, int64_t *
 GBFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *levels, int32_t *parents, void *stream,
                             bfs_stats *stats);
 
+/* Multi-source search: up to 64 roots run as one wave, one bit per root in a 64-bit
+ * visited mask and 64-bit frontier masks per vertex, so that every row read from the CSR
+ * serves all the roots that have the vertex in their frontier. Each root's result is the
+ * single-source result (levels identical; parents any valid BFS tree). The paper has no
+ * batched form; each root's search is Algorithm 2 / Algorithm 3 with R = C = 1.
+ *   roots: HOST int32[n_roots], 1 <= n_roots <= 64, each in [0, n) (repeats allowed).
+ *   levels, parents: int32[n_roots][n_vertices] (row b belongs to roots[b]), device memory
+ *     or host memory (detected; results copied back before return).
+ *   per_root_stats: NULL or bfs_stats[n_roots]; device_ms / expand_ms are the wave's time.
+ * The call returns once the work is enqueued unless stats are requested or the outputs
+ * are host memory. Failures: BFS_ERR_INVALID_ARG, BFS_ERR_INVALID_GRAPH, BFS_ERR_OOM,
+ * BFS_ERR_CUDA. */
+GBFS_API bfs_status bfs_run_batch(bfs_graph_t g, const int32_t *roots, int n_roots, int32_t *levels,
+                                  int32_t *parents, void *stream, bfs_stats *per_root_stats);
+
 /* One top-down level on caller-held state: the frontier expansion routine of Algorithm 2
  * line 14 (Algorithm 3) with R = C = 1, including the degree gather and exclusive scan
  * (Sec. 3.4). All pointers are device memory:

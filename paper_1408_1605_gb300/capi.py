@@ -69,6 +69,7 @@ def lib():
             "bfs_run": [_P, i32, _P, _P, _P, ctypes.POINTER(bfs_stats)],
             "bfs_expand": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P],
             "bfs_run_noalloc": [_P, _P, i64, i64, i32, _P, _P, _P],
+            "bfs_run_batch": [_P, _P, ctypes.c_int, _P, _P, _P, _P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -140,6 +141,17 @@ def bfs_run(graph: int, root: int, levels, parents, stream=None, want_stats: boo
     check(lib().bfs_run(graph, int(root), ptr(levels), ptr(parents), stream_handle(stream),
                         ctypes.byref(st) if want_stats else None))
     return st if want_stats else None
+
+
+def bfs_run_batch(graph: int, roots, levels, parents, stream=None, want_stats: bool = False):
+    """roots: host int32 array (<= 64); levels / parents: int32[len(roots)][n]."""
+    import numpy as np
+
+    r = np.ascontiguousarray(roots, dtype=np.int32)
+    st = (bfs_stats * max(1, r.size))()
+    check(lib().bfs_run_batch(graph, r.ctypes.data, int(r.size), ptr(levels), ptr(parents), stream_handle(stream),
+                              st if want_stats else None))
+    return list(st)[: r.size] if want_stats else None
 
 
 def bfs_expand(graph: int, frontier, n_frontier: int, level: int, bitmap, levels, parents, next_, next_count,

@@ -1,0 +1,89 @@
+// Multi-source (batched) BFS state shared by the batch and serving translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace gbfs {
+
+constexpr int kMaxWave = 64;  // roots per wave: one bit each in a 64-bit mask
+
+// Where the outputs of each bit (slot) of a wave go, and the wave level at which each
+// slot's root entered (so level[v] for that root = wave level - start).
+struct WaveSlots {
+  int32_t* lvl[kMaxWave];
+  int32_t* par[kMaxWave];
+  int32_t start[kMaxWave];
+};
+
+// Device control block of a wave. Queue buffers rotate by 3 (the expansion of frontier t
+// clears the masks of frontier t - 1), scan buffers and counters by 2.
+struct BatchCtl {
+  unsigned long long counter[2];
+  unsigned int done[2];
+  int level;                      // wave level assigned by the running expansion (t + 1)
+  int cont;                       // next frontier non-empty
+  long long prev_count;           // size of frontier t - 1
+  unsigned int error;
+  int pad;
+  unsigned long long alive[2];    // OR of the masks claimed by the running expansion (next parity)
+};
+
+template <typename OffT>
+struct BatchArgs {
+  const OffT* off;
+  const int32_t* cols;
+  int64_t n;
+  unsigned long long* visited;    // V[v]: bit b set once root b reached v
+  unsigned long long* fmask[3];   // F_t[v]: bits of roots that have v in frontier t
+  int32_t* qv[3];                 // frontier vertex lists
+  OffT* cum[2];
+  OffT* base[2];
+  int32_t* chunk[2];
+  BatchCtl* ctl;
+  const WaveSlots* slots;
+  Packed pk;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
+// Work buffers of multi-source searches on one graph.
+struct BatchBufs {
+  bool ready = false;
+  unsigned long long* visited = nullptr;
+  unsigned long long* fmask[3] = {nullptr, nullptr, nullptr};
+  int32_t* qv[3] = {nullptr, nullptr, nullptr};
+  void* cum[2] = {nullptr, nullptr};
+  void* base[2] = {nullptr, nullptr};
+  int32_t* chunk[2] = {nullptr, nullptr};
+  int64_t chunk_cap = 0;
+  BatchCtl* ctl = nullptr;
+  WaveSlots* slots = nullptr;       // device
+  long long* stats = nullptr;       // device: per slot [edges2, reached, depth]
+  int32_t* roots_dev = nullptr;     // device: (vertex, mask lo, mask hi) per distinct root
+};
+
+struct RootSeed {
+  int32_t v;
+  unsigned long long mask;
+};
+
+template <typename OffT>
+void launch_batch_clear(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
+template <typename OffT>
+void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int n_seeds, int wave_level,
+                       bool fresh, cudaStream_t st);
+template <typename OffT>
+cudaError_t launch_batch_expand(const BatchArgs<OffT>& a, int grid, cudaStream_t st);
+template <typename OffT>
+int batch_expand_grid(int num_sms);
+void launch_fill(int32_t* p, int64_t count, int32_t value, int num_sms, cudaStream_t st);
+template <typename OffT>
+void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int n_slots, long long* stats,
+                        int num_sms, cudaStream_t st);
+void launch_clear_bits(unsigned long long* visited, int64_t n, unsigned long long mask, int num_sms,
+                       cudaStream_t st);
+
+}  // namespace gbfs

@@ -1,10 +1,313 @@
-// Multi-source (batched) BFS: filled in below.
+// C ABI of the multi-source search: bfs_run_batch runs up to 64 roots as one wave (one
+// bit per root in 64-bit visited / frontier masks). The level loop is a CUDA graph with a
+// conditional WHILE node, as for single-source searches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "batch.h"
 #include "capi_internal.h"
+#include "gbfs.h"
 
 namespace gbfs {
-struct BatchState {};
-void destroy_batch_state(bfs_graph_s* G) {
-  delete G->batch;
-  G->batch = nullptr;
+
+struct BatchState {
+  BatchBufs b;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 0;
+  cudaEvent_t ev0 = nullptr, ev_mid = nullptr, ev1 = nullptr;
+  BatchCtl* ctl_host = nullptr;      // pinned
+  long long* stats_host = nullptr;   // pinned, 3 * kMaxWave
+  int32_t* stage_lvl = nullptr;      // device staging when outputs are host memory
+  int32_t* stage_par = nullptr;
+  int stage_roots = 0;
+};
+
+static void free_batch(BatchState* S) {
+  BatchBufs& b = S->b;
+  cudaFree(b.visited);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(b.fmask[i]);
+    cudaFree(b.qv[i]);
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(b.cum[i]);
+    cudaFree(b.base[i]);
+    cudaFree(b.chunk[i]);
+  }
+  cudaFree(b.ctl);
+  cudaFree(b.slots);
+  cudaFree(b.stats);
+  cudaFree(b.roots_dev);
+  cudaFree(S->stage_lvl);
+  cudaFree(S->stage_par);
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->graph) cudaGraphDestroy(S->graph);
+  if (S->ev0) cudaEventDestroy(S->ev0);
+  if (S->ev_mid) cudaEventDestroy(S->ev_mid);
+  if (S->ev1) cudaEventDestroy(S->ev1);
+  if (S->ctl_host) cudaFreeHost(S->ctl_host);
+  if (S->stats_host) cudaFreeHost(S->stats_host);
 }
+
+void destroy_batch_state(bfs_graph_s* G) {
+  if (G->batch) {
+    free_batch(G->batch);
+    delete G->batch;
+    G->batch = nullptr;
+  }
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+bfs_status ensure_batch_state(bfs_graph_s* G) {
+  if (G->batch && G->batch->b.ready) return BFS_OK;
+  auto* S = new (std::nothrow) BatchState();
+  if (!S) return fail(BFS_ERR_OOM, "host allocation");
+  const GraphDev& g = G->g;
+  const size_t osz = g.off64 ? 8 : 4;
+  BatchBufs& b = S->b;
+  b.chunk_cap = g.nnz / kChunk + 2;
+  cudaError_t e = dalloc(&b.visited, (size_t)g.n);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = dalloc(&b.fmask[i], (size_t)g.n);
+    if (e == cudaSuccess) e = dalloc(&b.qv[i], (size_t)g.n);
+  }
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = dalloc(reinterpret_cast<char**>(&b.cum[i]), (size_t)g.n * osz);
+    if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&b.base[i]), (size_t)g.n * osz);
+    if (e == cudaSuccess) e = dalloc(&b.chunk[i], (size_t)b.chunk_cap);
+  }
+  if (e == cudaSuccess) e = dalloc(&b.ctl, 1);
+  if (e == cudaSuccess) e = dalloc(&b.slots, 1);
+  if (e == cudaSuccess) e = dalloc(&b.stats, 3 * kMaxWave);
+  if (e == cudaSuccess) e = dalloc(&b.roots_dev, 4 * kMaxWave);
+  if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&S->ev_mid);
+  if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->ctl_host), sizeof(BatchCtl), 0);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->stats_host), sizeof(long long) * 3 * kMaxWave, 0);
+  if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
+  if (e != cudaSuccess) {
+    free_batch(S);
+    delete S;
+    return cuda_fail(e, "batch work buffers");
+  }
+  S->grid = g.off64 ? batch_expand_grid<int64_t>(g.num_sms) : batch_expand_grid<int32_t>(g.num_sms);
+  b.ready = true;
+  G->batch = S;
+  return BFS_OK;
+}
+
+template <typename OffT>
+BatchArgs<OffT> batch_args(const bfs_graph_s* G) {
+  const GraphDev& g = G->g;
+  const BatchBufs& b = G->batch->b;
+  BatchArgs<OffT> a{};
+  a.off = reinterpret_cast<const OffT*>(g.off);
+  a.cols = g.cols;
+  a.n = g.n;
+  a.visited = b.visited;
+  for (int i = 0; i < 3; ++i) {
+    a.fmask[i] = b.fmask[i];
+    a.qv[i] = b.qv[i];
+  }
+  for (int i = 0; i < 2; ++i) {
+    a.cum[i] = reinterpret_cast<OffT*>(b.cum[i]);
+    a.base[i] = reinterpret_cast<OffT*>(b.base[i]);
+    a.chunk[i] = b.chunk[i];
+  }
+  a.ctl = b.ctl;
+  a.slots = b.slots;
+  a.pk = g.pk;
+  a.use_cond = 0;
+  return a;
+}
+
+template BatchArgs<int32_t> batch_args<int32_t>(const bfs_graph_s*);
+template BatchArgs<int64_t> batch_args<int64_t>(const bfs_graph_s*);
+
+template <typename OffT>
+static bfs_status build_batch_graph(bfs_graph_s* G) {
+  BatchState* S = G->batch;
+  cudaError_t e;
+  cudaGraph_t graph = nullptr;
+  if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+  cudaGraphConditionalHandle handle;
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t captured = nullptr;
+  BatchArgs<OffT> a = batch_args<OffT>(G);
+  if ((e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) goto bad;
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) goto bad;
+  a.cond = handle;
+  a.use_cond = 1;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) goto bad;
+  if ((e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    goto bad;
+  }
+  {
+    cudaError_t le = launch_batch_expand<OffT>(a, S->grid, cs);
+    e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e != cudaSuccess) goto bad;
+  if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) goto bad;
+  S->graph = graph;
+  S->exec = exec;
+  return BFS_OK;
+bad:
+  cudaGraphDestroy(graph);
+  return cuda_fail(e, "batch level-loop graph");
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename OffT>
+static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, int32_t* levels, int32_t* parents,
+                            cudaStream_t st, bfs_stats* stats) {
+  BatchState* S = G->batch;
+  const GraphDev& g = G->g;
+  cudaError_t e;
+  const bool host_out = !is_device_ptr(levels) || !is_device_ptr(parents);
+  int32_t* dl = levels;
+  int32_t* dp = parents;
+  const size_t per = (size_t)g.n;
+  if (host_out) {
+    if (S->stage_roots < n_roots) {
+      cudaFree(S->stage_lvl);
+      cudaFree(S->stage_par);
+      S->stage_lvl = S->stage_par = nullptr;
+      S->stage_roots = 0;
+      if ((e = dalloc(&S->stage_lvl, per * n_roots)) != cudaSuccess ||
+          (e = dalloc(&S->stage_par, per * n_roots)) != cudaSuccess)
+        return cuda_fail(e, "batch output staging");
+      S->stage_roots = n_roots;
+    }
+    dl = S->stage_lvl;
+    dp = S->stage_par;
+  }
+  // slot table: root b writes row b of the outputs
+  WaveSlots slots{};
+  for (int b = 0; b < kMaxWave; ++b) {
+    const int bb = b < n_roots ? b : 0;
+    slots.lvl[b] = dl + per * bb;
+    slots.par[b] = dp + per * bb;
+    slots.start[b] = 0;
+  }
+  // distinct roots, each with the mask of the slots it seeds
+  std::map<int32_t, unsigned long long> masks;
+  for (int b = 0; b < n_roots; ++b) masks[roots[b]] |= 1ull << b;
+  std::vector<RootSeed> seeds;
+  for (auto& kv : masks) seeds.push_back(RootSeed{kv.first, kv.second});
+  if (G->last_done) cudaStreamWaitEvent(st, G->last_done, 0);
+  if ((e = cudaEventRecord(S->ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if ((e = cudaMemcpyAsync(S->b.slots, &slots, sizeof(WaveSlots), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(S->b.roots_dev, seeds.data(), sizeof(RootSeed) * seeds.size(), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return cuda_fail(e, "batch inputs");
+  BatchArgs<OffT> a = batch_args<OffT>(G);
+  launch_fill(dl, (int64_t)per * n_roots, -1, g.num_sms, st);
+  launch_fill(dp, (int64_t)per * n_roots, -1, g.num_sms, st);
+  launch_batch_clear<OffT>(a, g.num_sms, st);
+  launch_batch_seed<OffT>(a, reinterpret_cast<const RootSeed*>(S->b.roots_dev), (int)seeds.size(), 0, true, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch init");
+  if ((e = cudaEventRecord(S->ev_mid, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if (G->host_loop) {
+    for (int64_t it = 0; it <= g.n; ++it) {
+      if ((e = launch_batch_expand<OffT>(a, S->grid, st)) != cudaSuccess) return cuda_fail(e, "batch expand");
+      if ((e = cudaMemcpyAsync(S->ctl_host, S->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "batch level sync");
+      if (!S->ctl_host->cont) break;
+    }
+  } else {
+    if (!S->exec) {
+      bfs_status s = build_batch_graph<OffT>(G);
+      if (s != BFS_OK) return s;
+    }
+    if ((e = cudaGraphLaunch(S->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  }
+  if ((e = cudaEventRecord(S->ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if (stats)
+    launch_batch_stats<OffT>(reinterpret_cast<const OffT*>(g.off), g.n, S->b.slots, n_roots, S->b.stats, g.num_sms,
+                             st);
+  if (host_out) {
+    if ((e = cudaMemcpyAsync(levels, dl, per * n_roots * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(parents, dp, per * n_roots * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "batch output copy");
+  }
+  if ((e = cudaMemcpyAsync(S->ctl_host, S->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "batch control copy");
+  if (stats && (e = cudaMemcpyAsync(S->stats_host, S->b.stats, sizeof(long long) * 3 * n_roots,
+                                    cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "batch stats copy");
+  if (!G->last_done && (e = cudaEventCreateWithFlags(&G->last_done, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate");
+  cudaEventRecord(G->last_done, st);
+  if (stats || host_out) {
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "batch search");
+    if (S->ctl_host->error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
+    if (stats) {
+      float ms = 0.f, loop_ms = 0.f;
+      cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+      cudaEventElapsedTime(&loop_ms, S->ev_mid, S->ev1);
+      for (int b = 0; b < n_roots; ++b) {
+        stats[b].depth = (int32_t)S->stats_host[3 * b + 2];
+        stats[b].reserved = 0;
+        stats[b].vertices_reached = S->stats_host[3 * b + 1];
+        stats[b].edges_traversed = S->stats_host[3 * b + 0] / 2;
+        stats[b].device_ms = ms;
+        stats[b].expand_ms = loop_ms;
+      }
+    }
+  }
+  return BFS_OK;
+}
+
 }  // namespace gbfs
+
+using namespace gbfs;
+
+extern "C" GBFS_API bfs_status bfs_run_batch(bfs_graph_t G, const int32_t* roots, int n_roots, int32_t* levels,
+                                             int32_t* parents, void* stream, bfs_stats* per_root_stats) {
+  clear_last_error();
+  if (!G) return fail(BFS_ERR_INVALID_ARG, "graph is NULL");
+  if (!roots || !levels || !parents) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  if (n_roots < 1 || n_roots > kMaxWave) return fail(BFS_ERR_INVALID_ARG, "n_roots outside [1, 64]");
+  for (int b = 0; b < n_roots; ++b)
+    if (roots[b] < 0 || roots[b] >= G->g.n) return fail(BFS_ERR_INVALID_ARG, "root outside [0, n)");
+  std::lock_guard<std::mutex> lock(G->mu);
+  cudaError_t e = cudaSetDevice(G->g.device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  bfs_status s = ensure_batch_state(G);
+  if (s != BFS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return G->g.off64 ? run_batch<int64_t>(G, roots, n_roots, levels, parents, st, per_root_stats)
+                    : run_batch<int32_t>(G, roots, n_roots, levels, parents, st, per_root_stats);
+}

@@ -1,0 +1,423 @@
+// Multi-source BFS kernels: up to 64 searches advance together, one bit per root in a
+// 64-bit visited mask V[v] and in per-frontier masks F_t[v]. The frontier of a wave is the
+// list of vertices with F_t[v] != 0; each of their rows is read once per level and serves
+// every root that has the vertex in its frontier. Per edge (u, v):
+//     new = F_t[u] & ~V[v];  old = atomicOr(&V[v], new);  claimed = new & ~old
+// (the visited-bitmap claim of Algorithm 3 lines 5-8, one bit per root); for every claimed
+// bit b the level and parent of (b, v) are written (lines 15, 17), and v joins frontier
+// t + 1 when atomicOr(&F_{t+1}[v], claimed) returns 0 (first touch), through the same
+// buffered append with the fused degree scan as the single-source kernel. Thread-to-edge
+// mapping is the single-source one (Sec. 3.4 and 3.4.1). The paper has no batched form;
+// batching multiplies the work done per column read.
+#include <cuda_runtime.h>
+
+#include "batch.h"
+#include "common.cuh"
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace gbfs {
+
+__global__ void k_fill(int32_t* p, int64_t count, int32_t value) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const bool aligned = (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+  if (aligned) {
+    int4* q = reinterpret_cast<int4*>(p);
+    const int64_t nv = count / 4;
+    const int4 val = make_int4(value, value, value, value);
+    for (int64_t i = tid; i < nv; i += stride) q[i] = val;
+    for (int64_t i = nv * 4 + tid; i < count; i += stride) p[i] = value;
+  } else {
+    for (int64_t i = tid; i < count; i += stride) p[i] = value;
+  }
+}
+
+void launch_fill(int32_t* p, int64_t count, int32_t value, int num_sms, cudaStream_t st) {
+  if (count > 0) k_fill<<<num_sms * 8, 256, 0, st>>>(p, count, value);
+}
+
+template <typename OffT>
+__global__ void k_batch_clear(BatchArgs<OffT> a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = tid; v < a.n; v += stride) {
+    a.visited[v] = 0ull;
+    a.fmask[0][v] = 0ull;
+    a.fmask[1][v] = 0ull;
+    a.fmask[2][v] = 0ull;
+  }
+}
+
+template <typename OffT>
+void launch_batch_clear(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
+  k_batch_clear<OffT><<<num_sms * 8, 256, 0, st>>>(a);
+}
+
+__global__ void k_clear_bits(unsigned long long* visited, int64_t n, unsigned long long keep) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = tid; v < n; v += stride) {
+    const unsigned long long x = visited[v];
+    if (x & ~keep) visited[v] = x & keep;
+  }
+}
+
+void launch_clear_bits(unsigned long long* visited, int64_t n, unsigned long long mask, int num_sms,
+                       cudaStream_t st) {
+  if (mask) k_clear_bits<<<num_sms * 8, 256, 0, st>>>(visited, n, ~mask);
+}
+
+// Adds roots to the frontier the next expansion will read (frontier t = level - 1). With
+// fresh != 0 a new wave starts at frontier 0. One thread: at most 64 roots.
+template <typename OffT>
+__global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_seeds, int fresh) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  BatchCtl* c = a.ctl;
+  if (fresh) {
+    c->counter[0] = c->counter[1] = 0;
+    c->done[0] = c->done[1] = 0;
+    c->level = 1;
+    c->cont = 1;
+    c->prev_count = 0;
+    c->error = 0;
+    c->alive[0] = c->alive[1] = 0;
+  }
+  const int t = c->level - 1;
+  const int cur = t & 1, q3 = t % 3;
+  long long cnt = a.pk.count(c->counter[cur]);
+  long long e = a.pk.edges(c->counter[cur]);
+  const WaveSlots* sl = a.slots;
+  for (int i = 0; i < n_seeds; ++i) {
+    const int32_t v = seeds[i].v;
+    const unsigned long long m = seeds[i].mask;
+    a.visited[v] |= m;
+    const unsigned long long old = a.fmask[q3][v];
+    a.fmask[q3][v] = old | m;
+    for (unsigned long long bits = m; bits; bits &= bits - 1) {
+      const int b = __ffsll((long long)bits) - 1;
+      sl->lvl[b][v] = 0;
+      sl->par[b][v] = v;
+    }
+    if (old == 0) {
+      const OffT o = a.off[v], d = a.off[v + 1] - o;
+      a.qv[q3][cnt] = v;
+      a.cum[cur][cnt] = (OffT)e;
+      a.base[cur][cnt] = o - (OffT)e;
+      write_chunks(a.chunk[cur], (OffT)e, d, (int32_t)cnt);
+      ++cnt;
+      e += (long long)d;
+    }
+  }
+  c->counter[cur] = a.pk.make(cnt, e);
+  c->cont = cnt > 0;
+}
+
+template <typename OffT>
+void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int n_seeds, int wave_level,
+                       bool fresh, cudaStream_t st) {
+  (void)wave_level;
+  k_batch_seed<OffT><<<1, 32, 0, st>>>(a, seeds_dev, n_seeds, fresh ? 1 : 0);
+}
+
+constexpr int kBatchBlock = 256;
+constexpr int kBatchE = 4;
+constexpr int kBatchClaim = 2048;
+
+template <typename OffT>
+struct BatchSmem {
+  static constexpr int T = kBatchBlock * kBatchE;
+  static constexpr int CAP = T + 1;
+  static constexpr size_t off_f = 0;  // uint64 masks first (8-byte aligned)
+  static constexpr size_t off_base = off_f + 8 * CAP;
+  static constexpr size_t off_rel = off_base + sizeof(OffT) * CAP;
+  static constexpr size_t off_u = off_rel + 4 * (CAP + 1);
+  static constexpr size_t off_claim = ((off_u + 4 * CAP) + 15) & ~size_t(15);
+  static constexpr size_t bytes = off_claim + sizeof(int2) * kBatchClaim;
+};
+
+template <typename OffT>
+__device__ __forceinline__ void batch_flush(const BatchArgs<OffT>& a, int nxt, int q3n, int2* s_claim, int nc,
+                                            OffT* s_warp, unsigned long long* s_resv) {
+  constexpr int P = (kBatchClaim + kBatchBlock - 1) / kBatchBlock;
+  const int lo = min(nc, (int)threadIdx.x * P), hi = min(nc, lo + P);
+  OffT mine = 0;
+  for (int i = lo; i < hi; ++i) mine += (OffT)s_claim[i].y;
+  OffT total;
+  OffT run = block_exclusive_scan(mine, s_warp, &total);
+  if (threadIdx.x == 0) *s_resv = atomicAdd(&a.ctl->counter[nxt], a.pk.make(nc, (long long)total));
+  __syncthreads();
+  const unsigned long long resv = *s_resv;
+  const long long slot0 = a.pk.count(resv);
+  run += (OffT)a.pk.edges(resv);
+  for (int i = lo; i < hi; ++i) {
+    const int32_t v = s_claim[i].x;
+    const OffT d = (OffT)s_claim[i].y;
+    const int32_t slot = (int32_t)(slot0 + i);
+    a.qv[q3n][slot] = v;
+    a.cum[nxt][slot] = run;
+    a.base[nxt][slot] = a.off[v] - run;
+    write_chunks(a.chunk[nxt], run, d, slot);
+    run += d;
+  }
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kBatchBlock) k_expand_batch(BatchArgs<OffT> a) {
+  using S = BatchSmem<OffT>;
+  constexpr int T = S::T, CAP = S::CAP, E = kBatchE, BLOCK = kBatchBlock;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* s_f = reinterpret_cast<unsigned long long*>(smem + S::off_f);
+  OffT* s_base = reinterpret_cast<OffT*>(smem + S::off_base);
+  int32_t* s_rel = reinterpret_cast<int32_t*>(smem + S::off_rel);
+  int32_t* s_u = reinterpret_cast<int32_t*>(smem + S::off_u);
+  int2* s_claim = reinterpret_cast<int2*>(smem + S::off_claim);
+  __shared__ int32_t* s_lvl[kMaxWave];
+  __shared__ int32_t* s_par[kMaxWave];
+  __shared__ int32_t s_start[kMaxWave];
+  __shared__ OffT s_warp[33];
+  __shared__ unsigned long long s_resv, s_alive;
+  __shared__ int s_nclaim, s_klo, s_kend;
+
+  BatchCtl* ctl = a.ctl;
+  const int L = *(volatile int*)&ctl->level;
+  const int t = L - 1;
+  const int cur = t & 1, nxt = cur ^ 1, q3 = t % 3, q3n = (t + 1) % 3, q3p = (t + 2) % 3;
+  const unsigned long long pc = *(volatile unsigned long long*)&ctl->counter[cur];
+  const int64_t nf = a.pk.count(pc);
+  const OffT r = (OffT)a.pk.edges(pc);
+  const long long prev = *(volatile long long*)&ctl->prev_count;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < kMaxWave) {
+    s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
+    s_par[threadIdx.x] = a.slots->par[threadIdx.x];
+    s_start[threadIdx.x] = a.slots->start[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    s_nclaim = 0;
+    s_alive = 0ull;
+  }
+  // Frontier t - 1 is no longer read by anyone: clear its masks so that the buffer can
+  // collect frontier t + 2.
+  {
+    const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * BLOCK;
+    for (int64_t k = tid; k < prev; k += stride) a.fmask[q3p][a.qv[q3p][k]] = 0ull;
+  }
+  const unsigned long long* F = a.fmask[q3];
+  unsigned long long* Fn = a.fmask[q3n];
+  const int32_t* qv = a.qv[q3];
+  const OffT* cum = a.cum[cur];
+  const OffT* basep = a.base[cur];
+  const int32_t* chunk_in = a.chunk[cur];
+  const int64_t ntiles = ((int64_t)r + T - 1) / T;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const OffT e0 = (OffT)(tile * T);
+    const int cnt = (int)min((OffT)T, r - e0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_klo = chunk_in[e0 / kChunk];
+      s_kend = (e0 + cnt < r) ? chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+    }
+    __syncthreads();
+    const int klo = s_klo;
+    const int s = s_kend - klo + 1;
+    const bool fast = s <= CAP;
+    if (fast) {
+      for (int i = threadIdx.x; i < s; i += BLOCK) {
+        const int32_t u = qv[klo + i];
+        s_rel[i] = (int32_t)max(cum[klo + i] - e0, (OffT)0);
+        s_base[i] = basep[klo + i];
+        s_u[i] = u;
+        s_f[i] = F[u];
+      }
+      if (threadIdx.x == 0) s_rel[s] = 0x7fffffff;
+      __syncthreads();
+    }
+    int32_t vv[E], uu[E];
+    unsigned long long ff[E];
+    OffT col[E];
+    bool ok[E];
+    {
+      const int er0 = warp * 32 * E + lane;
+      int k = 0;
+      if (fast && er0 < cnt) k = binsearch_maxle(s_rel, 0, s, er0);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int er = er0 + 32 * j;
+        ok[j] = er < cnt;
+        uu[j] = 0;
+        ff[j] = 0ull;
+        col[j] = 0;
+        if (ok[j]) {
+          if (fast) {
+            int steps = 0;
+            while (s_rel[k + 1] <= er && steps < 4) { ++k; ++steps; }
+            if (s_rel[k + 1] <= er) k = binsearch_maxle(s_rel, k, s, er);
+            col[j] = s_base[k] + e0 + er;
+            uu[j] = s_u[k];
+            ff[j] = s_f[k];
+          } else {
+            const OffT e = e0 + er;
+            const int32_t kk = binsearch_maxle(cum, (int64_t)klo, (int64_t)s_kend + 1, e);
+            col[j] = basep[kk] + e;
+            uu[j] = qv[kk];
+            ff[j] = F[uu[j]];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) vv[j] = ok[j] ? ld_nc(a.cols + col[j]) : 0;
+    unsigned long long nb[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (ok[j] && (uint32_t)vv[j] >= (uint64_t)a.n) {
+        atomicOr(&ctl->error, kErrColumnRange);
+        ok[j] = false;
+      }
+      nb[j] = ok[j] ? (ff[j] & ~a.visited[vv[j]]) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int32_t v = vv[j];
+      unsigned long long claimed = 0ull;
+      if (nb[j]) claimed = nb[j] & ~atomicOr(a.visited + v, nb[j]);
+      bool first = false;
+      int32_t deg = 0;
+      if (claimed) {
+        for (unsigned long long bits = claimed; bits; bits &= bits - 1) {
+          const int b = __ffsll((long long)bits) - 1;
+          s_lvl[b][v] = L - s_start[b];
+          s_par[b][v] = uu[j];
+        }
+        atomicOr(&s_alive, claimed);
+        first = atomicOr(Fn + v, claimed) == 0ull;
+        if (first) deg = (int32_t)(a.off[v + 1] - a.off[v]);
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, first);
+      if (ball) {
+        const int leader = __ffs(ball) - 1;
+        int pos = 0;
+        if (lane == leader) pos = atomicAdd(&s_nclaim, __popc(ball));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (first) s_claim[pos + __popc(ball & lanemask_lt())] = make_int2(v, deg);
+      }
+    }
+    __syncthreads();
+    const int nc = s_nclaim;
+    if (nc > kBatchClaim - T) {
+      batch_flush<OffT>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
+      __syncthreads();
+      if (threadIdx.x == 0) s_nclaim = 0;
+    }
+  }
+  __syncthreads();
+  const int nc = s_nclaim;
+  if (nc > 0) batch_flush<OffT>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_alive) atomicOr(&ctl->alive[nxt], s_alive);
+    __threadfence();
+    const unsigned tdone = atomicAdd(&ctl->done[cur], 1u);
+    if (tdone == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long pn = atomicAdd(&ctl->counter[nxt], 0ull);
+      const long long nn = a.pk.count(pn);
+      ctl->prev_count = nf;
+      ctl->counter[cur] = 0;
+      ctl->done[cur] = 0;
+      ctl->alive[cur] = 0;
+      ctl->level = L + 1;
+      ctl->cont = nn > 0;
+      if (a.use_cond) cudaGraphSetConditional(a.cond, nn > 0 ? 1u : 0u);
+    }
+  }
+}
+
+template <typename OffT>
+cudaError_t launch_batch_expand(const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
+  using S = BatchSmem<OffT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_expand_batch<OffT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_expand_batch<OffT><<<grid, kBatchBlock, S::bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename OffT>
+int batch_expand_grid(int num_sms) {
+  using S = BatchSmem<OffT>;
+  cudaFuncSetAttribute(k_expand_batch<OffT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_batch<OffT>, kBatchBlock, S::bytes) !=
+      cudaSuccess)
+    per_sm = 1;
+  return (per_sm > 0 ? per_sm : 1) * num_sms;
+}
+
+// Per-slot statistics from the outputs: stats[3 b + 0] = sum of degrees of reached
+// vertices (2 m_c), [3 b + 1] = reached count, [3 b + 2] = max level + 1.
+template <typename OffT>
+__global__ void k_batch_stats(const OffT* __restrict__ off, int64_t n, const WaveSlots* slots, long long* stats) {
+  __shared__ long long s_red[3][32];
+  const int b = blockIdx.y;
+  const int32_t* lv = slots->lvl[b];
+  long long e2 = 0, reached = 0, depth = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = lv[v];
+    if (l >= 0) {
+      e2 += (long long)(off[v + 1] - off[v]);
+      ++reached;
+      depth = max(depth, (long long)l + 1);
+    }
+  }
+  for (int d = 16; d; d >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, d);
+    reached += __shfl_xor_sync(0xffffffffu, reached, d);
+    depth = max(depth, __shfl_xor_sync(0xffffffffu, depth, d));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][w] = e2;
+    s_red[1][w] = reached;
+    s_red[2][w] = depth;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long a0 = 0, a1 = 0, a2 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a0 += s_red[0][i];
+      a1 += s_red[1][i];
+      a2 = max(a2, s_red[2][i]);
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats[3 * b + 0]), (unsigned long long)a0);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats[3 * b + 1]), (unsigned long long)a1);
+    atomicMax(&stats[3 * b + 2], a2);
+  }
+}
+
+template <typename OffT>
+void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int n_slots, long long* stats,
+                        int num_sms, cudaStream_t st) {
+  cudaMemsetAsync(stats, 0, sizeof(long long) * 3 * n_slots, st);
+  dim3 grid((unsigned)std::max(1, num_sms * 2 / std::max(1, n_slots / 8)), (unsigned)n_slots);
+  k_batch_stats<OffT><<<grid, 256, 0, st>>>(off, n, slots, stats);
+}
+
+#define INST(OffT)                                                                                          \
+  template void launch_batch_clear<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
+  template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
+  template cudaError_t launch_batch_expand<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                \
+  template int batch_expand_grid<OffT>(int);                                                                \
+  template void launch_batch_stats<OffT>(const OffT*, int64_t, const WaveSlots*, int, long long*, int, cudaStream_t);
+INST(int32_t)
+INST(int64_t)
+#undef INST
+
+}  // namespace gbfs

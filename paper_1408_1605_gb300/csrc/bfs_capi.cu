@@ -25,6 +25,8 @@ bfs_status fail(bfs_status s, const std::string& msg) {
   return s;
 }
 
+void clear_last_error() { t_last_error.clear(); }
+
 bfs_status cuda_fail(cudaError_t e, const char* what) {
   cudaGetLastError();  // clear a sticky-free error so later calls are not affected
   return fail(e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA,

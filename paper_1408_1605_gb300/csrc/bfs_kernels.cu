@@ -26,21 +26,13 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "device_util.cuh"
 #include "kernels.h"
 
 namespace gbfs {
 
 // ---------------------------------------------------------------------------------------
 // Frontier construction helpers
-
-// Writes chunk[c] = k for every chunk start c * kChunk inside [cum, cum + deg).
-template <typename OffT>
-__device__ __forceinline__ void write_chunks(int32_t* chunk, OffT cum, OffT deg, int32_t k) {
-  if (deg <= 0) return;
-  OffT c = (cum + kChunk - 1) / kChunk;
-  const OffT end = cum + deg;
-  for (; c * kChunk < end; ++c) chunk[c] = k;
-}
 
 template <typename OffT>
 __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t root, int32_t* levels,
@@ -88,25 +80,6 @@ __device__ __forceinline__ OffT frontier_degree(const OffT* off, int64_t n, int3
     return 0;
   }
   return off[v + 1] - off[v];
-}
-
-template <typename OffT>
-__device__ OffT block_exclusive_scan(OffT x, OffT* s_warp, OffT* total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  OffT inc = warp_inclusive_scan(x);
-  if (lane == 31) s_warp[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    OffT t = lane < nw ? s_warp[lane] : 0;
-    OffT ti = warp_inclusive_scan(t);
-    if (lane < nw) s_warp[lane] = ti - t;
-    if (lane == nw - 1) s_warp[32] = ti;
-  }
-  __syncthreads();
-  OffT ex = s_warp[w] + inc - x;
-  *total = s_warp[32];
-  __syncthreads();
-  return ex;
 }
 
 template <typename OffT>

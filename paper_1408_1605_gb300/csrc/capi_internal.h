@@ -17,6 +17,7 @@ struct BatchState;  // multi-source work buffers, see bfs_batch.cu
 constexpr int kDefaultShape = 0;
 
 bfs_status fail(bfs_status s, const std::string& msg);
+void clear_last_error();
 bfs_status cuda_fail(cudaError_t e, const char* what);
 
 void launch_write_count(Ctl* ctl, Packed pk, int64_t* out, cudaStream_t st);

@@ -1,0 +1,39 @@
+// Device helpers shared by the single-source and multi-source kernels.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gbfs {
+
+// Writes chunk[c] = k for every chunk start c * kChunk inside [cum, cum + deg).
+template <typename OffT>
+__device__ __forceinline__ void write_chunks(int32_t* chunk, OffT cum, OffT deg, int32_t k) {
+  if (deg <= 0) return;
+  OffT c = (cum + kChunk - 1) / kChunk;
+  const OffT end = cum + deg;
+  for (; c * kChunk < end; ++c) chunk[c] = k;
+}
+
+// Exclusive scan of one value per thread across the block; *total receives the sum.
+// s_warp needs 33 entries. Every thread of the block must call it.
+template <typename OffT>
+__device__ __forceinline__ OffT block_exclusive_scan(OffT x, OffT* s_warp, OffT* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  OffT inc = warp_inclusive_scan(x);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    OffT t = lane < nw ? s_warp[lane] : 0;
+    OffT ti = warp_inclusive_scan(t);
+    if (lane < nw) s_warp[lane] = ti - t;
+    if (lane == nw - 1) s_warp[32] = ti;
+  }
+  __syncthreads();
+  OffT ex = s_warp[w] + inc - x;
+  *total = s_warp[32];
+  __syncthreads();
+  return ex;
+}
+
+}  // namespace gbfs

@@ -1,0 +1,150 @@
+"""Parity of the multi-source (batched) search with the oracle: every root's slice of a
+64-root wave has exactly the single-source levels, valid parents, and the oracle's m_c."""
+import os
+
+import numpy as np
+import pytest
+
+from _graphs import binary_tree_edges, load_golden, path_edges
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1408_1605_gb300 import _build
+
+    _build.build_bfs()
+    return torch
+
+
+def _upload(capi, g, force64=False, host_loop=False):
+    env = {"GBFS_FORCE_OFF64": "1" if force64 else "0", "GBFS_HOST_LOOP": "1" if host_loop else "0"}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def check_wave(capi, oracle, torch, h, g, roots, host_out=False):
+    roots = np.asarray(roots, dtype=np.int32)
+    k = roots.size
+    if host_out:
+        lv = np.empty((k, g.n), dtype=np.int32)
+        pr = np.empty((k, g.n), dtype=np.int32)
+        st = capi.bfs_run_batch(h, roots, lv, pr, want_stats=True)
+    else:
+        dl = torch.empty((k, g.n), dtype=torch.int32, device="cuda")
+        dp = torch.empty((k, g.n), dtype=torch.int32, device="cuda")
+        st = capi.bfs_run_batch(h, roots, dl, dp, want_stats=True)
+        lv, pr = dl.cpu().numpy(), dp.cpu().numpy()
+    for b, r in enumerate(roots.tolist()):
+        ref, _ = oracle.bfs(g.offsets, g.cols, r)
+        assert np.array_equal(lv[b], ref), f"root slot {b} ({r}): levels differ at {np.flatnonzero(lv[b] != ref)[:8]}"
+        code, bad = oracle.check_tree(g.offsets, g.cols, r, ref, lv[b], pr[b])
+        assert code == 0, (b, r, oracle.TREE_CODES[code], bad)
+        assert st[b].edges_traversed == oracle.component_edges(g.offsets, ref)
+        assert st[b].vertices_reached == int((ref >= 0).sum())
+        assert st[b].depth == int(ref.max()) + 1
+    return st
+
+
+@pytest.mark.parametrize("force64", [False, True])
+def test_rmat16_wave_of_64(torch_cuda, oracle_mod, graphs_mod, force64):
+    from paper_1408_1605_gb300 import capi
+
+    g = graphs_mod.rmat(16, 16, seed=graphs_mod.GRAPH_SEED_BASE)
+    roots = graphs_mod.pick_roots(g, 64, 11)
+    h = _upload(capi, g, force64)
+    try:
+        check_wave(capi, oracle_mod, torch_cuda, h, g, roots)
+        check_wave(capi, oracle_mod, torch_cuda, h, g, roots[:17])  # ragged wave, reused buffers
+    finally:
+        capi.bfs_graph_destroy(h)
+
+
+def test_wave_sizes_duplicates_components(torch_cuda, oracle_mod, graphs_mod):
+    from paper_1408_1605_gb300 import capi
+
+    fx = load_golden("two_components.txt")
+    g = graphs_mod.from_edges(fx["n"], fx["src"], fx["dst"])
+    h = _upload(capi, g)
+    try:
+        check_wave(capi, oracle_mod, torch_cuda, h, g, [0])
+        check_wave(capi, oracle_mod, torch_cuda, h, g, list(range(12)))  # every vertex, isolated 11 too
+        check_wave(capi, oracle_mod, torch_cuda, h, g, [3, 3, 8, 11, 3, 0])  # repeats
+        check_wave(capi, oracle_mod, torch_cuda, h, g, [5] * 64)
+    finally:
+        capi.bfs_graph_destroy(h)
+
+
+def test_grid_tree_path_waves(torch_cuda, oracle_mod, graphs_mod):
+    from paper_1408_1605_gb300 import capi
+
+    rng = np.random.default_rng(3)
+    for g in (graphs_mod.grid3d(21, 17, 13), graphs_mod.from_edges(2047, *binary_tree_edges(2047)),
+              graphs_mod.from_edges(3000, *path_edges(3000))):
+        h = _upload(capi, g)
+        try:
+            check_wave(capi, oracle_mod, torch_cuda, h, g, rng.integers(0, g.n, 64))
+        finally:
+            capi.bfs_graph_destroy(h)
+
+
+def test_host_loop_and_host_outputs(torch_cuda, oracle_mod, graphs_mod):
+    from paper_1408_1605_gb300 import capi
+
+    g = graphs_mod.rmat(14, 16, seed=31)
+    roots = graphs_mod.pick_roots(g, 40, 2)
+    for host_loop in (False, True):
+        h = _upload(capi, g, host_loop=host_loop)
+        try:
+            check_wave(capi, oracle_mod, torch_cuda, h, g, roots, host_out=True)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, roots[:9], host_out=False)
+        finally:
+            capi.bfs_graph_destroy(h)
+
+
+def test_batch_matches_single_source(torch_cuda, oracle_mod, graphs_mod):
+    """A root alone (bfs_run) and inside a wave give identical levels."""
+    from paper_1408_1605_gb300 import capi
+
+    torch = torch_cuda
+    g = graphs_mod.rmat(18, 16, seed=77)
+    roots = graphs_mod.pick_roots(g, 64, 5)
+    h = _upload(capi, g)
+    try:
+        dl = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+        dp = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+        capi.bfs_run_batch(h, roots, dl, dp)
+        sl = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        sp = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for b in (0, 31, 63):
+            capi.bfs_run(h, int(roots[b]), sl, sp)
+            assert torch.equal(sl, dl[b])
+    finally:
+        capi.bfs_graph_destroy(h)
+
+
+def test_batch_errors(torch_cuda, graphs_mod):
+    from paper_1408_1605_gb300 import capi
+
+    g = graphs_mod.rmat(10, 8, seed=1)
+    h = _upload(capi, g)
+    out = torch_cuda.empty((65, g.n), dtype=torch_cuda.int32, device="cuda")
+    try:
+        for roots in ([], list(range(65)), [0, g.n], [-1]):
+            with pytest.raises(capi.BfsError) as e:
+                capi.bfs_run_batch(h, np.array(roots, dtype=np.int32), out, out)
+            assert e.value.status == 1
+    finally:
+        capi.bfs_graph_destroy(h)
