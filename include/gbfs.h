@@ -160,6 +160,82 @@ GBFS_API bfs_status bfs_run_noalloc(const int32_t *row_offsets, const int32_t *c
                                     int64_t n_entries, int32_t root, int32_t *levels, int32_t *parents,
                                     void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: BFS queries on resident graphs with continuous batching. The paper has no
+ * serving layer; every query runs as one bit-slot of a multi-source wave (see
+ * bfs_run_batch) on its graph, and its result is identical to the same query run alone
+ * (levels equal; parents a valid BFS tree).
+ *   - Each added graph gets a wave of up to max_wave slots and its own CUDA stream; one
+ *     scheduler thread runs every active wave one level at a time, so the waves of
+ *     different graphs overlap on the device.
+ *   - Between two levels, finished queries retire (their bit left every frontier) and
+ *     pending queries are admitted into free slots in arrival order per graph, starting
+ *     from their root at the current wave level; a wave is never restarted for admission.
+ *   - Admission is gated by memory_cap_bytes: the graphs' wave state plus, for each
+ *     running query whose outputs are host memory, a device staging buffer of 8 bytes
+ *     per vertex. A query waits in the queue until a slot and the memory are free.
+ * --------------------------------------------------------------------------------------- */
+typedef struct bfs_server_s *bfs_server_t;
+
+typedef struct bfs_serve_config {
+  uint64_t memory_cap_bytes; /* device memory budget (0 = unlimited) */
+  int32_t max_wave;          /* slots per graph wave, 1..64 (0 = 64) */
+  int32_t queue_capacity;    /* pending queries before submit returns BFS_ERR_BUSY (0 = 2^20) */
+} bfs_serve_config;
+
+typedef struct bfs_serve_report {
+  uint64_t submitted, completed, cancelled, rejected, failed;
+  uint64_t levels;             /* wave levels run, all graphs */
+  int64_t edges_traversed;     /* sum of m_c over completed queries */
+  double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms; /* submit -> done */
+  double wall_s;               /* first submission -> last completion */
+  double gteps;                /* edges_traversed / wall_s / 1e9 */
+  int32_t max_concurrent;      /* most queries running at once */
+  int32_t reserved;
+  uint64_t peak_memory_bytes;  /* wave state + staging, at most memory_cap_bytes */
+} bfs_serve_report;
+
+/* Creates a server (no graphs yet). cfg may be NULL for defaults. Failures:
+ * BFS_ERR_INVALID_ARG (max_wave outside [0, 64]), BFS_ERR_OOM. */
+GBFS_API bfs_status bfs_serve_create(const bfs_serve_config *cfg, bfs_server_t *out);
+
+/* Makes a graph resident in the server and allocates its wave state (about 44 bytes per
+ * vertex). The graph handle must outlive the server. Graphs are added before the first
+ * submission, all on one device. Failures: BFS_ERR_INVALID_ARG, BFS_ERR_BUSY (already
+ * serving), BFS_ERR_OOM (memory budget or device memory), BFS_ERR_CUDA. */
+GBFS_API bfs_status bfs_serve_add_graph(bfs_server_t srv, bfs_graph_t g, int *graph_id);
+
+/* Queues one query: BFS from `root` on graph `graph_id`. levels / parents:
+ * int32[n_vertices] each, caller-owned, device or host memory (detected), written when the
+ * query completes and not touched after bfs_serve_wait / bfs_serve_poll report it done.
+ * Non-blocking. Failures: BFS_ERR_INVALID_ARG, BFS_ERR_NOT_FOUND (graph id),
+ * BFS_ERR_BUSY (queue full: retry later), BFS_ERR_CANCELLED (server shutting down). */
+GBFS_API bfs_status bfs_serve_submit(bfs_server_t srv, int graph_id, int32_t root, int32_t *levels,
+                                     int32_t *parents, uint64_t *ticket);
+
+/* *done = 1 once the query has completed, failed or been cancelled. */
+GBFS_API bfs_status bfs_serve_poll(bfs_server_t srv, uint64_t ticket, int *done);
+
+/* Blocks until the query is done or timeout_ms passes (BFS_ERR_TIMEOUT). Returns the
+ * query's own status once done (BFS_OK, BFS_ERR_CANCELLED, BFS_ERR_CUDA ...). */
+GBFS_API bfs_status bfs_serve_wait(bfs_server_t srv, uint64_t ticket, int timeout_ms);
+
+/* Requests cancellation: a pending query is dropped; a running one stops at the next level
+ * boundary (no output writes after it is reported done). */
+GBFS_API bfs_status bfs_serve_cancel(bfs_server_t srv, uint64_t ticket);
+
+/* Statistics of a completed query (depth, vertices reached, m_c; device_ms = time from
+ * admission to completion) and release of its ticket. Returns the query's status;
+ * BFS_ERR_BUSY if it is not done yet. */
+GBFS_API bfs_status bfs_serve_result(bfs_server_t srv, uint64_t ticket, bfs_stats *stats);
+
+/* Latency percentiles, throughput and counters since creation. */
+GBFS_API bfs_status bfs_serve_stats(bfs_server_t srv, bfs_serve_report *report);
+
+/* Stops the scheduler (pending queries are cancelled, running ones finish) and frees the
+ * server's device memory. NULL is accepted. */
+GBFS_API bfs_status bfs_serve_destroy(bfs_server_t srv);
+
 /* Message for the last failing call on this thread ("" if none). */
 GBFS_API const char *bfs_last_error(void);
 

@@ -35,6 +35,23 @@ class BfsError(RuntimeError):
         self.status = status
 
 
+class bfs_serve_config(ctypes.Structure):
+    _fields_ = [("memory_cap_bytes", ctypes.c_uint64), ("max_wave", ctypes.c_int32), ("queue_capacity", ctypes.c_int32)]
+
+
+class bfs_serve_report(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("edges_traversed", ctypes.c_int64), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("latency_mean_ms", ctypes.c_double),
+                ("latency_max_ms", ctypes.c_double), ("wall_s", ctypes.c_double), ("gteps", ctypes.c_double),
+                ("max_concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("peak_memory_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class bfs_stats(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("reserved", ctypes.c_int32), ("vertices_reached", ctypes.c_int64),
                 ("edges_traversed", ctypes.c_int64), ("device_ms", ctypes.c_double), ("expand_ms", ctypes.c_double)]
@@ -70,6 +87,15 @@ def lib():
             "bfs_expand": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P],
             "bfs_run_noalloc": [_P, _P, i64, i64, i32, _P, _P, _P],
             "bfs_run_batch": [_P, _P, ctypes.c_int, _P, _P, _P, _P],
+            "bfs_serve_create": [ctypes.POINTER(bfs_serve_config), ctypes.POINTER(_P)],
+            "bfs_serve_add_graph": [_P, _P, ctypes.POINTER(ctypes.c_int)],
+            "bfs_serve_submit": [_P, ctypes.c_int, i32, _P, _P, ctypes.POINTER(ctypes.c_uint64)],
+            "bfs_serve_poll": [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
+            "bfs_serve_wait": [_P, ctypes.c_uint64, ctypes.c_int],
+            "bfs_serve_cancel": [_P, ctypes.c_uint64],
+            "bfs_serve_result": [_P, ctypes.c_uint64, ctypes.POINTER(bfs_stats)],
+            "bfs_serve_stats": [_P, ctypes.POINTER(bfs_serve_report)],
+            "bfs_serve_destroy": [_P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -164,6 +190,55 @@ def bfs_run_noalloc(row_offsets, cols, n_vertices: int, n_entries: int, root: in
                     stream=None) -> None:
     check(lib().bfs_run_noalloc(ptr(row_offsets), ptr(cols), int(n_vertices), int(n_entries), int(root),
                                 ptr(levels), ptr(parents), stream_handle(stream)))
+
+
+def bfs_serve_create(memory_cap_bytes: int = 0, max_wave: int = 0, queue_capacity: int = 0) -> int:
+    cfg = bfs_serve_config(int(memory_cap_bytes), int(max_wave), int(queue_capacity))
+    out = _P()
+    check(lib().bfs_serve_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def bfs_serve_add_graph(server: int, graph: int) -> int:
+    gid = ctypes.c_int()
+    check(lib().bfs_serve_add_graph(server, graph, ctypes.byref(gid)))
+    return gid.value
+
+
+def bfs_serve_submit(server: int, graph_id: int, root: int, levels, parents) -> int:
+    t = ctypes.c_uint64()
+    check(lib().bfs_serve_submit(server, int(graph_id), int(root), ptr(levels), ptr(parents), ctypes.byref(t)))
+    return t.value
+
+
+def bfs_serve_poll(server: int, ticket: int) -> bool:
+    d = ctypes.c_int()
+    check(lib().bfs_serve_poll(server, int(ticket), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def bfs_serve_wait(server: int, ticket: int, timeout_ms: int = 60000) -> None:
+    check(lib().bfs_serve_wait(server, int(ticket), int(timeout_ms)))
+
+
+def bfs_serve_cancel(server: int, ticket: int) -> None:
+    check(lib().bfs_serve_cancel(server, int(ticket)))
+
+
+def bfs_serve_result(server: int, ticket: int) -> bfs_stats:
+    st = bfs_stats()
+    check(lib().bfs_serve_result(server, int(ticket), ctypes.byref(st)))
+    return st
+
+
+def bfs_serve_stats(server: int) -> dict:
+    rep = bfs_serve_report()
+    check(lib().bfs_serve_stats(server, ctypes.byref(rep)))
+    return rep.as_dict()
+
+
+def bfs_serve_destroy(server: int) -> None:
+    check(lib().bfs_serve_destroy(server))
 
 
 def bfs_last_error() -> str:

@@ -71,6 +71,39 @@ struct RootSeed {
 };
 
 template <typename OffT>
+BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
+  BatchArgs<OffT> a{};
+  a.off = reinterpret_cast<const OffT*>(g.off);
+  a.cols = g.cols;
+  a.n = g.n;
+  a.visited = b.visited;
+  for (int i = 0; i < 3; ++i) {
+    a.fmask[i] = b.fmask[i];
+    a.qv[i] = b.qv[i];
+  }
+  for (int i = 0; i < 2; ++i) {
+    a.cum[i] = reinterpret_cast<OffT*>(b.cum[i]);
+    a.base[i] = reinterpret_cast<OffT*>(b.base[i]);
+    a.chunk[i] = b.chunk[i];
+  }
+  a.ctl = b.ctl;
+  a.slots = b.slots;
+  a.pk = g.pk;
+  a.use_cond = 0;
+  return a;
+}
+
+// Statistics of one output array: out[0] = degree sum of reached vertices (2 m_c),
+// out[1] = reached count, out[2] = max level + 1.
+template <typename OffT>
+void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long long* out, int num_sms,
+                        cudaStream_t st);
+
+cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b);
+void free_batch_bufs(BatchBufs& b);
+size_t batch_bufs_bytes(const GraphDev& g);
+
+template <typename OffT>
 void launch_batch_clear(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int n_seeds, int wave_level,

@@ -29,22 +29,15 @@ struct BatchState {
   int stage_roots = 0;
 };
 
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_batch_bufs(BatchBufs& b);
+
 static void free_batch(BatchState* S) {
-  BatchBufs& b = S->b;
-  cudaFree(b.visited);
-  for (int i = 0; i < 3; ++i) {
-    cudaFree(b.fmask[i]);
-    cudaFree(b.qv[i]);
-  }
-  for (int i = 0; i < 2; ++i) {
-    cudaFree(b.cum[i]);
-    cudaFree(b.base[i]);
-    cudaFree(b.chunk[i]);
-  }
-  cudaFree(b.ctl);
-  cudaFree(b.slots);
-  cudaFree(b.stats);
-  cudaFree(b.roots_dev);
+  free_batch_bufs(S->b);
   cudaFree(S->stage_lvl);
   cudaFree(S->stage_par);
   if (S->exec) cudaGraphExecDestroy(S->exec);
@@ -64,18 +57,32 @@ void destroy_batch_state(bfs_graph_s* G) {
   }
 }
 
-template <typename T>
-static cudaError_t dalloc(T** p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+
+void free_batch_bufs(BatchBufs& b) {
+  cudaFree(b.visited);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(b.fmask[i]);
+    cudaFree(b.qv[i]);
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(b.cum[i]);
+    cudaFree(b.base[i]);
+    cudaFree(b.chunk[i]);
+  }
+  cudaFree(b.ctl);
+  cudaFree(b.slots);
+  cudaFree(b.stats);
+  cudaFree(b.roots_dev);
+  b = BatchBufs{};
 }
 
-bfs_status ensure_batch_state(bfs_graph_s* G) {
-  if (G->batch && G->batch->b.ready) return BFS_OK;
-  auto* S = new (std::nothrow) BatchState();
-  if (!S) return fail(BFS_ERR_OOM, "host allocation");
-  const GraphDev& g = G->g;
+size_t batch_bufs_bytes(const GraphDev& g) {
   const size_t osz = g.off64 ? 8 : 4;
-  BatchBufs& b = S->b;
+  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz) + 2 * 4 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
+}
+
+cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b) {
+  const size_t osz = g.off64 ? 8 : 4;
   b.chunk_cap = g.nnz / kChunk + 2;
   cudaError_t e = dalloc(&b.visited, (size_t)g.n);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
@@ -91,46 +98,39 @@ bfs_status ensure_batch_state(bfs_graph_s* G) {
   if (e == cudaSuccess) e = dalloc(&b.slots, 1);
   if (e == cudaSuccess) e = dalloc(&b.stats, 3 * kMaxWave);
   if (e == cudaSuccess) e = dalloc(&b.roots_dev, 4 * kMaxWave);
+  if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
+  if (e != cudaSuccess) {
+    free_batch_bufs(b);
+    return e;
+  }
+  b.ready = true;
+  return cudaSuccess;
+}
+
+bfs_status ensure_batch_state(bfs_graph_s* G) {
+  if (G->batch && G->batch->b.ready) return BFS_OK;
+  auto* S = new (std::nothrow) BatchState();
+  if (!S) return fail(BFS_ERR_OOM, "host allocation");
+  const GraphDev& g = G->g;
+  cudaError_t e = alloc_batch_bufs(g, S->b);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev_mid);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->ctl_host), sizeof(BatchCtl), 0);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&S->stats_host), sizeof(long long) * 3 * kMaxWave, 0);
-  if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
   if (e != cudaSuccess) {
     free_batch(S);
     delete S;
     return cuda_fail(e, "batch work buffers");
   }
   S->grid = g.off64 ? batch_expand_grid<int64_t>(g.num_sms) : batch_expand_grid<int32_t>(g.num_sms);
-  b.ready = true;
   G->batch = S;
   return BFS_OK;
 }
 
 template <typename OffT>
 BatchArgs<OffT> batch_args(const bfs_graph_s* G) {
-  const GraphDev& g = G->g;
-  const BatchBufs& b = G->batch->b;
-  BatchArgs<OffT> a{};
-  a.off = reinterpret_cast<const OffT*>(g.off);
-  a.cols = g.cols;
-  a.n = g.n;
-  a.visited = b.visited;
-  for (int i = 0; i < 3; ++i) {
-    a.fmask[i] = b.fmask[i];
-    a.qv[i] = b.qv[i];
-  }
-  for (int i = 0; i < 2; ++i) {
-    a.cum[i] = reinterpret_cast<OffT*>(b.cum[i]);
-    a.base[i] = reinterpret_cast<OffT*>(b.base[i]);
-    a.chunk[i] = b.chunk[i];
-  }
-  a.ctl = b.ctl;
-  a.slots = b.slots;
-  a.pk = g.pk;
-  a.use_cond = 0;
-  return a;
+  return make_batch_args<OffT>(G->g, G->batch->b);
 }
 
 template BatchArgs<int32_t> batch_args<int32_t>(const bfs_graph_s*);

@@ -410,12 +410,58 @@ void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int 
   k_batch_stats<OffT><<<grid, 256, 0, st>>>(off, n, slots, stats);
 }
 
+template <typename OffT>
+__global__ void k_level_stats(const OffT* __restrict__ off, int64_t n, const int32_t* __restrict__ lv,
+                              long long* out) {
+  __shared__ long long s_red[3][32];
+  long long e2 = 0, reached = 0, depth = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = lv[v];
+    if (l >= 0) {
+      e2 += (long long)(off[v + 1] - off[v]);
+      ++reached;
+      depth = max(depth, (long long)l + 1);
+    }
+  }
+  for (int d = 16; d; d >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, d);
+    reached += __shfl_xor_sync(0xffffffffu, reached, d);
+    depth = max(depth, __shfl_xor_sync(0xffffffffu, depth, d));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][w] = e2;
+    s_red[1][w] = reached;
+    s_red[2][w] = depth;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long a0 = 0, a1 = 0, a2 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a0 += s_red[0][i];
+      a1 += s_red[1][i];
+      a2 = max(a2, s_red[2][i]);
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&out[0]), (unsigned long long)a0);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&out[1]), (unsigned long long)a1);
+    atomicMax(&out[2], a2);
+  }
+}
+
+template <typename OffT>
+void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long long* out, int num_sms,
+                        cudaStream_t st) {
+  cudaMemsetAsync(out, 0, sizeof(long long) * 3, st);
+  k_level_stats<OffT><<<num_sms * 2, 256, 0, st>>>(off, n, levels, out);
+}
+
 #define INST(OffT)                                                                                          \
   template void launch_batch_clear<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
   template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
   template cudaError_t launch_batch_expand<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                \
   template int batch_expand_grid<OffT>(int);                                                                \
-  template void launch_batch_stats<OffT>(const OffT*, int64_t, const WaveSlots*, int, long long*, int, cudaStream_t);
+  template void launch_batch_stats<OffT>(const OffT*, int64_t, const WaveSlots*, int, long long*, int, cudaStream_t); \
+  template void launch_level_stats<OffT>(const OffT*, int64_t, const int32_t*, long long*, int, cudaStream_t);
 INST(int32_t)
 INST(int64_t)
 #undef INST

@@ -1,0 +1,598 @@
+// Serving loop: BFS queries on resident graphs with continuous batching.
+//
+// Each graph added to a server gets its own wave (multi-source state with 64 bit-slots,
+// see bfs_batch_kernels.cu) and its own CUDA stream. A scheduler thread runs the waves one
+// level at a time, all waves launched before any is waited on, so the waves of different
+// graphs overlap on the device. Between two levels it
+//   * retires slots whose bit left every frontier (the query is complete: its outputs are
+//     final), copying results to host buffers where the caller gave host memory;
+//   * admits pending queries into free slots, in arrival order per graph, as long as the
+//     device-memory budget allows (a query with host outputs needs a device staging buffer
+//     of 8 bytes per vertex, charged to the budget until it completes). A query admitted at
+//     wave level t starts from its root at that level, so admission never restarts a wave;
+//     its levels are the wave level minus t, which makes each result identical to the
+//     same query run alone.
+// The paper has no serving layer; each query's search is Algorithm 2 / Algorithm 3 with
+// R = C = 1, run as one bit of a multi-source wave.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "batch.h"
+#include "capi_internal.h"
+#include "gbfs.h"
+
+namespace gbfs {
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { kPending = 0, kRunning = 1, kDone = 2 };
+
+struct ServeReq {
+  uint64_t ticket = 0;
+  int graph_id = 0;
+  int32_t root = 0;
+  int32_t* user_lvl = nullptr;
+  int32_t* user_par = nullptr;
+  bool host_out = false;
+  int32_t* dev_lvl = nullptr;  // where the kernels write
+  int32_t* dev_par = nullptr;
+  size_t charged = 0;
+  int slot = -1;
+  int start = 0;               // wave frontier index at admission
+  int state = kPending;
+  bool cancel = false;
+  bfs_status status = BFS_OK;
+  std::string message;
+  bfs_stats stats{};
+  Clock::time_point t_submit, t_admit, t_done;
+};
+
+struct Wave {
+  bfs_graph_s* G = nullptr;
+  GraphDev g;
+  BatchBufs b;
+  cudaStream_t stream = nullptr;
+  int grid = 0;
+  bool active = false;
+  int t = 0;                          // frontier index the next expansion reads
+  uint64_t used = 0;                  // occupied slot bits
+  ServeReq* slot_req[kMaxWave] = {};
+  std::deque<ServeReq*> pending;
+  WaveSlots* slots_host = nullptr;    // pinned
+  BatchCtl* ctl_host = nullptr;       // pinned
+  RootSeed* seeds_host = nullptr;     // pinned
+  long long* stats_host = nullptr;    // pinned, 3 per slot
+  long long* stats_dev = nullptr;     // device, 3 per slot
+  unsigned long long pending_clear = 0;  // bits to clear from V before reuse
+};
+
+}  // namespace gbfs
+
+struct bfs_server_s {
+  bfs_serve_config cfg{};
+  int device = -1;
+  std::vector<gbfs::Wave*> waves;
+  std::map<uint64_t, gbfs::ServeReq*> reqs;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread th;
+  bool stop = false;
+  bool started = false;
+  uint64_t next_ticket = 1;
+  size_t mem_used = 0, mem_peak = 0, mem_fixed = 0;
+  // report
+  uint64_t submitted = 0, completed = 0, cancelled = 0, rejected = 0, failed = 0, levels = 0;
+  int running = 0, max_running = 0;
+  std::vector<double> latencies_ms;
+  long long edges_done = 0;
+  bool have_first = false;
+  gbfs::Clock::time_point first_submit, last_done;
+  std::string fatal;
+};
+
+namespace gbfs {
+
+static void free_wave(Wave* w) {
+  if (!w) return;
+  free_batch_bufs(w->b);
+  if (w->stream) cudaStreamDestroy(w->stream);
+  if (w->slots_host) cudaFreeHost(w->slots_host);
+  if (w->ctl_host) cudaFreeHost(w->ctl_host);
+  if (w->seeds_host) cudaFreeHost(w->seeds_host);
+  if (w->stats_host) cudaFreeHost(w->stats_host);
+  cudaFree(w->stats_dev);
+  delete w;
+}
+
+template <typename OffT>
+static void wave_launch_level(Wave* w) {
+  BatchArgs<OffT> a = make_batch_args<OffT>(w->g, w->b);
+  launch_batch_expand<OffT>(a, w->grid, w->stream);
+}
+
+template <typename OffT>
+static void wave_seed(Wave* w, int n_seeds, bool fresh) {
+  BatchArgs<OffT> a = make_batch_args<OffT>(w->g, w->b);
+  if (fresh) launch_batch_clear<OffT>(a, w->g.num_sms, w->stream);
+  launch_batch_seed<OffT>(a, reinterpret_cast<const RootSeed*>(w->b.roots_dev), n_seeds, 0, fresh, w->stream);
+}
+
+static void finish_req(bfs_server_s* S, ServeReq* r, bfs_status st, const std::string& msg) {
+  // called with S->mu held
+  r->status = st;
+  r->message = msg;
+  r->state = kDone;
+  r->t_done = Clock::now();
+  if (r->charged) {
+    cudaFree(r->dev_lvl);
+    cudaFree(r->dev_par);
+    S->mem_used -= r->charged;
+    r->charged = 0;
+  }
+  if (st == BFS_OK) {
+    ++S->completed;
+    S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    S->edges_done += r->stats.edges_traversed;
+    S->last_done = r->t_done;
+  } else if (st == BFS_ERR_CANCELLED) {
+    ++S->cancelled;
+  } else {
+    ++S->failed;
+  }
+}
+
+// One scheduler round: admission, seeding, one level of every active wave, retirement.
+static void scheduler_round(bfs_server_s* S) {
+  struct Admit {
+    Wave* w;
+    std::vector<ServeReq*> reqs;
+  };
+  std::vector<Admit> admits;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (Wave* w : S->waves) {
+      // pending cancellations
+      for (auto it = w->pending.begin(); it != w->pending.end();) {
+        if ((*it)->cancel) {
+          finish_req(S, *it, BFS_ERR_CANCELLED, "cancelled before admission");
+          it = w->pending.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      Admit ad{w, {}};
+      const int cap_slots = std::max(1, std::min(kMaxWave, S->cfg.max_wave > 0 ? S->cfg.max_wave : kMaxWave));
+      while (!w->pending.empty()) {
+        int free_bit = -1;
+        for (int b = 0; b < cap_slots; ++b)
+          if (!((w->used >> b) & 1ull)) {
+            free_bit = b;
+            break;
+          }
+        if (free_bit < 0) break;
+        ServeReq* r = w->pending.front();
+        const size_t need = r->host_out ? (size_t)w->g.n * 8 : 0;
+        if (S->cfg.memory_cap_bytes && S->mem_fixed + S->mem_used + need > S->cfg.memory_cap_bytes)
+          break;  // FIFO: wait until running queries release memory
+        if (need) {
+          if (cudaMalloc(reinterpret_cast<void**>(&r->dev_lvl), (size_t)w->g.n * 4) != cudaSuccess ||
+              cudaMalloc(reinterpret_cast<void**>(&r->dev_par), (size_t)w->g.n * 4) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(r->dev_lvl);
+            r->dev_lvl = nullptr;
+            break;  // device memory is short: retry once slots complete
+          }
+          r->charged = need;
+          S->mem_used += need;
+          S->mem_peak = std::max(S->mem_peak, S->mem_used + S->mem_fixed);
+        } else {
+          r->dev_lvl = r->user_lvl;
+          r->dev_par = r->user_par;
+        }
+        w->pending.pop_front();
+        r->slot = free_bit;
+        r->start = w->active ? w->t : 0;
+        r->state = kRunning;
+        r->t_admit = Clock::now();
+        w->used |= 1ull << free_bit;
+        w->slot_req[free_bit] = r;
+        ad.reqs.push_back(r);
+        ++S->running;
+        S->max_running = std::max(S->max_running, S->running);
+      }
+      if (!ad.reqs.empty()) admits.push_back(ad);
+    }
+  }
+  // seeding (outside the lock; only this thread touches the waves' device state)
+  for (Admit& ad : admits) {
+    Wave* w = ad.w;
+    const bool fresh = !w->active;
+    if (fresh) {
+      w->t = 0;
+      for (ServeReq* r : ad.reqs) r->start = 0;
+    } else if (w->pending_clear) {
+      launch_clear_bits(w->b.visited, w->g.n, w->pending_clear, w->g.num_sms, w->stream);
+    }
+    w->pending_clear = 0;
+    std::map<int32_t, unsigned long long> masks;
+    for (ServeReq* r : ad.reqs) {
+      w->slots_host->lvl[r->slot] = r->dev_lvl;
+      w->slots_host->par[r->slot] = r->dev_par;
+      w->slots_host->start[r->slot] = r->start;
+      launch_fill(r->dev_lvl, w->g.n, -1, w->g.num_sms, w->stream);
+      launch_fill(r->dev_par, w->g.n, -1, w->g.num_sms, w->stream);
+      masks[r->root] |= 1ull << r->slot;
+    }
+    int ns = 0;
+    for (auto& kv : masks) w->seeds_host[ns++] = RootSeed{kv.first, kv.second};
+    cudaMemcpyAsync(w->b.slots, w->slots_host, sizeof(WaveSlots), cudaMemcpyHostToDevice, w->stream);
+    cudaMemcpyAsync(w->b.roots_dev, w->seeds_host, sizeof(RootSeed) * ns, cudaMemcpyHostToDevice, w->stream);
+    if (w->g.off64)
+      wave_seed<int64_t>(w, ns, fresh);
+    else
+      wave_seed<int32_t>(w, ns, fresh);
+    w->active = true;
+  }
+  // running-query cancellation: drop the bits at this boundary (no later writes)
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (Wave* w : S->waves) {
+      unsigned long long drop = 0;
+      for (int b = 0; b < kMaxWave; ++b) {
+        ServeReq* r = w->slot_req[b];
+        if (r && r->cancel && r->state == kRunning) drop |= 1ull << b;
+      }
+      if (drop && w->active) {
+        launch_clear_bits(w->b.fmask[w->t % 3], w->g.n, drop, w->g.num_sms, w->stream);
+        launch_clear_bits(w->b.visited, w->g.n, drop, w->g.num_sms, w->stream);
+        for (int b = 0; b < kMaxWave; ++b)
+          if ((drop >> b) & 1ull) {
+            cudaStreamSynchronize(w->stream);
+            finish_req(S, w->slot_req[b], BFS_ERR_CANCELLED, "cancelled while running");
+            w->slot_req[b] = nullptr;
+            w->used &= ~(1ull << b);
+            --S->running;
+          }
+      }
+    }
+  }
+  // one level of every active wave; launch all, then wait for all
+  for (Wave* w : S->waves) {
+    if (!w->active) continue;
+    if (w->g.off64)
+      wave_launch_level<int64_t>(w);
+    else
+      wave_launch_level<int32_t>(w);
+    cudaMemcpyAsync(w->ctl_host, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, w->stream);
+  }
+  for (Wave* w : S->waves) {
+    if (!w->active) continue;
+    cudaError_t e = cudaStreamSynchronize(w->stream);
+    std::vector<int> retire;
+    unsigned long long alive = 0;
+    if (e == cudaSuccess) {
+      const int t_expanded = w->t;
+      ++w->t;
+      alive = w->ctl_host->alive[w->t & 1];
+      for (int b = 0; b < kMaxWave; ++b) {
+        ServeReq* r = w->slot_req[b];
+        if (r && r->start <= t_expanded && !((alive >> b) & 1ull)) retire.push_back(b);
+      }
+      if (!w->ctl_host->cont) w->active = false;
+    }
+    // statistics and host copies of the retiring slots
+    if (e == cudaSuccess) {
+      for (int b : retire) {
+        ServeReq* r = w->slot_req[b];
+        if (w->g.off64)
+          launch_level_stats<int64_t>(reinterpret_cast<const int64_t*>(w->g.off), w->g.n, r->dev_lvl,
+                                      w->stats_dev + 3 * b, w->g.num_sms, w->stream);
+        else
+          launch_level_stats<int32_t>(reinterpret_cast<const int32_t*>(w->g.off), w->g.n, r->dev_lvl,
+                                      w->stats_dev + 3 * b, w->g.num_sms, w->stream);
+        cudaMemcpyAsync(w->stats_host + 3 * b, w->stats_dev + 3 * b, sizeof(long long) * 3, cudaMemcpyDeviceToHost,
+                        w->stream);
+        if (r->host_out) {
+          cudaMemcpyAsync(r->user_lvl, r->dev_lvl, (size_t)w->g.n * 4, cudaMemcpyDeviceToHost, w->stream);
+          cudaMemcpyAsync(r->user_par, r->dev_par, (size_t)w->g.n * 4, cudaMemcpyDeviceToHost, w->stream);
+        }
+      }
+      if (!retire.empty()) e = cudaStreamSynchronize(w->stream);
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    ++S->levels;
+    if (e != cudaSuccess) {
+      const std::string msg = std::string("CUDA error in serving wave: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      for (int b = 0; b < kMaxWave; ++b)
+        if (w->slot_req[b]) {
+          finish_req(S, w->slot_req[b], BFS_ERR_CUDA, msg);
+          w->slot_req[b] = nullptr;
+          --S->running;
+        }
+      w->used = 0;
+      w->active = false;
+      S->fatal = msg;
+      continue;
+    }
+    for (int b : retire) {
+      ServeReq* r = w->slot_req[b];
+      r->stats.edges_traversed = w->stats_host[3 * b + 0] / 2;
+      r->stats.vertices_reached = w->stats_host[3 * b + 1];
+      r->stats.depth = (int32_t)w->stats_host[3 * b + 2];
+      r->stats.device_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_admit).count();
+      r->stats.expand_ms = r->stats.device_ms;
+      finish_req(S, r, BFS_OK, "");
+      w->slot_req[b] = nullptr;
+      w->used &= ~(1ull << b);
+      w->pending_clear |= 1ull << b;
+      --S->running;
+    }
+    if (w->ctl_host->error & kErrColumnRange) S->fatal = "a column id outside [0, n) was met";
+  }
+  S->cv_done.notify_all();
+}
+
+static void scheduler_main(bfs_server_s* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      auto busy = [&] {
+        for (Wave* w : S->waves)
+          if (w->active || !w->pending.empty()) return true;
+        return false;
+      };
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || busy(); });
+      if (S->stop && !busy()) break;
+      if (!busy()) continue;
+      if (S->stop)  // drain: cancel what has not started
+        for (Wave* w : S->waves) {
+          for (ServeReq* r : w->pending) finish_req(S, r, BFS_ERR_CANCELLED, "server shutting down");
+          w->pending.clear();
+        }
+    }
+    scheduler_round(S);
+  }
+}
+
+}  // namespace gbfs
+
+using namespace gbfs;
+
+extern "C" {
+
+GBFS_API bfs_status bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
+  clear_last_error();
+  if (!out) return fail(BFS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  auto* S = new (std::nothrow) bfs_server_s();
+  if (!S) return fail(BFS_ERR_OOM, "host allocation");
+  if (cfg) S->cfg = *cfg;
+  if (S->cfg.max_wave < 0 || S->cfg.max_wave > kMaxWave) {
+    delete S;
+    return fail(BFS_ERR_INVALID_ARG, "max_wave outside [0, 64]");
+  }
+  if (S->cfg.queue_capacity <= 0) S->cfg.queue_capacity = 1 << 20;
+  *out = S;
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_add_graph(bfs_server_t S, bfs_graph_t G, int* graph_id) {
+  clear_last_error();
+  if (!S || !G || !graph_id) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->started) return fail(BFS_ERR_BUSY, "graphs must be added before the first submission");
+  if (S->device >= 0 && G->g.device != S->device) return fail(BFS_ERR_INVALID_ARG, "graphs must share one device");
+  cudaError_t e = cudaSetDevice(G->g.device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  const size_t need = batch_bufs_bytes(G->g);
+  if (S->cfg.memory_cap_bytes && S->mem_fixed + need > S->cfg.memory_cap_bytes)
+    return fail(BFS_ERR_OOM, "the graph's wave state exceeds the server's memory budget");
+  auto* w = new (std::nothrow) Wave();
+  if (!w) return fail(BFS_ERR_OOM, "host allocation");
+  w->G = G;
+  w->g = G->g;
+  e = alloc_batch_bufs(w->g, w->b);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->slots_host), sizeof(WaveSlots), 0);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->ctl_host), sizeof(BatchCtl), 0);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->seeds_host), sizeof(RootSeed) * kMaxWave, 0);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->stats_host), sizeof(long long) * 3 * kMaxWave, 0);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&w->stats_dev), sizeof(long long) * 3 * kMaxWave);
+  if (e != cudaSuccess) {
+    free_wave(w);
+    return cuda_fail(e, "wave state");
+  }
+  for (int b = 0; b < kMaxWave; ++b) {
+    w->slots_host->lvl[b] = w->slots_host->par[b] = nullptr;
+    w->slots_host->start[b] = 0;
+  }
+  w->grid = w->g.off64 ? batch_expand_grid<int64_t>(w->g.num_sms) : batch_expand_grid<int32_t>(w->g.num_sms);
+  S->device = G->g.device;
+  S->mem_fixed += need;
+  S->mem_peak = std::max(S->mem_peak, S->mem_fixed + S->mem_used);
+  *graph_id = (int)S->waves.size();
+  S->waves.push_back(w);
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_submit(bfs_server_t S, int graph_id, int32_t root, int32_t* levels, int32_t* parents,
+                                     uint64_t* ticket) {
+  clear_last_error();
+  if (!S || !levels || !parents || !ticket) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (graph_id < 0 || graph_id >= (int)S->waves.size()) return fail(BFS_ERR_NOT_FOUND, "unknown graph id");
+  Wave* w = S->waves[graph_id];
+  if (root < 0 || root >= w->g.n) return fail(BFS_ERR_INVALID_ARG, "root outside [0, n)");
+  if (S->stop) return fail(BFS_ERR_CANCELLED, "server shutting down");
+  size_t queued = 0;
+  for (Wave* x : S->waves) queued += x->pending.size();
+  if ((int64_t)queued >= S->cfg.queue_capacity) {
+    ++S->rejected;
+    return fail(BFS_ERR_BUSY, "request queue is full");
+  }
+  auto* r = new (std::nothrow) ServeReq();
+  if (!r) return fail(BFS_ERR_OOM, "host allocation");
+  cudaPointerAttributes at{};
+  const bool dev_l = cudaPointerGetAttributes(&at, levels) == cudaSuccess &&
+                     (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  const bool dev_p = cudaPointerGetAttributes(&at, parents) == cudaSuccess &&
+                     (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  r->ticket = S->next_ticket++;
+  r->graph_id = graph_id;
+  r->root = root;
+  r->user_lvl = levels;
+  r->user_par = parents;
+  r->host_out = !(dev_l && dev_p);
+  r->t_submit = Clock::now();
+  if (!S->have_first) {
+    S->have_first = true;
+    S->first_submit = r->t_submit;
+  }
+  ++S->submitted;
+  S->reqs[r->ticket] = r;
+  w->pending.push_back(r);
+  if (!S->started) {
+    S->started = true;
+    S->th = std::thread(scheduler_main, S);
+  }
+  *ticket = r->ticket;
+  S->cv_work.notify_one();
+  return BFS_OK;
+}
+
+static bfs_status req_status(bfs_server_s* S, uint64_t ticket, ServeReq** out) {
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(BFS_ERR_NOT_FOUND, "unknown ticket");
+  *out = it->second;
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_poll(bfs_server_t S, uint64_t ticket, int* done) {
+  clear_last_error();
+  if (!S || !done) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  ServeReq* r;
+  bfs_status s = req_status(S, ticket, &r);
+  if (s != BFS_OK) return s;
+  *done = r->state == kDone;
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_wait(bfs_server_t S, uint64_t ticket, int timeout_ms) {
+  clear_last_error();
+  if (!S) return fail(BFS_ERR_INVALID_ARG, "NULL server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  ServeReq* r;
+  bfs_status s = req_status(S, ticket, &r);
+  if (s != BFS_OK) return s;
+  const auto deadline = Clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
+  while (r->state != kDone) {
+    if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state != kDone)
+      return fail(BFS_ERR_TIMEOUT, "request not complete within the timeout");
+  }
+  if (r->status != BFS_OK) return fail(r->status, r->message);
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_cancel(bfs_server_t S, uint64_t ticket) {
+  clear_last_error();
+  if (!S) return fail(BFS_ERR_INVALID_ARG, "NULL server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  ServeReq* r;
+  bfs_status s = req_status(S, ticket, &r);
+  if (s != BFS_OK) return s;
+  if (r->state != kDone) {
+    r->cancel = true;
+    S->cv_work.notify_one();
+  }
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_result(bfs_server_t S, uint64_t ticket, bfs_stats* stats) {
+  clear_last_error();
+  if (!S) return fail(BFS_ERR_INVALID_ARG, "NULL server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  ServeReq* r;
+  bfs_status s = req_status(S, ticket, &r);
+  if (s != BFS_OK) return s;
+  if (r->state != kDone) return fail(BFS_ERR_BUSY, "request not complete");
+  if (stats) *stats = r->stats;
+  const bfs_status st = r->status;
+  const std::string msg = r->message;
+  S->reqs.erase(ticket);
+  delete r;
+  if (st != BFS_OK) return fail(st, msg);
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_stats(bfs_server_t S, bfs_serve_report* rep) {
+  clear_last_error();
+  if (!S || !rep) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  bfs_serve_report R{};
+  R.submitted = S->submitted;
+  R.completed = S->completed;
+  R.cancelled = S->cancelled;
+  R.rejected = S->rejected;
+  R.failed = S->failed;
+  R.levels = S->levels;
+  R.max_concurrent = S->max_running;
+  R.peak_memory_bytes = S->mem_peak;
+  std::vector<double> lat = S->latencies_ms;
+  std::sort(lat.begin(), lat.end());
+  auto pct = [&](double p) {
+    if (lat.empty()) return 0.0;
+    const size_t i = std::min(lat.size() - 1, (size_t)(p * (double)(lat.size() - 1) + 0.5));
+    return lat[i];
+  };
+  R.latency_p50_ms = pct(0.50);
+  R.latency_p99_ms = pct(0.99);
+  R.latency_max_ms = lat.empty() ? 0.0 : lat.back();
+  double sum = 0;
+  for (double x : lat) sum += x;
+  R.latency_mean_ms = lat.empty() ? 0.0 : sum / (double)lat.size();
+  if (S->have_first && S->completed) {
+    R.wall_s = std::chrono::duration<double>(S->last_done - S->first_submit).count();
+    R.gteps = R.wall_s > 0 ? (double)S->edges_done / R.wall_s / 1e9 : 0.0;
+  }
+  R.edges_traversed = S->edges_done;
+  *rep = R;
+  if (!S->fatal.empty()) return fail(BFS_ERR_CUDA, S->fatal);
+  return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_serve_destroy(bfs_server_t S) {
+  if (!S) return BFS_OK;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv_work.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  if (S->device >= 0) cudaSetDevice(S->device);
+  for (Wave* w : S->waves) free_wave(w);
+  for (auto& kv : S->reqs) {
+    if (kv.second->charged) {
+      cudaFree(kv.second->dev_lvl);
+      cudaFree(kv.second->dev_par);
+    }
+    delete kv.second;
+  }
+  delete S;
+  return BFS_OK;
+}
+
+}  // extern "C"

@@ -78,3 +78,24 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(capi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         capi.lib()
+
+
+def test_serve_host_side_checks(capi):
+    """Server creation, lookups and reports need no GPU."""
+    with pytest.raises(capi.BfsError) as e:
+        capi.bfs_serve_create(max_wave=65)
+    assert e.value.status == 1
+    srv = capi.bfs_serve_create(memory_cap_bytes=1 << 20, max_wave=8, queue_capacity=4)
+    try:
+        buf = np.zeros(4, dtype=np.int32)
+        with pytest.raises(capi.BfsError) as e:
+            capi.bfs_serve_submit(srv, 0, 0, buf, buf)
+        assert e.value.status == 8
+        with pytest.raises(capi.BfsError) as e:
+            capi.bfs_serve_wait(srv, 1, 0)
+        assert e.value.status == 8
+        rep = capi.bfs_serve_stats(srv)
+        assert rep["submitted"] == 0 and rep["completed"] == 0
+    finally:
+        capi.bfs_serve_destroy(srv)
+    assert capi.lib().bfs_serve_destroy(None) == 0
