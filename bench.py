@@ -214,17 +214,21 @@ def main() -> int:
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "serve"])
+    ap.add_argument("--mode", default="single", choices=["single", "serve", "multigraph"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     args = ap.parse_args()
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "multigraph":
+        return run_multigraph(args)
     args.warmup = max(args.warmup, 0)
 
     from paper_1408_1605_gb300.workloads import WORKLOADS
 
     wl = WORKLOADS[args.workload]
+    args.grid_dims = wl.dims if wl.kind == "grid3d" else None
     rank, world, local_rank = dist_env()
     t = time.perf_counter()
     g = wl.make()
@@ -258,6 +262,14 @@ def main() -> int:
     off_bytes = 8 if g.nnz > 2**31 - 1 else 4
     lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
     pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    shapes = {}
+    if not args.no_autotune:
+        from paper_1408_1605_gb300 import autotune
+
+        tune_roots = pool[: max(3, min(len(pool), 3))]
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, wl.kind, g.n, tune_roots, lv, pr)
+        shapes["single"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"]}
+        log(f"[bench] single-source shape {shapes['single']} ms per shape {rec.get('ms')}")
     for r in warm_roots:
         capi.bfs_run(h, int(r), lv, pr, want_stats=True)
     torch.cuda.synchronize()
@@ -309,7 +321,7 @@ def main() -> int:
 
     batched = None
     if not args.no_batched:
-        batched = batched_leg(h, g, timed_roots, stats)
+        batched = batched_leg(h, g, timed_roots, stats, None if args.no_autotune else wl.kind, shapes)
 
     # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks
     value, ms_step = hm, elapsed_ms / max(len(stats), 1)
@@ -332,7 +344,7 @@ def main() -> int:
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": len(stats),
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
-            "config": config_for(wl, g, args),
+            "config": dict(config_for(wl, g, args), shapes=shapes),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                          "kernel": "k_expand", "launches": launches_expand,
@@ -363,7 +375,7 @@ def main() -> int:
     return 0
 
 
-def batched_leg(h, g, roots, single_stats):
+def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
     """The same roots as 64-root waves (bfs_run_batch): aggregate GTEPS of the waves against
     the aggregate of the single-source searches (sum m_c / sum time for both)."""
     import torch
@@ -374,6 +386,13 @@ def batched_leg(h, g, roots, single_stats):
     k = min(wave, len(roots))
     lv = torch.empty((k, g.n), dtype=torch.int32, device="cuda")
     pr = torch.empty((k, g.n), dtype=torch.int32, device="cuda")
+    if graph_class is not None:
+        from paper_1408_1605_gb300 import autotune
+
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, graph_class, g.n, roots[:k], lv, pr)
+        if shapes is not None:
+            shapes["batch"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"]}
+        log(f"[bench] batch shape {rec['shape']} ms per shape {rec.get('ms')}")
     capi.bfs_run_batch(h, roots[:k], lv, pr, want_stats=True)  # warm-up (buffers, graph)
     edges, ms, waves = 0, 0.0, 0
     for i in range(0, len(roots), wave):
@@ -462,6 +481,90 @@ def run_serve(args) -> int:
     return 0
 
 
+def run_multigraph(args) -> int:
+    """Uneven batch: 32 R-MAT graphs (edge factor 16) with scales drawn uniformly from 14 to
+    20 (seeded), 64 roots each, one 64-root wave per graph; every wave is a CUDA-graph level
+    loop, the waves of different graphs run on four streams at once, and each graph's batch
+    shape comes from the autotuner (cached per scale). Aggregate GTEPS = sum of m_c over all
+    roots / device time of the whole set."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1408_1605_gb300 import autotune, capi, graphs
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    rng = np.random.default_rng(20140806 + 3)
+    scales = rng.integers(14, 21, 32)
+    gs, hs, roots, outs = [], [], [], []
+    t = time.perf_counter()
+    for i, sc in enumerate(scales):
+        g = graphs.rmat(int(sc), 16, seed=20140806 + 300 + i)
+        h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
+        r = graphs.pick_roots(g, 64, graphs.root_seed(20140806 + 300 + i))
+        lv = torch.empty((r.size, g.n), dtype=torch.int32, device="cuda")
+        pr = torch.empty((r.size, g.n), dtype=torch.int32, device="cuda")
+        gs.append(g), hs.append(h), roots.append(r), outs.append((lv, pr))
+    log(f"[multigraph] 32 graphs, scales {sorted(scales.tolist())}, built in {time.perf_counter() - t:.1f}s")
+    chosen = {}
+    for g, h, r, (lv, pr) in zip(gs, hs, roots, outs):
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, "rmat", g.n, r, lv, pr)
+        chosen[int(round(np.log2(g.n)))] = rec["shape"]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+
+    def one_pass(want_stats):
+        sts = []
+        for i, (h, r, (lv, pr)) in enumerate(zip(hs, roots, outs)):
+            st = capi.bfs_run_batch(h, r, lv, pr, stream=streams[i % 4], want_stats=want_stats)
+            sts.append(st)
+        return sts
+
+    stats = one_pass(True)  # warm-up, and the per-root m_c
+    edges = sum(s.edges_traversed for st in stats for s in st)
+    for _ in range(max(args.warmup - 1, 0)):
+        one_pass(False)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    main = torch.cuda.current_stream()
+    times = []
+    for _ in range(max(1, args.steps)):
+        ev0.record(main)
+        for s in streams:
+            s.wait_event(ev0)
+        one_pass(False)
+        for s in streams:
+            e = torch.cuda.Event()
+            e.record(s)
+            main.wait_event(e)
+        ev1.record(main)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    ms = float(np.median(times))
+    # parity on sampled roots of four graphs
+    ok, checked = True, 0
+    for i in (0, 10, 20, 31):
+        L, P = outs[i][0].cpu().numpy(), outs[i][1].cpu().numpy()
+        for b in (0, 63):
+            ref, _ = oracle.bfs(gs[i].offsets, gs[i].cols, int(roots[i][b]))
+            ok &= bool(np.array_equal(L[b], ref))
+            ok &= oracle.check_tree(gs[i].offsets, gs[i].cols, int(roots[i][b]), ref, L[b], P[b])[0] == 0
+            checked += 1
+    for h in hs:
+        capi.bfs_graph_destroy(h)
+    if rank == 0:
+        print(json.dumps({"metric": "aggregate GTEPS, 32 uneven R-MAT graphs x 64 roots (batched waves)",
+                          "mode": "multigraph", "value": round(edges / (ms * 1e-3) / 1e9, 3), "unit": "GTEPS",
+                          "n_gpus": world, "steps": len(times), "warmup": args.warmup,
+                          "ms_per_step": round(ms, 3), "higher_is_better": True, "data": "synthetic",
+                          "dtype": "i32/i64",
+                          "config": {"workload": "32 R-MAT graphs, scales U{14..20}, EF16, 64 roots each",
+                                     "scales": sorted(int(x) for x in scales), "streams": 4,
+                                     "batch_shape_per_scale": chosen},
+                          "parity": {"roots_checked": checked, "ok": ok}}), flush=True)
+    return 0 if ok else 1
+
+
 def cpu_leg(args, g, h, roots, lv, pr):
     """Oracle timed single-threaded on a bounded sample of the timed roots; the GPU result
     for the same roots is checked against it (levels exact, parents valid)."""
@@ -489,6 +592,22 @@ def cpu_leg(args, g, h, roots, lv, pr):
             break
     parity = {"roots_checked": checked, "levels_exact": exact_all, "parents_valid": valid_all,
               "ok": exact_all and valid_all}
+    dims = getattr(args, "grid_dims", None)
+    if dims:
+        # full-size closed form on more roots: level = Manhattan distance on the grid
+        X, Y, Z = dims
+        ids = np.arange(g.n, dtype=np.int64)
+        x, y, z = ids % X, (ids // X) % Y, ids // (X * Y)
+        closed_ok, n_closed = True, 0
+        for r in roots[:8]:
+            capi.bfs_run(h, int(r), lv, pr)
+            rx, ry, rz = int(r) % X, (int(r) // X) % Y, int(r) // (X * Y)
+            want = np.abs(x - rx) + np.abs(y - ry) + np.abs(z - rz)
+            closed_ok &= bool(np.array_equal(lv.cpu().numpy(), want))
+            n_closed += 1
+        parity["closed_form_roots"] = n_closed
+        parity["closed_form_ok"] = closed_ok
+        parity["ok"] = parity["ok"] and closed_ok
     cpu = {"value": round(harmonic_mean(teps), 4), "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"{used} of the {len(roots)} timed roots, full searches on the same graph"}
     return parity, cpu

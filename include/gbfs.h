@@ -69,7 +69,7 @@ typedef struct bfs_graph_s *bfs_graph_t;
  * sum over reached vertices. */
 typedef struct bfs_stats {
   int32_t depth;            /* number of non-empty levels, i.e. max level + 1 */
-  int32_t reserved;
+  int32_t bottom_up_levels; /* levels run bottom-up (BFS_OPT_BOTTOM_UP), else 0 */
   int64_t vertices_reached; /* including the root */
   int64_t edges_traversed;  /* m_c */
   double device_ms;         /* device time of the whole search, CUDA events on `stream` */
@@ -89,6 +89,28 @@ GBFS_API bfs_status bfs_graph_create(const void *row_offsets, const int32_t *col
 /* Releases the graph's device memory and work buffers. Waits for the graph's pending
  * work. NULL is accepted (no-op). */
 GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
+
+/* Per-graph options of single-source searches (bfs_run):
+ *   BFS_OPT_LOOP: how the level loop runs. BFS_LOOP_GRAPH (default): a CUDA graph with a
+ *     conditional WHILE node, one expansion launch per level. BFS_LOOP_PERSISTENT: one
+ *     cooperative launch runs every level, separated by a grid barrier whose waits are
+ *     bounded (expiry: BFS_ERR_TIMEOUT). BFS_LOOP_HOST: one launch per level and a host
+ *     check of the next frontier (for profilers that cannot see graph kernel nodes).
+ *   BFS_OPT_BOTTOM_UP: 1 lets a persistent search run large levels bottom-up (every
+ *     unvisited vertex looks for a parent in the frontier; Beamer et al., the paper's
+ *     related work, Sec. 6) when frontier edges x ALPHA exceed the unexplored edges, and
+ *     return to top-down once frontier vertices x BETA < n. Results are the same BFS
+ *     (levels identical; parents valid). Default 0: every level top-down (Algorithm 3).
+ *   BFS_OPT_ALPHA (default 14), BFS_OPT_BETA (default 24): the switching thresholds. */
+#define BFS_OPT_LOOP 1
+#define BFS_OPT_BOTTOM_UP 2
+#define BFS_OPT_ALPHA 3
+#define BFS_OPT_BETA 4
+#define BFS_LOOP_PERSISTENT 0
+#define BFS_LOOP_GRAPH 1
+#define BFS_LOOP_HOST 2
+GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t g, int option, int64_t value);
+GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t g, int option, int64_t *value);
 
 /* Vertex and CSR-entry counts of a graph. */
 GBFS_API bfs_status bfs_graph_info(bfs_graph_t g, int64_t *n_vertices, int64_t *n_entries);
@@ -235,6 +257,36 @@ GBFS_API bfs_status bfs_serve_stats(bfs_server_t srv, bfs_serve_report *report);
 /* Stops the scheduler (pending queries are cancelled, running ones finish) and frees the
  * server's device memory. NULL is accepted. */
 GBFS_API bfs_status bfs_serve_destroy(bfs_server_t srv);
+
+/* ---------------------------------------------------------------------------------------
+ * Kernel shapes and tuning. Each expansion kernel is compiled for a few shapes (threads per
+ * CTA, edges per thread, claim-buffer entries); the paper picks its edges-per-thread value
+ * by a sweep (Sec. 3.4.1, Fig. 3), and bfs_tune does the same sweep per graph.
+ * --------------------------------------------------------------------------------------- */
+#define BFS_KERNEL_SINGLE 0 /* single-source expansion (bfs_run, bfs_expand) */
+#define BFS_KERNEL_BATCH 1  /* multi-source expansion (bfs_run_batch, serving waves) */
+
+/* Number of compiled shapes of a kernel kind (0 for an unknown kind). */
+GBFS_API int bfs_shape_count(int kind);
+
+/* Shape parameters: CTA size, edges per thread, claim-buffer entries per CTA. */
+GBFS_API bfs_status bfs_shape_info(int kind, int shape, int *block, int *edges_per_thread, int *claim_buffer);
+
+/* Selects the shape a graph's later searches use (waits for the graph's pending work). A
+ * server takes a graph's batch shape when the graph is added. */
+GBFS_API bfs_status bfs_graph_set_shape(bfs_graph_t g, int kind, int shape);
+GBFS_API bfs_status bfs_graph_get_shape(bfs_graph_t g, int kind, int *shape);
+
+/* Times every compiled shape of `kind` on this graph and keeps the fastest.
+ *   BFS_KERNEL_SINGLE: one warm-up search, then one bfs_run per root; levels / parents as
+ *     for bfs_run; ms_per_shape[s] = mean device ms per root.
+ *   BFS_KERNEL_BATCH: n_roots <= 64; one warm-up wave and one timed wave per shape;
+ *     levels / parents as for bfs_run_batch; ms_per_shape[s] = device ms per wave.
+ * ms_per_shape: NULL or double[bfs_shape_count(kind)]; best_shape: NULL or the choice.
+ * Other calls on the graph must not run meanwhile. Failures as for bfs_run /
+ * bfs_run_batch. */
+GBFS_API bfs_status bfs_tune(bfs_graph_t g, int kind, const int32_t *roots, int n_roots, int32_t *levels,
+                             int32_t *parents, void *stream, double *ms_per_shape, int *best_shape);
 
 /* Message for the last failing call on this thread ("" if none). */
 GBFS_API const char *bfs_last_error(void);

@@ -24,6 +24,15 @@ BFS_DEVICE_PTRS = 0x2
 BFS_OFFSETS_INT32 = 0x4
 BFS_OFFSETS_INT64 = 0x8
 BFS_VALIDATE = 0x10
+BFS_OPT_LOOP = 1
+BFS_OPT_BOTTOM_UP = 2
+BFS_OPT_ALPHA = 3
+BFS_OPT_BETA = 4
+BFS_LOOP_PERSISTENT = 0
+BFS_LOOP_GRAPH = 1
+BFS_LOOP_HOST = 2
+BFS_KERNEL_SINGLE = 0
+BFS_KERNEL_BATCH = 1
 
 _P = ctypes.c_void_p
 _lib = None
@@ -53,11 +62,11 @@ class bfs_serve_report(ctypes.Structure):
 
 
 class bfs_stats(ctypes.Structure):
-    _fields_ = [("depth", ctypes.c_int32), ("reserved", ctypes.c_int32), ("vertices_reached", ctypes.c_int64),
+    _fields_ = [("depth", ctypes.c_int32), ("bottom_up_levels", ctypes.c_int32), ("vertices_reached", ctypes.c_int64),
                 ("edges_traversed", ctypes.c_int64), ("device_ms", ctypes.c_double), ("expand_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def library_path() -> str:
@@ -96,11 +105,21 @@ def lib():
             "bfs_serve_result": [_P, ctypes.c_uint64, ctypes.POINTER(bfs_stats)],
             "bfs_serve_stats": [_P, ctypes.POINTER(bfs_serve_report)],
             "bfs_serve_destroy": [_P],
+            "bfs_shape_info": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int)],
+            "bfs_graph_set_shape": [_P, ctypes.c_int, ctypes.c_int],
+            "bfs_graph_set_option": [_P, ctypes.c_int, i64],
+            "bfs_graph_get_option": [_P, ctypes.c_int, ctypes.POINTER(i64)],
+            "bfs_graph_get_shape": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+            "bfs_tune": [_P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_int)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        L.bfs_shape_count.restype = ctypes.c_int
+        L.bfs_shape_count.argtypes = [ctypes.c_int]
         L.bfs_last_error.restype = ctypes.c_char_p
         L.bfs_version.restype = ctypes.c_char_p
         _lib = L
@@ -239,6 +258,49 @@ def bfs_serve_stats(server: int) -> dict:
 
 def bfs_serve_destroy(server: int) -> None:
     check(lib().bfs_serve_destroy(server))
+
+
+def bfs_graph_set_option(graph: int, option: int, value: int) -> None:
+    check(lib().bfs_graph_set_option(graph, int(option), int(value)))
+
+
+def bfs_graph_get_option(graph: int, option: int) -> int:
+    v = ctypes.c_int64()
+    check(lib().bfs_graph_get_option(graph, int(option), ctypes.byref(v)))
+    return v.value
+
+
+def bfs_shape_count(kind: int) -> int:
+    return int(lib().bfs_shape_count(int(kind)))
+
+
+def bfs_shape_info(kind: int, shape: int) -> dict:
+    b, e, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().bfs_shape_info(int(kind), int(shape), ctypes.byref(b), ctypes.byref(e), ctypes.byref(c)))
+    return {"block": b.value, "edges_per_thread": e.value, "claim_buffer": c.value}
+
+
+def bfs_graph_set_shape(graph: int, kind: int, shape: int) -> None:
+    check(lib().bfs_graph_set_shape(graph, int(kind), int(shape)))
+
+
+def bfs_graph_get_shape(graph: int, kind: int) -> int:
+    s = ctypes.c_int()
+    check(lib().bfs_graph_get_shape(graph, int(kind), ctypes.byref(s)))
+    return s.value
+
+
+def bfs_tune(graph: int, kind: int, roots, levels, parents, stream=None):
+    """Returns (best_shape, [ms per shape])."""
+    import numpy as np
+
+    r = np.ascontiguousarray(roots, dtype=np.int32)
+    n = bfs_shape_count(kind)
+    ms = (ctypes.c_double * max(n, 1))()
+    best = ctypes.c_int(-1)
+    check(lib().bfs_tune(graph, int(kind), r.ctypes.data, int(r.size), ptr(levels), ptr(parents),
+                         stream_handle(stream), ms, ctypes.byref(best)))
+    return best.value, [ms[i] for i in range(n)]
 
 
 def bfs_last_error() -> str:

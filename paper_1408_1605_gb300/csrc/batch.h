@@ -108,10 +108,13 @@ void launch_batch_clear(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int n_seeds, int wave_level,
                        bool fresh, cudaStream_t st);
+extern const ExpandShape kBatchShapes[];
+extern const int kNumBatchShapes;
+constexpr int kDefaultBatchShape = 0;
 template <typename OffT>
-cudaError_t launch_batch_expand(const BatchArgs<OffT>& a, int grid, cudaStream_t st);
+cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, cudaStream_t st);
 template <typename OffT>
-int batch_expand_grid(int num_sms);
+int batch_expand_grid(int shape, int num_sms);
 void launch_fill(int32_t* p, int64_t count, int32_t value, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int n_slots, long long* stats,

@@ -123,7 +123,8 @@ bfs_status ensure_batch_state(bfs_graph_s* G) {
     delete S;
     return cuda_fail(e, "batch work buffers");
   }
-  S->grid = g.off64 ? batch_expand_grid<int64_t>(g.num_sms) : batch_expand_grid<int32_t>(g.num_sms);
+  S->grid = g.off64 ? batch_expand_grid<int64_t>(G->batch_shape, g.num_sms)
+                    : batch_expand_grid<int32_t>(G->batch_shape, g.num_sms);
   G->batch = S;
   return BFS_OK;
 }
@@ -164,7 +165,7 @@ static bfs_status build_batch_graph(bfs_graph_s* G) {
     goto bad;
   }
   {
-    cudaError_t le = launch_batch_expand<OffT>(a, S->grid, cs);
+    cudaError_t le = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, cs);
     e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
     if (le != cudaSuccess) e = le;
@@ -240,7 +241,8 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
   if ((e = cudaEventRecord(S->ev_mid, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if (G->host_loop) {
     for (int64_t it = 0; it <= g.n; ++it) {
-      if ((e = launch_batch_expand<OffT>(a, S->grid, st)) != cudaSuccess) return cuda_fail(e, "batch expand");
+      if ((e = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, st)) != cudaSuccess)
+        return cuda_fail(e, "batch expand");
       if ((e = cudaMemcpyAsync(S->ctl_host, S->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "batch level sync");
@@ -279,7 +281,7 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
       cudaEventElapsedTime(&loop_ms, S->ev_mid, S->ev1);
       for (int b = 0; b < n_roots; ++b) {
         stats[b].depth = (int32_t)S->stats_host[3 * b + 2];
-        stats[b].reserved = 0;
+        stats[b].bottom_up_levels = 0;
         stats[b].vertices_reached = S->stats_host[3 * b + 1];
         stats[b].edges_traversed = S->stats_host[3 * b + 0] / 2;
         stats[b].device_ms = ms;
@@ -288,6 +290,20 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
     }
   }
   return BFS_OK;
+}
+
+// Switches the multi-source expansion shape; the level-loop graph is rebuilt on next use.
+void set_batch_shape(bfs_graph_s* G, int shape) {
+  G->batch_shape = shape;
+  if (G->batch) {
+    BatchState* S = G->batch;
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    S->exec = nullptr;
+    S->graph = nullptr;
+    S->grid = G->g.off64 ? batch_expand_grid<int64_t>(shape, G->g.num_sms)
+                         : batch_expand_grid<int32_t>(shape, G->g.num_sms);
+  }
 }
 
 }  // namespace gbfs

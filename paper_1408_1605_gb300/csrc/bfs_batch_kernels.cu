@@ -120,26 +120,22 @@ void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int 
   k_batch_seed<OffT><<<1, 32, 0, st>>>(a, seeds_dev, n_seeds, fresh ? 1 : 0);
 }
 
-constexpr int kBatchBlock = 256;
-constexpr int kBatchE = 4;
-constexpr int kBatchClaim = 2048;
-
-template <typename OffT>
+template <typename OffT, int BLOCK, int E, int CLAIM>
 struct BatchSmem {
-  static constexpr int T = kBatchBlock * kBatchE;
+  static constexpr int T = BLOCK * E;
   static constexpr int CAP = T + 1;
   static constexpr size_t off_f = 0;  // uint64 masks first (8-byte aligned)
   static constexpr size_t off_base = off_f + 8 * CAP;
   static constexpr size_t off_rel = off_base + sizeof(OffT) * CAP;
   static constexpr size_t off_u = off_rel + 4 * (CAP + 1);
   static constexpr size_t off_claim = ((off_u + 4 * CAP) + 15) & ~size_t(15);
-  static constexpr size_t bytes = off_claim + sizeof(int2) * kBatchClaim;
+  static constexpr size_t bytes = off_claim + sizeof(int2) * CLAIM;
 };
 
-template <typename OffT>
+template <typename OffT, int BLOCK, int CLAIM>
 __device__ __forceinline__ void batch_flush(const BatchArgs<OffT>& a, int nxt, int q3n, int2* s_claim, int nc,
                                             OffT* s_warp, unsigned long long* s_resv) {
-  constexpr int P = (kBatchClaim + kBatchBlock - 1) / kBatchBlock;
+  constexpr int P = (CLAIM + BLOCK - 1) / BLOCK;
   const int lo = min(nc, (int)threadIdx.x * P), hi = min(nc, lo + P);
   OffT mine = 0;
   for (int i = lo; i < hi; ++i) mine += (OffT)s_claim[i].y;
@@ -162,10 +158,11 @@ __device__ __forceinline__ void batch_flush(const BatchArgs<OffT>& a, int nxt, i
   }
 }
 
-template <typename OffT>
-__global__ void __launch_bounds__(kBatchBlock) k_expand_batch(BatchArgs<OffT> a) {
-  using S = BatchSmem<OffT>;
-  constexpr int T = S::T, CAP = S::CAP, E = kBatchE, BLOCK = kBatchBlock;
+template <typename OffT, int BLOCK, int E, int CLAIM>
+__global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
+  using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
+  constexpr int T = S::T, CAP = S::CAP;
+  static_assert(CLAIM >= T, "claim buffer must hold one full tile");
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* s_f = reinterpret_cast<unsigned long long*>(smem + S::off_f);
   OffT* s_base = reinterpret_cast<OffT*>(smem + S::off_base);
@@ -307,15 +304,15 @@ __global__ void __launch_bounds__(kBatchBlock) k_expand_batch(BatchArgs<OffT> a)
     }
     __syncthreads();
     const int nc = s_nclaim;
-    if (nc > kBatchClaim - T) {
-      batch_flush<OffT>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
+    if (nc > CLAIM - T) {
+      batch_flush<OffT, BLOCK, CLAIM>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
       __syncthreads();
       if (threadIdx.x == 0) s_nclaim = 0;
     }
   }
   __syncthreads();
   const int nc = s_nclaim;
-  if (nc > 0) batch_flush<OffT>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
+  if (nc > 0) batch_flush<OffT, BLOCK, CLAIM>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_alive) atomicOr(&ctl->alive[nxt], s_alive);
@@ -336,29 +333,64 @@ __global__ void __launch_bounds__(kBatchBlock) k_expand_batch(BatchArgs<OffT> a)
   }
 }
 
-template <typename OffT>
-cudaError_t launch_batch_expand(const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
-  using S = BatchSmem<OffT>;
+template <typename OffT, int BLOCK, int E, int CLAIM>
+static cudaError_t launch_batch_expand_t(const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
+  using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
+  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_expand_batch<OffT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::bytes);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_expand_batch<OffT><<<grid, kBatchBlock, S::bytes, st>>>(a);
+  kern<<<grid, BLOCK, S::bytes, st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename OffT>
-int batch_expand_grid(int num_sms) {
-  using S = BatchSmem<OffT>;
-  cudaFuncSetAttribute(k_expand_batch<OffT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+template <typename OffT, int BLOCK, int E, int CLAIM>
+static int batch_grid_t(int num_sms) {
+  using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
+  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_batch<OffT>, kBatchBlock, S::bytes) !=
-      cudaSuccess)
-    per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
   return (per_sm > 0 ? per_sm : 1) * num_sms;
+}
+
+// Compiled shapes of the batched expansion (BLOCK, E, CLAIM); the autotuner picks one.
+#define GBFS_BATCH_SHAPES(X) \
+  X(0, 256, 4, 2048)         \
+  X(1, 256, 2, 2048)         \
+  X(2, 128, 4, 1024)         \
+  X(3, 512, 2, 2048)
+
+const ExpandShape kBatchShapes[] = {
+#define X(id, b, e, c) {id, b, e, c},
+    GBFS_BATCH_SHAPES(X)
+#undef X
+};
+const int kNumBatchShapes = sizeof(kBatchShapes) / sizeof(kBatchShapes[0]);
+
+template <typename OffT>
+cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
+  switch (shape) {
+#define X(id, b, e, c) \
+  case id: return launch_batch_expand_t<OffT, b, e, c>(a, grid, st);
+    GBFS_BATCH_SHAPES(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename OffT>
+int batch_expand_grid(int shape, int num_sms) {
+  switch (shape) {
+#define X(id, b, e, c) \
+  case id: return batch_grid_t<OffT, b, e, c>(num_sms);
+    GBFS_BATCH_SHAPES(X)
+#undef X
+  }
+  return num_sms;
 }
 
 // Per-slot statistics from the outputs: stats[3 b + 0] = sum of degrees of reached
@@ -458,8 +490,8 @@ void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long 
 #define INST(OffT)                                                                                          \
   template void launch_batch_clear<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
   template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
-  template cudaError_t launch_batch_expand<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                \
-  template int batch_expand_grid<OffT>(int);                                                                \
+  template cudaError_t launch_batch_expand<OffT>(int, const BatchArgs<OffT>&, int, cudaStream_t);           \
+  template int batch_expand_grid<OffT>(int, int);                                                           \
   template void launch_batch_stats<OffT>(const OffT*, int64_t, const WaveSlots*, int, long long*, int, cudaStream_t); \
   template void launch_level_stats<OffT>(const OffT*, int64_t, const int32_t*, long long*, int, cudaStream_t);
 INST(int32_t)

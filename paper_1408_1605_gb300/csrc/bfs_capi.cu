@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "capi_internal.h"
 #include "gbfs.h"
 #include "kernels.h"
@@ -63,6 +64,9 @@ static void free_single_ws(SingleWs& ws) {
   cudaFree(ws.scan_partial);
   cudaFree(ws.host_levels);
   cudaFree(ws.host_parents);
+  for (int i = 0; i < 3; ++i) cudaFree(ws.fbm[i]);
+  cudaFree(ws.pctl);
+  if (ws.pctl_host) cudaFreeHost(ws.pctl_host);
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);
   if (ws.ev0) cudaEventDestroy(ws.ev0);
   if (ws.ev1) cudaEventDestroy(ws.ev1);
@@ -85,11 +89,15 @@ bfs_status ensure_single_ws(bfs_graph_s* G) {
     if ((s = device_alloc(&ws.chunk[i], (size_t)ws.chunk_cap, "chunk index"))) goto bad;
   }
   if ((s = device_alloc(&ws.ctl, 1, "control block"))) goto bad;
+  if ((s = device_alloc(&ws.pctl, 1, "control block"))) goto bad;
+  for (int i = 0; i < 3; ++i)
+    if ((s = device_alloc(&ws.fbm[i], (size_t)(g.n + 31) / 32, "frontier bitmap"))) goto bad;
   ws.scan_parts = g.num_sms * 4;
   if ((s = device_alloc(reinterpret_cast<char**>(&ws.scan_partial), (size_t)ws.scan_parts * 8, "scan partials")))
     goto bad;
   {
     cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&ws.ctl_host), sizeof(Ctl), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&ws.pctl_host), sizeof(PCtl), cudaHostAllocDefault);
     if (e != cudaSuccess) {
       s = cuda_fail(e, "pinned control mirror");
       goto bad;
@@ -216,10 +224,36 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
   }
   if (G->last_done) cudaStreamWaitEvent(st, G->last_done, 0);  // workspace reuse across streams
   if ((e = cudaEventRecord(ws.ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-  launch_init_single<OffT>(G->g, root, dl, dp, ws, st);
+  const bool persistent = G->loop_mode == BFS_LOOP_PERSISTENT;
+  if (persistent)
+    launch_init_persist<OffT>(G->g, root, dl, dp, ws, st);
+  else
+    launch_init_single<OffT>(G->g, root, dl, dp, ws, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "init kernel");
   if ((e = cudaEventRecord(ws.ev_mid, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-  if (G->host_loop) {
+  if (persistent) {
+    PersistArgs<OffT> pa{};
+    pa.off = reinterpret_cast<const OffT*>(G->g.off);
+    pa.cols = G->g.cols;
+    pa.bitmap = ws.bitmap;
+    for (int i = 0; i < 3; ++i) pa.fbm[i] = ws.fbm[i];
+    pa.n = G->g.n;
+    pa.nnz = G->g.nnz;
+    pa.fr[0] = ws.fr<OffT>(0);
+    pa.fr[1] = ws.fr<OffT>(1);
+    pa.chunk[0] = ws.chunk[0];
+    pa.chunk[1] = ws.chunk[1];
+    pa.ctl = ws.pctl;
+    pa.pk = G->g.pk;
+    pa.levels = dl;
+    pa.parents = dp;
+    pa.alpha = G->alpha;
+    pa.beta = G->beta;
+    pa.allow_bottom_up = G->bottom_up;
+    if (!G->pgrid) G->pgrid = persistent_grid<OffT>(G->shape, G->g.num_sms);
+    if ((e = launch_persistent<OffT>(G->shape, pa, G->pgrid, st)) != cudaSuccess)
+      return cuda_fail(e, "persistent search kernel");
+  } else if (G->host_loop) {
     ExpandArgs<OffT> a = make_args<OffT>(G, ws.bitmap);
     for (int64_t it = 0; it <= G->g.n; ++it) {
       if ((e = launch_expand<OffT>(G->shape, a, G->grid, st)) != cudaSuccess) return cuda_fail(e, "expand kernel");
@@ -244,23 +278,31 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     if ((e = cudaMemcpyAsync(parents, dp, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "parents copy");
   }
-  if ((e = cudaMemcpyAsync(ws.ctl_host, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+  if (persistent) {
+    if ((e = cudaMemcpyAsync(ws.pctl_host, ws.pctl, sizeof(PCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "control copy");
+  } else if ((e = cudaMemcpyAsync(ws.ctl_host, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess) {
     return cuda_fail(e, "control copy");
+  }
   if (!G->last_done && (e = cudaEventCreateWithFlags(&G->last_done, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "cudaEventCreate");
   cudaEventRecord(G->last_done, st);
   if (stats || host_out) {
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "search");
-    const Ctl& c = *ws.ctl_host;
-    if (c.error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
+    const unsigned error = persistent ? ws.pctl_host->error : ws.ctl_host->error;
+    if (error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
+    if (error & kErrTimeout) return fail(BFS_ERR_TIMEOUT, "a grid barrier wait expired");
     if (stats) {
       float ms = 0.f, loop_ms = 0.f;
       cudaEventElapsedTime(&ms, ws.ev0, ws.ev1);
       cudaEventElapsedTime(&loop_ms, ws.ev_mid, ws.ev1);
-      stats->depth = c.depth;
-      stats->reserved = 0;
-      stats->vertices_reached = c.reached;
-      stats->edges_traversed = c.edges2 / 2;
+      const int depth = persistent ? ws.pctl_host->depth : ws.ctl_host->depth;
+      const long long reached = persistent ? ws.pctl_host->reached : ws.ctl_host->reached;
+      const long long edges2 = persistent ? ws.pctl_host->edges2 : ws.ctl_host->edges2;
+      stats->depth = depth;
+      stats->bottom_up_levels = persistent ? ws.pctl_host->steps_bottom_up : 0;
+      stats->vertices_reached = reached;
+      stats->edges_traversed = edges2 / 2;
       stats->device_ms = ms;
       stats->expand_ms = loop_ms;
     }
@@ -288,6 +330,17 @@ static bfs_status expand_one(bfs_graph_s* G, const int32_t* front, int64_t nf, i
   if (c.error & kErrCounterOverflow) return fail(BFS_ERR_INVALID_ARG, "frontier edge total exceeds capacity");
   if (c.error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
   return BFS_OK;
+}
+
+// Switches the single-source expansion shape; the level-loop graph is rebuilt on next use.
+void set_single_shape(bfs_graph_s* G, int shape) {
+  G->shape = shape;
+  G->pgrid = 0;
+  G->grid = G->g.off64 ? expand_grid<int64_t>(shape, G->g.num_sms) : expand_grid<int32_t>(shape, G->g.num_sms);
+  if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
+  if (G->loop_graph) cudaGraphDestroy(G->loop_graph);
+  G->loop_exec = nullptr;
+  G->loop_graph = nullptr;
 }
 
 }  // namespace gbfs
@@ -443,9 +496,20 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
   }
   const char* hl = std::getenv("GBFS_HOST_LOOP");
   G->host_loop = hl && std::atoi(hl) != 0;
+  const char* lm = std::getenv("GBFS_LOOP");
+  if (lm) {
+    const std::string m(lm);
+    G->loop_mode = m == "persistent" ? BFS_LOOP_PERSISTENT : m == "host" ? BFS_LOOP_HOST : BFS_LOOP_GRAPH;
+  }
+  if (G->host_loop) G->loop_mode = BFS_LOOP_HOST;
+  G->host_loop = G->loop_mode == BFS_LOOP_HOST;
+  const char* bu = std::getenv("GBFS_BOTTOM_UP");
+  G->bottom_up = bu && std::atoi(bu) != 0;
   const char* sh = std::getenv("GBFS_SHAPE");
   G->shape = sh ? std::max(0, std::min(kNumExpandShapes - 1, std::atoi(sh))) : kDefaultShape;
   G->grid = g.off64 ? expand_grid<int64_t>(G->shape, g.num_sms) : expand_grid<int32_t>(G->shape, g.num_sms);
+  const char* bsh = std::getenv("GBFS_BATCH_SHAPE");
+  G->batch_shape = bsh ? std::max(0, std::min(kNumBatchShapes - 1, std::atoi(bsh))) : kDefaultBatchShape;
   *out = G;
   return BFS_OK;
 }
@@ -466,6 +530,40 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t G) {
   }
   delete G;
   return BFS_OK;
+}
+
+GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t value) {
+  clear_last_error();
+  if (!G) return fail(BFS_ERR_INVALID_ARG, "graph is NULL");
+  std::lock_guard<std::mutex> lock(G->mu);
+  switch (option) {
+    case BFS_OPT_LOOP:
+      if (value < BFS_LOOP_PERSISTENT || value > BFS_LOOP_HOST) return fail(BFS_ERR_INVALID_ARG, "unknown loop mode");
+      G->loop_mode = (int)value;
+      G->host_loop = value == BFS_LOOP_HOST;
+      return BFS_OK;
+    case BFS_OPT_BOTTOM_UP:
+      G->bottom_up = value != 0;
+      return BFS_OK;
+    case BFS_OPT_ALPHA:
+    case BFS_OPT_BETA:
+      if (value < 1 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "alpha/beta outside [1, 2^20]");
+      (option == BFS_OPT_ALPHA ? G->alpha : G->beta) = (int)value;
+      return BFS_OK;
+  }
+  return fail(BFS_ERR_INVALID_ARG, "unknown option");
+}
+
+GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* value) {
+  clear_last_error();
+  if (!G || !value) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  switch (option) {
+    case BFS_OPT_LOOP: *value = G->loop_mode; return BFS_OK;
+    case BFS_OPT_BOTTOM_UP: *value = G->bottom_up; return BFS_OK;
+    case BFS_OPT_ALPHA: *value = G->alpha; return BFS_OK;
+    case BFS_OPT_BETA: *value = G->beta; return BFS_OK;
+  }
+  return fail(BFS_ERR_INVALID_ARG, "unknown option");
 }
 
 GBFS_API bfs_status bfs_graph_info(bfs_graph_t G, int64_t* n_vertices, int64_t* n_entries) {

@@ -165,7 +165,7 @@ __global__ void k_scan_final(const OffT* __restrict__ off, int64_t n, const int3
 }
 
 // ---------------------------------------------------------------------------------------
-// Frontier expansion
+// Frontier expansion (top-down step, shared by the per-level kernel and the persistent one)
 
 template <typename OffT, int BLOCK, int E, int CLAIM>
 struct ExpandSmem {
@@ -179,83 +179,111 @@ struct ExpandSmem {
   static constexpr size_t bytes = off_claim + sizeof(int2) * CLAIM;
 };
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
-__device__ __forceinline__ void flush_claims(const ExpandArgs<OffT>& a, const FrontierBuf<OffT>& out,
-                                             int32_t* chunk_out, int nxt, int2* s_claim, int nc, OffT* s_warp,
-                                             unsigned long long* s_resv) {
+// Static shared state of one CTA.
+template <typename OffT>
+struct ExpandShared {
+  OffT warp[33];
+  unsigned long long resv;
+  int nclaim, klo, kend;
+};
+
+// Where one level reads its frontier and writes the next one.
+template <typename OffT>
+struct LevelIO {
+  FrontierBuf<OffT> in, out;
+  const int32_t* chunk_in;
+  int32_t* chunk_out;
+  unsigned long long* counter_out;  // packed (count, edges) of the next frontier
+  int32_t* levels;
+  int32_t* parents;
+  uint32_t* fbm_out;                // next frontier as a bitmap (nullptr: not kept)
+  int L;                            // level assigned to claimed vertices
+  int64_t nf;                       // current frontier size
+  OffT r;                           // current frontier's degree sum
+};
+
+// Appends the CTA's buffered claims to the next frontier: one 64-bit atomic reserves the
+// slots and the exclusive-scan range of their degrees (Sec. 3.4 scan, fused).
+template <typename OffT, int BLOCK, int CLAIM>
+__device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const LevelIO<OffT>& io, int2* s_claim,
+                                             int nc, ExpandShared<OffT>& sh) {
   // Thread t owns the consecutive buffer items [t * P, t * P + P).
   constexpr int P = (CLAIM + BLOCK - 1) / BLOCK;
   const int lo = min(nc, (int)threadIdx.x * P), hi = min(nc, lo + P);
   OffT mine = 0;
   for (int i = lo; i < hi; ++i) mine += (OffT)s_claim[i].y;
   OffT total;
-  OffT run = block_exclusive_scan(mine, s_warp, &total);
-  if (threadIdx.x == 0) *s_resv = atomicAdd(&a.ctl->counter[nxt], a.pk.make(nc, (long long)total));
+  OffT run = block_exclusive_scan(mine, sh.warp, &total);
+  if (threadIdx.x == 0) sh.resv = atomicAdd(io.counter_out, pk.make(nc, (long long)total));
   __syncthreads();
-  const unsigned long long resv = *s_resv;
-  const long long slot0 = a.pk.count(resv);
-  run += (OffT)a.pk.edges(resv);
+  const unsigned long long resv = sh.resv;
+  const long long slot0 = pk.count(resv);
+  run += (OffT)pk.edges(resv);
   for (int i = lo; i < hi; ++i) {
     const int32_t v = s_claim[i].x;
     const OffT d = (OffT)s_claim[i].y;
     const int32_t slot = (int32_t)(slot0 + i);
-    out.v[slot] = v;
-    out.cum[slot] = run;
-    out.base[slot] = a.off[v] - run;
-    write_chunks(chunk_out, run, d, slot);
+    io.out.v[slot] = v;
+    io.out.cum[slot] = run;
+    io.out.base[slot] = off[v] - run;
+    write_chunks(io.chunk_out, run, d, slot);
     run += d;
   }
 }
 
+// Warp-aggregated push of this thread's claim (if any) into the CTA buffer.
+__device__ __forceinline__ void push_claim(bool claimed, int32_t v, int32_t deg, int2* s_claim, int* nclaim) {
+  const unsigned ball = __ballot_sync(0xffffffffu, claimed);
+  if (ball) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ball) - 1;
+    int pos = 0;
+    if (lane == leader) pos = atomicAdd(nclaim, __popc(ball));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (claimed) s_claim[pos + __popc(ball & lanemask_lt())] = make_int2(v, deg);
+  }
+}
+
+// One top-down level over tiles tile0, tile0 + tstride, ... of the level's edge space,
+// followed by the final flush of the CTA's claims. Every thread of the CTA calls it.
 template <typename OffT, int BLOCK, int E, int CLAIM>
-__global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
+__device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
+                         int64_t n, Packed pk, unsigned* err, const LevelIO<OffT>& io, unsigned char* dsmem,
+                         ExpandShared<OffT>& sh, int64_t tile0, int64_t tstride) {
   using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
   constexpr int T = S::T;
   constexpr int CAP = S::CAP;
   static_assert(CLAIM >= T, "claim buffer must hold one full tile");
-  extern __shared__ __align__(16) unsigned char smem[];
-  OffT* s_base = reinterpret_cast<OffT*>(smem + S::off_base);
-  int32_t* s_rel = reinterpret_cast<int32_t*>(smem + S::off_rel);
-  int32_t* s_u = reinterpret_cast<int32_t*>(smem + S::off_u);
-  int2* s_claim = reinterpret_cast<int2*>(smem + S::off_claim);
-  __shared__ OffT s_warp[33];
-  __shared__ unsigned long long s_resv;
-  __shared__ int s_nclaim;
-  __shared__ int s_klo, s_kend;
-
-  Ctl* ctl = a.ctl;
-  const int L = *(volatile int*)&ctl->level;
-  const int cur = (L - 1) & 1, nxt = cur ^ 1;
-  const unsigned long long pc = *(volatile unsigned long long*)&ctl->counter[cur];
-  const int64_t nf = a.pk.count(pc);
-  const OffT r = (OffT)a.pk.edges(pc);
-  int32_t* const levels = *(int32_t* volatile*)&ctl->levels;
-  int32_t* const parents = *(int32_t* volatile*)&ctl->parents;
-  const FrontierBuf<OffT> in = a.fr[cur], out = a.fr[nxt];
-  const int32_t* chunk_in = a.chunk[cur];
-  int32_t* chunk_out = a.chunk[nxt];
-  const int64_t ntiles = ((int64_t)r + T - 1) / T;
+  OffT* s_base = reinterpret_cast<OffT*>(dsmem + S::off_base);
+  int32_t* s_rel = reinterpret_cast<int32_t*>(dsmem + S::off_rel);
+  int32_t* s_u = reinterpret_cast<int32_t*>(dsmem + S::off_u);
+  int2* s_claim = reinterpret_cast<int2*>(dsmem + S::off_claim);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const OffT r = io.r;
+  const int64_t nf = io.nf;
+  const int64_t ntiles = ((int64_t)r + T - 1) / T;
+  const int L = io.L;
 
-  if (threadIdx.x == 0) s_nclaim = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  if (threadIdx.x == 0) sh.nclaim = 0;
+  for (int64_t tile = tile0; tile < ntiles; tile += tstride) {
     const OffT e0 = (OffT)(tile * T);
     const int cnt = (int)min((OffT)T, r - e0);
     __syncthreads();  // the previous tile's shared-memory reads are done
     if (threadIdx.x == 0) {
-      s_klo = chunk_in[e0 / kChunk];
-      s_kend = (e0 + cnt < r) ? chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+      sh.klo = io.chunk_in[e0 / kChunk];
+      sh.kend = (e0 + cnt < r) ? io.chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
     }
     __syncthreads();
-    const int klo = s_klo;
-    const int s = s_kend - klo + 1;
+    const int klo = sh.klo;
+    const int kend = sh.kend;
+    const int s = kend - klo + 1;
     const bool fast = s <= CAP;
     if (fast) {
       for (int i = threadIdx.x; i < s; i += BLOCK) {
-        const OffT c = in.cum[klo + i];
+        const OffT c = io.in.cum[klo + i];
         s_rel[i] = (int32_t)max(c - e0, (OffT)0);
-        s_base[i] = in.base[klo + i];
-        s_u[i] = in.v[klo + i];
+        s_base[i] = io.in.base[klo + i];
+        s_u[i] = io.in.v[klo + i];
       }
       if (threadIdx.x == 0) s_rel[s] = 0x7fffffff;  // sentinel
       __syncthreads();
@@ -286,56 +314,75 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
           } else {
             // many zero-degree frontier entries: search the global scan directly
             const OffT e = e0 + er;
-            const int32_t kk = binsearch_maxle(in.cum, (int64_t)klo, (int64_t)s_kend + 1, e);
-            col[j] = in.base[kk] + e;
-            uu[j] = in.v[kk];
+            const int32_t kk = binsearch_maxle(io.in.cum, (int64_t)klo, (int64_t)kend + 1, e);
+            col[j] = io.in.base[kk] + e;
+            uu[j] = io.in.v[kk];
           }
         }
       }
     }
 #pragma unroll
-    for (int j = 0; j < E; ++j) vv[j] = ok[j] ? ld_nc(a.cols + col[j]) : 0;
+    for (int j = 0; j < E; ++j) vv[j] = ok[j] ? ld_nc(cols + col[j]) : 0;
     uint32_t bits[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      if (ok[j] && (uint32_t)vv[j] >= (uint64_t)a.n) {
-        atomicOr(&ctl->error, kErrColumnRange);
+      if (ok[j] && (uint32_t)vv[j] >= (uint64_t)n) {
+        atomicOr(err, kErrColumnRange);
         ok[j] = false;
       }
-      bits[j] = ok[j] ? a.bitmap[vv[j] >> 5] : 0xffffffffu;
+      bits[j] = ok[j] ? bitmap[vv[j] >> 5] : 0xffffffffu;
     }
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int32_t v = vv[j];
       const uint32_t m = 1u << (v & 31);
       bool claimed = false;
-      if (!(bits[j] & m)) claimed = !(atomicOr(a.bitmap + (v >> 5), m) & m);
+      if (!(bits[j] & m)) claimed = !(atomicOr(bitmap + (v >> 5), m) & m);
       int32_t deg = 0;
       if (claimed) {
-        levels[v] = L;
-        parents[v] = uu[j];
-        deg = (int32_t)(a.off[v + 1] - a.off[v]);
+        io.levels[v] = L;
+        io.parents[v] = uu[j];
+        deg = (int32_t)(off[v + 1] - off[v]);
+        if (io.fbm_out) atomicOr(io.fbm_out + (v >> 5), m);
       }
-      const unsigned ball = __ballot_sync(0xffffffffu, claimed);
-      if (ball) {
-        const int leader = __ffs(ball) - 1;
-        int pos = 0;
-        if (lane == leader) pos = atomicAdd(&s_nclaim, __popc(ball));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (claimed) s_claim[pos + __popc(ball & lanemask_lt())] = make_int2(v, deg);
-      }
+      push_claim(claimed, v, deg, s_claim, &sh.nclaim);
     }
     __syncthreads();
-    const int nc = s_nclaim;
+    const int nc = sh.nclaim;
     if (nc > CLAIM - T) {
-      flush_claims<OffT, BLOCK, E, CLAIM>(a, out, chunk_out, nxt, s_claim, nc, s_warp, &s_resv);
+      flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
       __syncthreads();
-      if (threadIdx.x == 0) s_nclaim = 0;
+      if (threadIdx.x == 0) sh.nclaim = 0;
     }
   }
   __syncthreads();
-  const int nc = s_nclaim;
-  if (nc > 0) flush_claims<OffT, BLOCK, E, CLAIM>(a, out, chunk_out, nxt, s_claim, nc, s_warp, &s_resv);
+  const int nc = sh.nclaim;
+  if (nc > 0) flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
+  __syncthreads();
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+__global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ExpandShared<OffT> sh;
+  Ctl* ctl = a.ctl;
+  const int L = *(volatile int*)&ctl->level;
+  const int cur = (L - 1) & 1, nxt = cur ^ 1;
+  const unsigned long long pc = *(volatile unsigned long long*)&ctl->counter[cur];
+  LevelIO<OffT> io;
+  io.in = a.fr[cur];
+  io.out = a.fr[nxt];
+  io.chunk_in = a.chunk[cur];
+  io.chunk_out = a.chunk[nxt];
+  io.counter_out = &ctl->counter[nxt];
+  io.levels = *(int32_t* volatile*)&ctl->levels;
+  io.parents = *(int32_t* volatile*)&ctl->parents;
+  io.fbm_out = nullptr;
+  io.L = L;
+  io.nf = a.pk.count(pc);
+  io.r = (OffT)a.pk.edges(pc);
+  td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, smem, sh, blockIdx.x,
+                                  gridDim.x);
 
   // Level epilogue by the last CTA to finish: close the level and prepare the next.
   if (threadIdx.x == 0) {
@@ -345,7 +392,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
       __threadfence();
       const unsigned long long pn = atomicAdd(&ctl->counter[nxt], 0ull);
       const long long nn = a.pk.count(pn);
-      ctl->edges2 += (long long)r;
+      ctl->edges2 += (long long)io.r;
       if (nn > 0) {
         ctl->depth += 1;
         ctl->reached += nn;
@@ -356,6 +403,218 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
       ctl->cont = nn > 0;
       if (a.use_cond) cudaGraphSetConditional(a.cond, nn > 0 ? 1u : 0u);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Persistent search: every level in one cooperative launch, with a grid barrier between
+// levels and a per-level choice between the top-down step above and a bottom-up step.
+
+// Grid barrier (sense reversal) with a bounded wait: after kBarrierSpinLimit polls the CTA
+// records kErrTimeout and leaves; the search then stops at the next level boundary.
+constexpr long long kBarrierSpinLimit = 1ll << 27;
+
+__device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &c->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      c->bar_count = 0;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicOr(&c->error, kErrTimeout);
+          break;
+        }
+        if (spins > 64) __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// One bottom-up level (Beamer et al.'s step, the paper's related work, Sec. 6): every
+// unvisited vertex scans its row for a neighbour in the current frontier (a bitmap) and
+// stops at the first; warp w owns visited word w (32 vertices), so no atomics are needed
+// on the visited and next-frontier bitmaps. Claimed vertices are appended to the next
+// frontier queue exactly as in the top-down step.
+template <typename OffT, int BLOCK, int CLAIM>
+__device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
+                         const uint32_t* __restrict__ fbm_in, int64_t n, Packed pk, const LevelIO<OffT>& io,
+                         int2* s_claim, ExpandShared<OffT>& sh, int64_t cta0, int64_t cstride) {
+  constexpr int WARPS = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nwords = (n + 31) / 32;
+  const int64_t rounds = (nwords + WARPS - 1) / WARPS;  // CTA-rounds of WARPS words
+  const int L = io.L;
+  if (threadIdx.x == 0) sh.nclaim = 0;
+  __syncthreads();
+  for (int64_t rd = cta0; rd < rounds; rd += cstride) {
+    const int64_t w = rd * WARPS + warp;
+    bool found = false;
+    int32_t v = 0, parent = 0, deg = 0;
+    if (w < nwords) {
+      const uint32_t vis = bitmap[w];
+      v = (int32_t)(w * 32 + lane);
+      if (v < n && !((vis >> lane) & 1u)) {
+        const OffT b = off[v], e = off[v + 1];
+        deg = (int32_t)(e - b);
+        OffT i = b;
+        for (; i + 4 <= e && !found; i += 4) {
+          int32_t u4[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) u4[j] = ld_nc(cols + i + j);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t u = (uint32_t)u4[j];
+            if (!found && u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
+              found = true;
+              parent = (int32_t)u;
+            }
+          }
+        }
+        for (; i < e && !found; ++i) {
+          const uint32_t u = (uint32_t)ld_nc(cols + i);
+          if (u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
+            found = true;
+            parent = (int32_t)u;
+          }
+        }
+      }
+    }
+    const unsigned claimed = __ballot_sync(0xffffffffu, found);
+    if (found) {
+      io.levels[v] = L;
+      io.parents[v] = parent;
+    }
+    if (lane == 0 && claimed) {
+      bitmap[w] |= claimed;
+      io.fbm_out[w] = claimed;
+    }
+    push_claim(found, v, deg, s_claim, &sh.nclaim);
+    __syncthreads();
+    const int nc = sh.nclaim;
+    if (nc > CLAIM - BLOCK) {
+      flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
+      __syncthreads();
+      if (threadIdx.x == 0) sh.nclaim = 0;
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  const int nc = sh.nclaim;
+  if (nc > 0) flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
+  __syncthreads();
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bfs_persistent(PersistArgs<OffT> a) {
+  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ExpandShared<OffT> sh;
+  PCtl* c = a.ctl;
+  int2* s_claim = reinterpret_cast<int2*>(smem + S::off_claim);
+  const int64_t nwords = (a.n + 31) / 32;
+  const int64_t gtid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * BLOCK;
+  long long seen_deg = 0;          // degree sum of every frontier so far (same on all CTAs)
+  long long prev_nf = 0;
+  bool bottom_up = false;
+  for (int it = 0;; ++it) {
+    const int cur3 = it % 3, nxt3 = (it + 1) % 3, old3 = (it + 2) % 3;
+    const unsigned long long pc = *(volatile unsigned long long*)&c->counter[cur3];
+    const long long nf = a.pk.count(pc);
+    const long long r = a.pk.edges(pc);
+    if (nf == 0 || (*(volatile unsigned*)&c->error & kErrTimeout)) break;
+    seen_deg += r;
+    // direction choice (Beamer's heuristic): bottom-up while the frontier's edges are a
+    // large share of the unexplored ones, back to top-down once the frontier shrinks
+    const long long unexplored = a.nnz - seen_deg + r;
+    if (a.allow_bottom_up) {
+      if (!bottom_up)
+        bottom_up = r * (long long)a.alpha > unexplored && nf > prev_nf;
+      else
+        bottom_up = !(nf * (long long)a.beta < a.n && nf < prev_nf);
+    }
+    prev_nf = nf;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->counter[old3] = 0;
+      c->steps_bottom_up += bottom_up ? 1 : 0;
+    }
+    for (int64_t w = gtid; w < nwords; w += gstride) a.fbm[old3][w] = 0u;  // collects level it + 2
+    LevelIO<OffT> io;
+    io.in = a.fr[it & 1];
+    io.out = a.fr[(it + 1) & 1];
+    io.chunk_in = a.chunk[it & 1];
+    io.chunk_out = a.chunk[(it + 1) & 1];
+    io.counter_out = &c->counter[nxt3];
+    io.levels = a.levels;
+    io.parents = a.parents;
+    io.fbm_out = a.fbm[nxt3];
+    io.L = it + 1;
+    io.nf = nf;
+    io.r = (OffT)r;
+    if (bottom_up)
+      bu_level<OffT, BLOCK, CLAIM>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, s_claim, sh, blockIdx.x,
+                                   gridDim.x);
+    else
+      td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &c->error, io, smem, sh, blockIdx.x,
+                                      gridDim.x);
+    grid_barrier(c, gridDim.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const long long nn = a.pk.count(*(volatile unsigned long long*)&c->counter[nxt3]);
+      c->edges2 += r;
+      if (nn > 0) {
+        c->depth += 1;
+        c->reached += nn;
+      }
+    }
+  }
+}
+
+template <typename OffT>
+__global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t root, int32_t* levels,
+                               int32_t* parents, uint32_t* bitmap, uint32_t* fbm0, uint32_t* fbm1, uint32_t* fbm2,
+                               FrontierBuf<OffT> f0, int32_t* chunk0, PCtl* c, Packed pk) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n; i += stride) {
+    const bool is_root = i == root;
+    levels[i] = is_root ? 0 : -1;
+    parents[i] = is_root ? root : -1;
+  }
+  const int64_t nw = (n + 31) / 32;
+  for (int64_t w = tid; w < nw; w += stride) {
+    const uint32_t rb = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
+    bitmap[w] = rb;
+    fbm0[w] = rb;
+    fbm1[w] = 0u;
+    fbm2[w] = 0u;
+  }
+  const OffT o0 = off[root], deg = off[root + 1] - o0;
+  const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
+  for (int64_t ch = tid; ch < nchunks; ch += stride) chunk0[ch] = 0;
+  if (tid == 0) {
+    f0.v[0] = root;
+    f0.cum[0] = 0;
+    f0.base[0] = o0;
+    c->counter[0] = pk.make(1, (long long)deg);
+    c->counter[1] = 0;
+    c->counter[2] = 0;
+    c->bar_count = 0;
+    c->bar_gen = 0;
+    c->error = 0;
+    c->depth = 1;
+    c->reached = 1;
+    c->edges2 = 0;
+    c->steps_bottom_up = 0;
   }
 }
 
@@ -435,6 +694,63 @@ const ExpandShape kExpandShapes[] = {
 };
 const int kNumExpandShapes = sizeof(kExpandShapes) / sizeof(kExpandShapes[0]);
 
+template <typename OffT, int BLOCK, int E, int CLAIM>
+static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
+  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  auto kern = k_bfs_persistent<OffT, BLOCK, E, CLAIM>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  PersistArgs<OffT> copy = a;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(BLOCK), params, S::bytes,
+                                     st);
+}
+
+// All CTAs of a cooperative launch must be resident at once: occupancy x SMs.
+template <typename OffT, int BLOCK, int E, int CLAIM>
+static int persistent_grid_t(int num_sms) {
+  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  auto kern = k_bfs_persistent<OffT, BLOCK, E, CLAIM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
+  return std::max(1, per_sm) * num_sms;
+}
+
+template <typename OffT>
+cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
+  switch (shape) {
+#define X(id, b, e, c) \
+  case id: return launch_persistent_t<OffT, b, e, c>(a, grid, st);
+    GBFS_EXPAND_SHAPES(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename OffT>
+int persistent_grid(int shape, int num_sms) {
+  switch (shape) {
+#define X(id, b, e, c) \
+  case id: return persistent_grid_t<OffT, b, e, c>(num_sms);
+    GBFS_EXPAND_SHAPES(X)
+#undef X
+  }
+  return num_sms;
+}
+
+template <typename OffT>
+void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
+                         cudaStream_t st) {
+  k_init_persist<OffT><<<g.num_sms * 8, 256, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, levels,
+                                                      parents, ws.bitmap, ws.fbm[0], ws.fbm[1], ws.fbm[2],
+                                                      ws.fr<OffT>(0), ws.chunk[0], ws.pctl, g.pk);
+}
+
 template <typename OffT>
 cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
@@ -467,5 +783,11 @@ template cudaError_t launch_expand<int32_t>(int, const ExpandArgs<int32_t>&, int
 template cudaError_t launch_expand<int64_t>(int, const ExpandArgs<int64_t>&, int, cudaStream_t);
 template int expand_grid<int32_t>(int, int);
 template int expand_grid<int64_t>(int, int);
+template cudaError_t launch_persistent<int32_t>(int, const PersistArgs<int32_t>&, int, cudaStream_t);
+template cudaError_t launch_persistent<int64_t>(int, const PersistArgs<int64_t>&, int, cudaStream_t);
+template int persistent_grid<int32_t>(int, int);
+template int persistent_grid<int64_t>(int, int);
+template void launch_init_persist<int32_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
+template void launch_init_persist<int64_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
 
 }  // namespace gbfs

@@ -62,6 +62,7 @@ struct Wave {
   BatchBufs b;
   cudaStream_t stream = nullptr;
   int grid = 0;
+  int shape = 0;
   bool active = false;
   int t = 0;                          // frontier index the next expansion reads
   uint64_t used = 0;                  // occupied slot bits
@@ -116,7 +117,7 @@ static void free_wave(Wave* w) {
 template <typename OffT>
 static void wave_launch_level(Wave* w) {
   BatchArgs<OffT> a = make_batch_args<OffT>(w->g, w->b);
-  launch_batch_expand<OffT>(a, w->grid, w->stream);
+  launch_batch_expand<OffT>(w->shape, a, w->grid, w->stream);
 }
 
 template <typename OffT>
@@ -417,7 +418,9 @@ GBFS_API bfs_status bfs_serve_add_graph(bfs_server_t S, bfs_graph_t G, int* grap
     w->slots_host->lvl[b] = w->slots_host->par[b] = nullptr;
     w->slots_host->start[b] = 0;
   }
-  w->grid = w->g.off64 ? batch_expand_grid<int64_t>(w->g.num_sms) : batch_expand_grid<int32_t>(w->g.num_sms);
+  w->shape = G->batch_shape;
+  w->grid = w->g.off64 ? batch_expand_grid<int64_t>(w->shape, w->g.num_sms)
+                       : batch_expand_grid<int32_t>(w->shape, w->g.num_sms);
   S->device = G->g.device;
   S->mem_fixed += need;
   S->mem_peak = std::max(S->mem_peak, S->mem_fixed + S->mem_used);

@@ -28,9 +28,14 @@ struct bfs_graph_s {
   gbfs::GraphDev g;
   gbfs::SingleWs ws;
   std::mutex mu;
-  int shape = gbfs::kDefaultShape;
+  int shape = gbfs::kDefaultShape;        // single-source expansion shape (kExpandShapes)
   int grid = 0;
+  int batch_shape = 0;                     // multi-source expansion shape (kBatchShapes)
   bool host_loop = false;
+  int loop_mode = 1;        // BFS_LOOP_PERSISTENT / BFS_LOOP_GRAPH / BFS_LOOP_HOST
+  int bottom_up = 0;        // allow bottom-up levels (persistent loop only)
+  int alpha = 14, beta = 24;
+  int pgrid = 0;            // CTAs of the persistent kernel
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   cudaEvent_t last_done = nullptr;  // completion of the last call that used the work buffers
@@ -39,5 +44,7 @@ struct bfs_graph_s {
 
 namespace gbfs {
 bfs_status ensure_single_ws(bfs_graph_s* G);
+void set_batch_shape(bfs_graph_s* G, int shape);
+void set_single_shape(bfs_graph_s* G, int shape);
 void destroy_batch_state(bfs_graph_s* G);
 }  // namespace gbfs

@@ -9,7 +9,7 @@
 namespace gbfs {
 
 // Device error bits, OR-ed into Ctl::error by kernels and read by the host after a search.
-enum : unsigned { kErrColumnRange = 1u, kErrFrontierRange = 2u, kErrCounterOverflow = 4u };
+enum : unsigned { kErrColumnRange = 1u, kErrFrontierRange = 2u, kErrCounterOverflow = 4u, kErrTimeout = 8u };
 
 // The next frontier's size and edge total are reserved together by one 64-bit atomicAdd
 // on a packed word (count << shift) | edges, so the slot order and the exclusive degree
@@ -47,6 +47,20 @@ struct Ctl {
   int cont;                  // 1 while the next frontier is non-empty
   int32_t* levels;           // output arrays of the running search
   int32_t* parents;
+};
+
+// Control block of a persistent (one-launch) search: counters rotate by 3 so that level
+// it reads counter[it % 3], fills counter[(it + 1) % 3] and clears counter[(it + 2) % 3].
+struct PCtl {
+  unsigned long long counter[3];
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned int error;
+  int depth;
+  long long reached;
+  long long edges2;
+  int steps_bottom_up;
+  int pad;
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -39,6 +39,9 @@ struct SingleWs {
   int32_t* host_levels = nullptr;   // device staging when the caller passes host outputs
   int32_t* host_parents = nullptr;
   Ctl* ctl_host = nullptr;          // pinned mirror of ctl
+  uint32_t* fbm[3] = {nullptr, nullptr, nullptr};  // frontier bitmaps (persistent search)
+  PCtl* pctl = nullptr;
+  PCtl* pctl_host = nullptr;        // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_mid = nullptr;
 
   template <typename OffT>
@@ -61,6 +64,25 @@ struct ExpandArgs {
   int use_cond;
 };
 
+template <typename OffT>
+struct PersistArgs {
+  const OffT* off;
+  const int32_t* cols;
+  uint32_t* bitmap;
+  uint32_t* fbm[3];
+  int64_t n;
+  int64_t nnz;
+  FrontierBuf<OffT> fr[2];
+  int32_t* chunk[2];
+  PCtl* ctl;
+  Packed pk;
+  int32_t* levels;
+  int32_t* parents;
+  int alpha;            // switch to bottom-up when frontier edges * alpha > unexplored edges
+  int beta;             // back to top-down when frontier vertices * beta < n (and shrinking)
+  int allow_bottom_up;
+};
+
 struct ExpandShape {
   int id, block, e, claim;
 };
@@ -77,5 +99,12 @@ template <typename OffT>
 cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaStream_t st);
 template <typename OffT>
 int expand_grid(int shape, int num_sms);
+template <typename OffT>
+void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
+                         cudaStream_t st);
+template <typename OffT>
+cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, cudaStream_t st);
+template <typename OffT>
+int persistent_grid(int shape, int num_sms);
 
 }  // namespace gbfs

@@ -99,3 +99,38 @@ def test_serve_host_side_checks(capi):
     finally:
         capi.bfs_serve_destroy(srv)
     assert capi.lib().bfs_serve_destroy(None) == 0
+
+
+def test_shape_tables(capi):
+    for kind in (capi.BFS_KERNEL_SINGLE, capi.BFS_KERNEL_BATCH):
+        n = capi.bfs_shape_count(kind)
+        assert n >= 2
+        for s in range(n):
+            info = capi.bfs_shape_info(kind, s)
+            assert info["block"] % 32 == 0 and info["edges_per_thread"] >= 1
+            assert info["claim_buffer"] >= info["block"] * info["edges_per_thread"]
+    assert capi.bfs_shape_count(7) == 0
+    with pytest.raises(capi.BfsError):
+        capi.bfs_shape_info(0, 99)
+
+
+def test_autotune_cache_roundtrip(capi, monkeypatch, tmp_path):
+    """Tunes once per key, then applies the cached shape without timing again."""
+    from paper_1408_1605_gb300 import autotune
+
+    monkeypatch.setenv("GBFS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    calls = {"tune": 0, "set": []}
+
+    def fake_tune(graph, kind, roots, levels, parents, stream=None):
+        calls["tune"] += 1
+        return 1, [3.0, 1.0]
+
+    monkeypatch.setattr(capi, "bfs_tune", fake_tune)
+    monkeypatch.setattr(capi, "bfs_graph_set_shape", lambda g, k, s: calls["set"].append((k, s)))
+    r1 = autotune.apply_or_tune(0, capi.BFS_KERNEL_SINGLE, "rmat", 1 << 20, [1], None, None)
+    assert r1["shape"] == 1 and not r1["cached"] and calls["tune"] == 1
+    r2 = autotune.apply_or_tune(0, capi.BFS_KERNEL_SINGLE, "rmat", (1 << 20) + 5, [1], None, None)
+    assert r2["cached"] and calls["tune"] == 1 and calls["set"] == [(0, 1)]
+    r3 = autotune.apply_or_tune(0, capi.BFS_KERNEL_BATCH, "rmat", 1 << 20, [1], None, None)
+    assert not r3["cached"] and calls["tune"] == 2
+    assert autotune.key(0, "grid", 1 << 24, "X") == "X|single|grid|s24"
