@@ -277,12 +277,15 @@ GBFS_API bfs_status bfs_shape_info(int kind, int shape, int *block, int *edges_p
 GBFS_API bfs_status bfs_graph_set_shape(bfs_graph_t g, int kind, int shape);
 GBFS_API bfs_status bfs_graph_get_shape(bfs_graph_t g, int kind, int *shape);
 
-/* Times every compiled shape of `kind` on this graph and keeps the fastest.
- *   BFS_KERNEL_SINGLE: one warm-up search, then one bfs_run per root; levels / parents as
- *     for bfs_run; ms_per_shape[s] = mean device ms per root.
- *   BFS_KERNEL_BATCH: n_roots <= 64; one warm-up wave and one timed wave per shape;
- *     levels / parents as for bfs_run_batch; ms_per_shape[s] = device ms per wave.
- * ms_per_shape: NULL or double[bfs_shape_count(kind)]; best_shape: NULL or the choice.
+/* Times the candidates of `kind` on this graph and keeps the fastest.
+ *   BFS_KERNEL_SINGLE: candidates c = loop x shape: c < count uses BFS_LOOP_GRAPH with shape
+ *     c, c >= count BFS_LOOP_PERSISTENT with shape c - count (with BFS_OPT_BOTTOM_UP set,
+ *     only the persistent ones; the others report -1). One warm-up search, then one
+ *     bfs_run per root; ms_per_shape[c] = mean device ms per root. The winner's loop mode
+ *     and shape are set on the graph. ms_per_shape: NULL or double[2 * count].
+ *   BFS_KERNEL_BATCH: candidates = shapes; n_roots <= 64; one warm-up wave and one timed
+ *     wave per shape; ms_per_shape[s] = device ms per wave (double[count]).
+ * count = bfs_shape_count(kind); best_shape: NULL or the winning candidate index.
  * Other calls on the graph must not run meanwhile. Failures as for bfs_run /
  * bfs_run_batch. */
 GBFS_API bfs_status bfs_tune(bfs_graph_t g, int kind, const int32_t *roots, int n_roots, int32_t *levels,

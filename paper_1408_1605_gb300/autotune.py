@@ -57,11 +57,17 @@ def apply_or_tune(graph: int, kind: int, graph_class: str, n_vertices: int, root
     k = key(kind, graph_class, n_vertices)
     db = _load()
     rec = db.get(k)
-    if rec is not None and not force and 0 <= rec.get("shape", -1) < capi.bfs_shape_count(kind):
+    count = capi.bfs_shape_count(kind)
+    if rec is not None and not force and 0 <= rec.get("shape", -1) < count:
+        if kind == capi.BFS_KERNEL_SINGLE and "loop" in rec:
+            capi.bfs_graph_set_option(graph, capi.BFS_OPT_LOOP, rec["loop"])
         capi.bfs_graph_set_shape(graph, kind, rec["shape"])
         return dict(rec, cached=True)
     best, ms = capi.bfs_tune(graph, kind, roots, levels, parents)
-    rec = {"shape": best, "ms": ms, "shape_info": capi.bfs_shape_info(kind, best), "when": time.time()}
+    shape = best % count
+    rec = {"shape": shape, "ms": ms, "shape_info": capi.bfs_shape_info(kind, shape), "when": time.time()}
+    if kind == capi.BFS_KERNEL_SINGLE:
+        rec["loop"] = capi.BFS_LOOP_GRAPH if best < count else capi.BFS_LOOP_PERSISTENT
     db = _load()
     db[k] = rec
     _store(db)

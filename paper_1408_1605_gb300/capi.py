@@ -291,11 +291,12 @@ def bfs_graph_get_shape(graph: int, kind: int) -> int:
 
 
 def bfs_tune(graph: int, kind: int, roots, levels, parents, stream=None):
-    """Returns (best_shape, [ms per shape])."""
+    """Returns (best candidate, [ms per candidate]); single-source candidates are
+    (graph loop, shape 0..count-1) then (persistent loop, shape 0..count-1)."""
     import numpy as np
 
     r = np.ascontiguousarray(roots, dtype=np.int32)
-    n = bfs_shape_count(kind)
+    n = bfs_shape_count(kind) * (2 if kind == BFS_KERNEL_SINGLE else 1)
     ms = (ctypes.c_double * max(n, 1))()
     best = ctypes.c_int(-1)
     check(lib().bfs_tune(graph, int(kind), r.ctypes.data, int(r.size), ptr(levels), ptr(parents),

@@ -27,9 +27,23 @@ struct BatchCtl {
   int cont;                       // next frontier non-empty
   long long prev_count;           // size of frontier t - 1
   unsigned int error;
-  int pad;
+  unsigned int emit_done;         // CTAs finished in the emit kernel (last-CTA detection)
   unsigned long long alive[2];    // OR of the masks claimed by the running expansion (next parity)
+  unsigned long long ovf_count;   // parent events that did not fit the per-vertex slots
 };
+
+// Parent event of a claim: vertex u's edge claimed the bits `mask` of the claimed vertex.
+struct ClaimEvent {
+  int32_t u;
+  int32_t pad;
+  unsigned long long mask;
+};
+struct OvfEvent {
+  int32_t v;
+  int32_t u;
+  unsigned long long mask;
+};
+constexpr int kEventSlots = 4;  // per-vertex event slots per level
 
 template <typename OffT>
 struct BatchArgs {
@@ -44,6 +58,10 @@ struct BatchArgs {
   int32_t* chunk[2];
   BatchCtl* ctl;
   const WaveSlots* slots;
+  int32_t* evc;                   // events recorded per vertex this level
+  ClaimEvent* ev;                 // [n][kEventSlots]
+  OvfEvent* ovf;                  // events beyond the slots
+  long long ovf_cap;
   Packed pk;
   cudaGraphConditionalHandle cond;
   int use_cond;
@@ -63,6 +81,10 @@ struct BatchBufs {
   WaveSlots* slots = nullptr;       // device
   long long* stats = nullptr;       // device: per slot [edges2, reached, depth]
   int32_t* roots_dev = nullptr;     // device: (vertex, mask lo, mask hi) per distinct root
+  int32_t* evc = nullptr;
+  ClaimEvent* ev = nullptr;
+  OvfEvent* ovf = nullptr;
+  long long ovf_cap = 0;
 };
 
 struct RootSeed {
@@ -88,6 +110,10 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   }
   a.ctl = b.ctl;
   a.slots = b.slots;
+  a.evc = b.evc;
+  a.ev = b.ev;
+  a.ovf = b.ovf;
+  a.ovf_cap = b.ovf_cap;
   a.pk = g.pk;
   a.use_cond = 0;
   return a;
@@ -116,6 +142,9 @@ cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, c
 template <typename OffT>
 int batch_expand_grid(int shape, int num_sms);
 void launch_fill(int32_t* p, int64_t count, int32_t value, int num_sms, cudaStream_t st);
+// Writes the levels and parents of the roots' vertices claimed by the last expansion.
+template <typename OffT>
+void launch_batch_emit(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int n_slots, long long* stats,
                         int num_sms, cudaStream_t st);

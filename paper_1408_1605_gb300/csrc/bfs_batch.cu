@@ -73,12 +73,17 @@ void free_batch_bufs(BatchBufs& b) {
   cudaFree(b.slots);
   cudaFree(b.stats);
   cudaFree(b.roots_dev);
+  cudaFree(b.evc);
+  cudaFree(b.ev);
+  cudaFree(b.ovf);
   b = BatchBufs{};
 }
 
 size_t batch_bufs_bytes(const GraphDev& g) {
   const size_t osz = g.off64 ? 8 : 4;
-  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz) + 2 * 4 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
+  const size_t ovf_cap = (size_t)g.n / 4 + 65536;
+  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * kEventSlots) +
+         ovf_cap * sizeof(OvfEvent) + 2 * 4 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
 }
 
 cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b) {
@@ -98,6 +103,11 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b) {
   if (e == cudaSuccess) e = dalloc(&b.slots, 1);
   if (e == cudaSuccess) e = dalloc(&b.stats, 3 * kMaxWave);
   if (e == cudaSuccess) e = dalloc(&b.roots_dev, 4 * kMaxWave);
+  b.ovf_cap = g.n / 4 + 65536;
+  if (e == cudaSuccess) e = dalloc(&b.evc, (size_t)g.n);
+  if (e == cudaSuccess) e = dalloc(&b.ev, (size_t)g.n * kEventSlots);
+  if (e == cudaSuccess) e = dalloc(&b.ovf, (size_t)b.ovf_cap);
+  if (e == cudaSuccess) e = cudaMemset(b.evc, 0, sizeof(int32_t) * (size_t)g.n);
   if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
   if (e != cudaSuccess) {
     free_batch_bufs(b);
@@ -166,6 +176,7 @@ static bfs_status build_batch_graph(bfs_graph_s* G) {
   }
   {
     cudaError_t le = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, cs);
+    launch_batch_emit<OffT>(a, G->g.num_sms, cs);
     e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
     if (le != cudaSuccess) e = le;
@@ -243,6 +254,7 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
     for (int64_t it = 0; it <= g.n; ++it) {
       if ((e = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, st)) != cudaSuccess)
         return cuda_fail(e, "batch expand");
+      launch_batch_emit<OffT>(a, g.num_sms, st);
       if ((e = cudaMemcpyAsync(S->ctl_host, S->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "batch level sync");

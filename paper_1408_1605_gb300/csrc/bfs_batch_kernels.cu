@@ -46,6 +46,11 @@ __global__ void k_batch_clear(BatchArgs<OffT> a) {
     a.fmask[0][v] = 0ull;
     a.fmask[1][v] = 0ull;
     a.fmask[2][v] = 0ull;
+    a.evc[v] = 0;
+  }
+  if (tid == 0) {
+    a.ctl->ovf_count = 0;
+    a.ctl->emit_done = 0;
   }
 }
 
@@ -284,10 +289,24 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
       bool first = false;
       int32_t deg = 0;
       if (claimed) {
-        for (unsigned long long bits = claimed; bits; bits &= bits - 1) {
-          const int b = __ffsll((long long)bits) - 1;
-          s_lvl[b][v] = L - s_start[b];
-          s_par[b][v] = uu[j];
+        // Parent event: the outputs are written in vertex order after the level (emit).
+        const int slot = atomicAdd(a.evc + v, 1);
+        if (slot < kEventSlots) {
+          ClaimEvent ce;
+          ce.u = uu[j];
+          ce.pad = 0;
+          ce.mask = claimed;
+          a.ev[(size_t)v * kEventSlots + slot] = ce;
+        } else {
+          const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
+          if ((long long)o < a.ovf_cap) {
+            a.ovf[o] = OvfEvent{v, uu[j], claimed};
+          } else {
+            for (unsigned long long bits = claimed; bits; bits &= bits - 1) {  // no room: write now
+              const int b = __ffsll((long long)bits) - 1;
+              s_par[b][v] = uu[j];
+            }
+          }
         }
         atomicOr(&s_alive, claimed);
         first = atomicOr(Fn + v, claimed) == 0ull;
@@ -331,6 +350,103 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
       if (a.use_cond) cudaGraphSetConditional(a.cond, nn > 0 ? 1u : 0u);
     }
   }
+}
+
+// After the expansion of frontier t (wave level L = t + 1): for every vertex v claimed in
+// it, F_{t+1}[v] holds the bits claimed and the per-vertex events hold their claimers.
+// Levels (L - start[b]) and parents are written in vertex order: a warp takes 32
+// consecutive vertices and loops over the union of their claimed bits, so each store
+// covers 32 consecutive entries of one root's row. When few vertices were claimed the
+// vertices come from the next frontier list instead (scattered, cheaper than a full pass).
+// Events that did not fit the per-vertex slots are applied last; the last CTA resets the
+// overflow count.
+template <typename OffT>
+__global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
+  __shared__ int32_t* s_lvl[kMaxWave];
+  __shared__ int32_t* s_par[kMaxWave];
+  __shared__ int32_t s_start[kMaxWave];
+  BatchCtl* ctl = a.ctl;
+  const int Lnext = *(volatile int*)&ctl->level;  // already advanced by the expansion
+  const int L = Lnext - 1;
+  const int t = L - 1;
+  const int nxt = (t & 1) ^ 1, q3n = (t + 1) % 3;
+  const long long nn = a.pk.count(*(volatile unsigned long long*)&ctl->counter[nxt]);
+  if (threadIdx.x < kMaxWave) {
+    s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
+    s_par[threadIdx.x] = a.slots->par[threadIdx.x];
+    s_start[threadIdx.x] = a.slots->start[threadIdx.x];
+  }
+  __syncthreads();
+  const unsigned long long* Fn = a.fmask[q3n];
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool ordered = nn * 32 > a.n;
+  const int64_t items = ordered ? (a.n + 31) / 32 : (nn + 31) / 32;
+  for (int64_t w = gwarp; w < items; w += nwarps) {
+    int32_t v = -1;
+    if (ordered) {
+      const int64_t vv = w * 32 + lane;
+      if (vv < a.n) v = (int32_t)vv;
+    } else {
+      const int64_t k = w * 32 + lane;
+      if (k < nn) v = a.qv[q3n][k];
+    }
+    const unsigned long long f = v >= 0 ? Fn[v] : 0ull;
+    int ne = 0;
+    int32_t eu[kEventSlots];
+    unsigned long long em[kEventSlots];
+    if (f) {
+      ne = min(a.evc[v], kEventSlots);
+#pragma unroll
+      for (int k = 0; k < kEventSlots; ++k) {
+        if (k < ne) {
+          const ClaimEvent ce = a.ev[(size_t)v * kEventSlots + k];
+          eu[k] = ce.u;
+          em[k] = ce.mask;
+        } else {
+          eu[k] = 0;
+          em[k] = 0ull;
+        }
+      }
+      a.evc[v] = 0;
+    }
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)f);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(f >> 32));
+    unsigned long long any = ((unsigned long long)hi << 32) | lo;
+    while (any) {
+      const int b = __ffsll((long long)any) - 1;
+      any &= any - 1;
+      if ((f >> b) & 1ull) {
+        s_lvl[b][v] = L - s_start[b];
+#pragma unroll
+        for (int k = 0; k < kEventSlots; ++k)
+          if ((em[k] >> b) & 1ull) s_par[b][v] = eu[k];
+      }
+    }
+  }
+  // overflow events (after every slot event of the level is consumed above)
+  const long long novf = min((long long)*(volatile unsigned long long*)&ctl->ovf_count, a.ovf_cap);
+  for (long long o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < novf; o += (int64_t)gridDim.x * blockDim.x) {
+    const OvfEvent e = a.ovf[o];
+    for (unsigned long long bits = e.mask; bits; bits &= bits - 1) {
+      const int b = __ffsll((long long)bits) - 1;
+      s_par[b][e.v] = e.u;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->emit_done, 1u) == gridDim.x - 1) {
+      ctl->ovf_count = 0;
+      ctl->emit_done = 0;
+    }
+  }
+}
+
+template <typename OffT>
+void launch_batch_emit(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
+  k_batch_emit<OffT><<<num_sms * 8, 256, 0, st>>>(a);
 }
 
 template <typename OffT, int BLOCK, int E, int CLAIM>
@@ -489,6 +605,7 @@ void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long 
 
 #define INST(OffT)                                                                                          \
   template void launch_batch_clear<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
+  template void launch_batch_emit<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                        \
   template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
   template cudaError_t launch_batch_expand<OffT>(int, const BatchArgs<OffT>&, int, cudaStream_t);           \
   template int batch_expand_grid<OffT>(int, int);                                                           \

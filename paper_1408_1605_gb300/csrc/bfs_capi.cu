@@ -250,8 +250,9 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.alpha = G->alpha;
     pa.beta = G->beta;
     pa.allow_bottom_up = G->bottom_up;
-    if (!G->pgrid) G->pgrid = persistent_grid<OffT>(G->shape, G->g.num_sms);
-    if ((e = launch_persistent<OffT>(G->shape, pa, G->pgrid, st)) != cudaSuccess)
+    int& pg = G->pgrid[G->bottom_up ? 1 : 0];
+    if (!pg) pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
+    if ((e = launch_persistent<OffT>(G->shape, pa, pg, st)) != cudaSuccess)
       return cuda_fail(e, "persistent search kernel");
   } else if (G->host_loop) {
     ExpandArgs<OffT> a = make_args<OffT>(G, ws.bitmap);
@@ -335,7 +336,7 @@ static bfs_status expand_one(bfs_graph_s* G, const int32_t* front, int64_t nf, i
 // Switches the single-source expansion shape; the level-loop graph is rebuilt on next use.
 void set_single_shape(bfs_graph_s* G, int shape) {
   G->shape = shape;
-  G->pgrid = 0;
+  G->pgrid[0] = G->pgrid[1] = 0;
   G->grid = G->g.off64 ? expand_grid<int64_t>(shape, G->g.num_sms) : expand_grid<int32_t>(shape, G->g.num_sms);
   if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
   if (G->loop_graph) cudaGraphDestroy(G->loop_graph);

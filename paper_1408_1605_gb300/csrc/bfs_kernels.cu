@@ -514,8 +514,9 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
   __syncthreads();
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bfs_persistent(PersistArgs<OffT> a) {
+// WITH_BU = false compiles the top-down-only variant (fewer registers, more resident CTAs).
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WITH_BU>
+__global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_persistent(PersistArgs<OffT> a) {
   using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ExpandShared<OffT> sh;
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bfs_persistent(PersistA
     // direction choice (Beamer's heuristic): bottom-up while the frontier's edges are a
     // large share of the unexplored ones, back to top-down once the frontier shrinks
     const long long unexplored = a.nnz - seen_deg + r;
-    if (a.allow_bottom_up) {
+    if (WITH_BU && a.allow_bottom_up) {
       if (!bottom_up)
         bottom_up = r * (long long)a.alpha > unexplored && nf > prev_nf;
       else
@@ -548,7 +549,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bfs_persistent(PersistA
       c->counter[old3] = 0;
       c->steps_bottom_up += bottom_up ? 1 : 0;
     }
-    for (int64_t w = gtid; w < nwords; w += gstride) a.fbm[old3][w] = 0u;  // collects level it + 2
+    if (WITH_BU)
+      for (int64_t w = gtid; w < nwords; w += gstride) a.fbm[old3][w] = 0u;  // collects level it + 2
     LevelIO<OffT> io;
     io.in = a.fr[it & 1];
     io.out = a.fr[(it + 1) & 1];
@@ -557,11 +559,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bfs_persistent(PersistA
     io.counter_out = &c->counter[nxt3];
     io.levels = a.levels;
     io.parents = a.parents;
-    io.fbm_out = a.fbm[nxt3];
+    io.fbm_out = WITH_BU ? a.fbm[nxt3] : nullptr;
     io.L = it + 1;
     io.nf = nf;
     io.r = (OffT)r;
-    if (bottom_up)
+    if (WITH_BU && bottom_up)
       bu_level<OffT, BLOCK, CLAIM>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, s_claim, sh, blockIdx.x,
                                    gridDim.x);
     else
@@ -697,12 +699,13 @@ const int kNumExpandShapes = sizeof(kExpandShapes) / sizeof(kExpandShapes[0]);
 template <typename OffT, int BLOCK, int E, int CLAIM>
 static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
   using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = k_bfs_persistent<OffT, BLOCK, E, CLAIM>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  auto kern = a.allow_bottom_up ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true>
+                                : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false>;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[a.allow_bottom_up ? 1 : 0]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set[a.allow_bottom_up ? 1 : 0] = true;
   }
   PersistArgs<OffT> copy = a;
   void* params[] = {&copy};
@@ -712,9 +715,9 @@ static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cud
 
 // All CTAs of a cooperative launch must be resident at once: occupancy x SMs.
 template <typename OffT, int BLOCK, int E, int CLAIM>
-static int persistent_grid_t(int num_sms) {
+static int persistent_grid_t(int num_sms, bool with_bu) {
   using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = k_bfs_persistent<OffT, BLOCK, E, CLAIM>;
+  auto kern = with_bu ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true> : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
@@ -733,10 +736,10 @@ cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, c
 }
 
 template <typename OffT>
-int persistent_grid(int shape, int num_sms) {
+int persistent_grid(int shape, int num_sms, bool with_bu) {
   switch (shape) {
 #define X(id, b, e, c) \
-  case id: return persistent_grid_t<OffT, b, e, c>(num_sms);
+  case id: return persistent_grid_t<OffT, b, e, c>(num_sms, with_bu);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -785,8 +788,8 @@ template int expand_grid<int32_t>(int, int);
 template int expand_grid<int64_t>(int, int);
 template cudaError_t launch_persistent<int32_t>(int, const PersistArgs<int32_t>&, int, cudaStream_t);
 template cudaError_t launch_persistent<int64_t>(int, const PersistArgs<int64_t>&, int, cudaStream_t);
-template int persistent_grid<int32_t>(int, int);
-template int persistent_grid<int64_t>(int, int);
+template int persistent_grid<int32_t>(int, int, bool);
+template int persistent_grid<int64_t>(int, int, bool);
 template void launch_init_persist<int32_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
 template void launch_init_persist<int64_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
 

@@ -118,6 +118,7 @@ template <typename OffT>
 static void wave_launch_level(Wave* w) {
   BatchArgs<OffT> a = make_batch_args<OffT>(w->g, w->b);
   launch_batch_expand<OffT>(w->shape, a, w->grid, w->stream);
+  launch_batch_emit<OffT>(a, w->g.num_sms, w->stream);
 }
 
 template <typename OffT>

@@ -61,14 +61,25 @@ GBFS_API bfs_status bfs_tune(bfs_graph_t G, int kind, const int32_t* roots, int 
   if (kind != BFS_KERNEL_SINGLE && kind != BFS_KERNEL_BATCH) return fail(BFS_ERR_INVALID_ARG, "unknown kernel kind");
   if (kind == BFS_KERNEL_BATCH && n_roots > kMaxWave) return fail(BFS_ERR_INVALID_ARG, "n_roots outside [1, 64]");
   const int count = bfs_shape_count(kind);
+  // Single-source candidates: every shape under the CUDA-graph loop, then every shape under
+  // the persistent loop (only the latter when bottom-up levels are enabled).
+  const int n_cand = kind == BFS_KERNEL_SINGLE ? 2 * count : count;
+  const bool bu = G->bottom_up != 0;
   int best = -1;
   double best_ms = std::numeric_limits<double>::infinity();
   std::vector<bfs_stats> st((size_t)n_roots);
-  for (int s = 0; s < count; ++s) {
-    bfs_status r = bfs_graph_set_shape(G, kind, s);
-    if (r != BFS_OK) return r;
+  for (int c = 0; c < n_cand; ++c) {
+    const int s = c % count;
     double ms = 0;
+    bfs_status r;
     if (kind == BFS_KERNEL_SINGLE) {
+      const int loop = c < count ? BFS_LOOP_GRAPH : BFS_LOOP_PERSISTENT;
+      if (bu && loop == BFS_LOOP_GRAPH) {
+        if (ms_per_shape) ms_per_shape[c] = -1.0;  // not a candidate
+        continue;
+      }
+      if ((r = bfs_graph_set_option(G, BFS_OPT_LOOP, loop)) != BFS_OK) return r;
+      if ((r = bfs_graph_set_shape(G, kind, s)) != BFS_OK) return r;
       if ((r = bfs_run(G, roots[0], levels, parents, stream, st.data())) != BFS_OK) return r;  // warm-up
       for (int i = 0; i < n_roots; ++i) {
         if ((r = bfs_run(G, roots[i], levels, parents, stream, st.data())) != BFS_OK) return r;
@@ -76,18 +87,22 @@ GBFS_API bfs_status bfs_tune(bfs_graph_t G, int kind, const int32_t* roots, int 
       }
       ms /= n_roots;
     } else {
+      if ((r = bfs_graph_set_shape(G, kind, s)) != BFS_OK) return r;
       if ((r = bfs_run_batch(G, roots, n_roots, levels, parents, stream, st.data())) != BFS_OK) return r;
       if ((r = bfs_run_batch(G, roots, n_roots, levels, parents, stream, st.data())) != BFS_OK) return r;
       ms = st[0].device_ms;
     }
-    if (ms_per_shape) ms_per_shape[s] = ms;
+    if (ms_per_shape) ms_per_shape[c] = ms;
     if (ms < best_ms) {
       best_ms = ms;
-      best = s;
+      best = c;
     }
   }
-  bfs_status r = bfs_graph_set_shape(G, kind, best);
-  if (r != BFS_OK) return r;
+  bfs_status r;
+  if (kind == BFS_KERNEL_SINGLE &&
+      (r = bfs_graph_set_option(G, BFS_OPT_LOOP, best < count ? BFS_LOOP_GRAPH : BFS_LOOP_PERSISTENT)) != BFS_OK)
+    return r;
+  if ((r = bfs_graph_set_shape(G, kind, best % count)) != BFS_OK) return r;
   if (best_shape) *best_shape = best;
   return BFS_OK;
 }

@@ -35,7 +35,7 @@ struct bfs_graph_s {
   int loop_mode = 1;        // BFS_LOOP_PERSISTENT / BFS_LOOP_GRAPH / BFS_LOOP_HOST
   int bottom_up = 0;        // allow bottom-up levels (persistent loop only)
   int alpha = 14, beta = 24;
-  int pgrid = 0;            // CTAs of the persistent kernel
+  int pgrid[2] = {0, 0};    // CTAs of the persistent kernel (top-down only, with bottom-up)
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   cudaEvent_t last_done = nullptr;  // completion of the last call that used the work buffers

@@ -105,6 +105,6 @@ void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32
 template <typename OffT>
 cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, cudaStream_t st);
 template <typename OffT>
-int persistent_grid(int shape, int num_sms);
+int persistent_grid(int shape, int num_sms, bool with_bu);
 
 }  // namespace gbfs

@@ -28,8 +28,12 @@ def test_tune_single_and_batch_then_exact(torch_cuda, oracle_mod, graphs_mod):
         lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
         pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
         best, ms = capi.bfs_tune(h, capi.BFS_KERNEL_SINGLE, roots[:3], lv, pr)
-        assert len(ms) == capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE) and all(x > 0 for x in ms)
-        assert capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE) == best == int(np.argmin(ms))
+        count = capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE)
+        assert len(ms) == 2 * count and all(x > 0 for x in ms)
+        assert best == int(np.argmin(ms))
+        assert capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE) == best % count
+        assert capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP) == (capi.BFS_LOOP_GRAPH if best < count
+                                                                  else capi.BFS_LOOP_PERSISTENT)
         bl = torch.empty((24, g.n), dtype=torch.int32, device="cuda")
         bp = torch.empty((24, g.n), dtype=torch.int32, device="cuda")
         bbest, bms = capi.bfs_tune(h, capi.BFS_KERNEL_BATCH, roots, bl, bp)
@@ -37,6 +41,8 @@ def test_tune_single_and_batch_then_exact(torch_cuda, oracle_mod, graphs_mod):
         for kind in (capi.BFS_KERNEL_SINGLE, capi.BFS_KERNEL_BATCH):
             for s in range(capi.bfs_shape_count(kind)):
                 capi.bfs_graph_set_shape(h, kind, s)
+                if kind == capi.BFS_KERNEL_SINGLE:
+                    capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, s % 3)
                 r = int(roots[s])
                 ref, _ = oracle_mod.bfs(g.offsets, g.cols, r)
                 if kind == capi.BFS_KERNEL_SINGLE:
