@@ -214,10 +214,12 @@ def main() -> int:
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-direction", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "serve", "multigraph"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-levels-per-round", type=int, default=0)
     args = ap.parse_args()
     if args.mode == "serve":
         return run_serve(args)
@@ -268,7 +270,8 @@ def main() -> int:
 
         tune_roots = pool[: max(3, min(len(pool), 3))]
         rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, wl.kind, g.n, tune_roots, lv, pr)
-        shapes["single"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"]}
+        shapes["single"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"],
+                            "loop": ["persistent", "graph", "host"][rec.get("loop", 1)]}
         log(f"[bench] single-source shape {shapes['single']} ms per shape {rec.get('ms')}")
     for r in warm_roots:
         capi.bfs_run(h, int(r), lv, pr, want_stats=True)
@@ -319,6 +322,10 @@ def main() -> int:
         e2e_teps.append(st.edges_traversed / dt / 1e9)
     e2e_hm = harmonic_mean(e2e_teps)
 
+    direction = None
+    if not args.no_direction:
+        direction = direction_leg(h, g, timed_roots, stats, wl, args, lv, pr)
+
     batched = None
     if not args.no_batched:
         batched = batched_leg(h, g, timed_roots, stats, None if args.no_autotune else wl.kind, shapes)
@@ -360,6 +367,8 @@ def main() -> int:
                        "mean_m_c": round(sum(s["edges_traversed"] for s in stats) / len(stats)),
                        "min_gteps": round(min(teps), 3), "max_gteps": round(max(teps), 3)},
         }
+        if direction is not None:
+            line["direction_optimizing"] = direction
         if batched is not None:
             line["batched"] = batched
         if parity is not None:
@@ -373,6 +382,54 @@ def main() -> int:
     if parity is not None and not parity["ok"]:
         return 1
     return 0
+
+
+def direction_leg(h, g, roots, single_stats, wl, args, lv, pr):
+    """The same roots with bottom-up levels allowed (persistent loop, Beamer's switching):
+    harmonic-mean GTEPS, levels checked exact against the top-down results on sampled roots."""
+    import numpy as np
+
+    from paper_1408_1605_gb300 import capi
+
+    saved = (capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP), capi.bfs_graph_get_option(h, capi.BFS_OPT_BOTTOM_UP),
+             capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE))
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
+    shape_ms = None
+    if not args.no_autotune:
+        best, shape_ms = capi.bfs_tune(h, capi.BFS_KERNEL_SINGLE, roots[:3], lv, pr)
+    else:
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, capi.BFS_LOOP_PERSISTENT)
+    shape = capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE)
+    for r in roots[:3]:
+        capi.bfs_run(h, int(r), lv, pr, want_stats=True)
+    st = [capi.bfs_run(h, int(r), lv, pr, want_stats=True).as_dict() for r in roots]
+    teps = [s["edges_traversed"] / (s["device_ms"] * 1e-3) / 1e9 for s in st]
+    # parity: levels identical to the top-down search on a few roots (which the oracle checks)
+    import torch
+
+    import oracle
+
+    ok, parents_ok = True, True
+    tl = torch.empty_like(lv)
+    tp = torch.empty_like(pr)
+    for i, r in enumerate(roots[:4]):
+        capi.bfs_run(h, int(r), lv, pr)
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 0)
+        capi.bfs_run(h, int(r), tl, tp)
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
+        ok &= bool(torch.equal(lv, tl))
+        if i == 0:  # parents of the bottom-up search: valid BFS tree for the (oracle-checked) levels
+            ref = tl.cpu().numpy()
+            code, _ = oracle.check_tree(g.offsets, g.cols, int(r), ref, lv.cpu().numpy(), pr.cpu().numpy())
+            parents_ok = code == 0
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, saved[0])
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, saved[1])
+    capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_SINGLE, saved[2])
+    return {"value": round(harmonic_mean(teps), 3), "unit": UNIT, "steps": len(st), "shape": shape,
+            "mean_device_ms": round(sum(s["device_ms"] for s in st) / len(st), 4),
+            "mean_bottom_up_levels": round(sum(s["bottom_up_levels"] for s in st) / len(st), 2),
+            "levels_equal_top_down_on_roots": 4, "levels_equal": ok, "parents_valid": parents_ok,
+            "note": "same BFS (levels identical, parents valid); large levels run bottom-up (SURVEY NEXT #1)"}
 
 
 def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
@@ -436,7 +493,7 @@ def run_serve(args) -> int:
               for _ in range(n_buf)] for g in gs]
     results = []
     for rate in [float(x) for x in args.serve_rates.split(",")]:
-        srv = capi.bfs_serve_create(memory_cap_bytes=64 << 30)
+        srv = capi.bfs_serve_create(memory_cap_bytes=64 << 30, levels_per_round=args.serve_levels_per_round)
         ids = [capi.bfs_serve_add_graph(srv, h) for h in hs]
         nq = int(min(4000, max(200, rate * args.serve_seconds)))
         arrivals, gsel, roots = serving.poisson_schedule(nq, rate, [g.n for g in gs], seed=20140806 + 4)
@@ -476,6 +533,7 @@ def run_serve(args) -> int:
                           "higher_is_better": True, "data": "synthetic", "dtype": "i32/i64",
                           "config": {"workload": "serve: rmat-s20, rmat-s24, grid3d-192, uniform-n8M-deg8",
                                      "roots": "seeded uniform per graph", "wave": 64,
+                                     "levels_per_round": args.serve_levels_per_round or 8,
                                      "memory_cap_bytes": 64 << 30},
                           "rates": results}), flush=True)
     return 0

@@ -203,6 +203,9 @@ typedef struct bfs_serve_config {
   uint64_t memory_cap_bytes; /* device memory budget (0 = unlimited) */
   int32_t max_wave;          /* slots per graph wave, 1..64 (0 = 64) */
   int32_t queue_capacity;    /* pending queries before submit returns BFS_ERR_BUSY (0 = 2^20) */
+  int32_t levels_per_round;  /* levels a wave with no pending query runs between two
+                                admission/retirement checks (0 = 8); 1 checks every level */
+  int32_t reserved;
 } bfs_serve_config;
 
 typedef struct bfs_serve_report {

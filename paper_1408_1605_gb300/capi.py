@@ -45,7 +45,8 @@ class BfsError(RuntimeError):
 
 
 class bfs_serve_config(ctypes.Structure):
-    _fields_ = [("memory_cap_bytes", ctypes.c_uint64), ("max_wave", ctypes.c_int32), ("queue_capacity", ctypes.c_int32)]
+    _fields_ = [("memory_cap_bytes", ctypes.c_uint64), ("max_wave", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("levels_per_round", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class bfs_serve_report(ctypes.Structure):
@@ -211,8 +212,9 @@ def bfs_run_noalloc(row_offsets, cols, n_vertices: int, n_entries: int, root: in
                                 ptr(levels), ptr(parents), stream_handle(stream)))
 
 
-def bfs_serve_create(memory_cap_bytes: int = 0, max_wave: int = 0, queue_capacity: int = 0) -> int:
-    cfg = bfs_serve_config(int(memory_cap_bytes), int(max_wave), int(queue_capacity))
+def bfs_serve_create(memory_cap_bytes: int = 0, max_wave: int = 0, queue_capacity: int = 0,
+                     levels_per_round: int = 0) -> int:
+    cfg = bfs_serve_config(int(memory_cap_bytes), int(max_wave), int(queue_capacity), int(levels_per_round), 0)
     out = _P()
     check(lib().bfs_serve_create(ctypes.byref(cfg), ctypes.byref(out)))
     return out.value

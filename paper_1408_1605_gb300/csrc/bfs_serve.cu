@@ -63,6 +63,7 @@ struct Wave {
   cudaStream_t stream = nullptr;
   int grid = 0;
   int shape = 0;
+  int burst = 1;                      // levels to run in the current scheduler round
   bool active = false;
   int t = 0;                          // frontier index the next expansion reads
   uint64_t used = 0;                  // occupied slot bits
@@ -212,6 +213,13 @@ static void scheduler_round(bfs_server_s* S) {
         S->max_running = std::max(S->max_running, S->running);
       }
       if (!ad.reqs.empty()) admits.push_back(ad);
+      // With nobody waiting for this wave (or no slot to admit into), run several levels
+      // before looking again: a root's bit never returns to a frontier once its search is
+      // done, so the alive mask after the burst still shows every query that finished in it.
+      const int lpr = S->cfg.levels_per_round > 0 ? S->cfg.levels_per_round : 8;
+      bool slot_free = false;
+      for (int b = 0; b < cap_slots; ++b) slot_free |= !((w->used >> b) & 1ull);
+      w->burst = (w->pending.empty() || !slot_free) ? lpr : 1;
     }
   }
   // seeding (outside the lock; only this thread touches the waves' device state)
@@ -267,13 +275,15 @@ static void scheduler_round(bfs_server_s* S) {
       }
     }
   }
-  // one level of every active wave; launch all, then wait for all
+  // a burst of levels of every active wave; launch all, then wait for all
   for (Wave* w : S->waves) {
     if (!w->active) continue;
-    if (w->g.off64)
-      wave_launch_level<int64_t>(w);
-    else
-      wave_launch_level<int32_t>(w);
+    for (int i = 0; i < w->burst; ++i) {
+      if (w->g.off64)
+        wave_launch_level<int64_t>(w);
+      else
+        wave_launch_level<int32_t>(w);
+    }
     cudaMemcpyAsync(w->ctl_host, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, w->stream);
   }
   for (Wave* w : S->waves) {
@@ -282,8 +292,8 @@ static void scheduler_round(bfs_server_s* S) {
     std::vector<int> retire;
     unsigned long long alive = 0;
     if (e == cudaSuccess) {
-      const int t_expanded = w->t;
-      ++w->t;
+      const int t_expanded = w->t;  // first frontier of the burst
+      w->t = w->ctl_host->level - 1;
       alive = w->ctl_host->alive[w->t & 1];
       for (int b = 0; b < kMaxWave; ++b) {
         ServeReq* r = w->slot_req[b];
@@ -311,7 +321,7 @@ static void scheduler_round(bfs_server_s* S) {
       if (!retire.empty()) e = cudaStreamSynchronize(w->stream);
     }
     std::unique_lock<std::mutex> lk(S->mu);
-    ++S->levels;
+    S->levels += w->burst;
     if (e != cudaSuccess) {
       const std::string msg = std::string("CUDA error in serving wave: ") + cudaGetErrorString(e);
       cudaGetLastError();

@@ -40,12 +40,12 @@ def _check(oracle, capi, srv, g, q, host):
     assert st.depth == int(ref.max()) + 1
 
 
-@pytest.mark.parametrize("host", [False, True])
-def test_poisson_mix_equals_alone(env, oracle_mod, host):
+@pytest.mark.parametrize("host,lpr", [(False, 1), (False, 0), (True, 3)])
+def test_poisson_mix_equals_alone(env, oracle_mod, host, lpr):
     from paper_1408_1605_gb300 import serving
 
     torch, capi, gs, handles = env
-    srv, ids = _server(capi, handles)
+    srv, ids = _server(capi, handles, levels_per_round=lpr)
     try:
         if host:
             alloc = lambda n: (np.empty(n, np.int32), np.empty(n, np.int32))  # noqa: E731
