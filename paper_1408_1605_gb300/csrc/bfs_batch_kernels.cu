@@ -281,44 +281,67 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
       }
       nb[j] = ok[j] ? (ff[j] & ~a.visited[vv[j]]) : 0ull;
     }
+    // Claims in phases, so that each kind of atomic / load is in flight for all E edges at
+    // once rather than one round trip after another.
+    unsigned long long claimed[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) claimed[j] = nb[j] ? nb[j] & ~atomicOr(a.visited + vv[j], nb[j]) : 0ull;
+    int slot[E];
+    unsigned long long fold[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      slot[j] = 0;
+      fold[j] = 1ull;
+      if (claimed[j]) {
+        slot[j] = atomicAdd(a.evc + vv[j], 1);
+        fold[j] = atomicOr(Fn + vv[j], claimed[j]);
+      }
+    }
+    unsigned long long mine = 0ull;
+    bool first[E];
+    OffT o0[E], o1[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int32_t v = vv[j];
-      unsigned long long claimed = 0ull;
-      if (nb[j]) claimed = nb[j] & ~atomicOr(a.visited + v, nb[j]);
-      bool first = false;
-      int32_t deg = 0;
-      if (claimed) {
+      first[j] = claimed[j] && fold[j] == 0ull;
+      o0[j] = 0;
+      o1[j] = 0;
+      if (first[j]) {
+        o0[j] = a.off[v];
+        o1[j] = a.off[v + 1];
+      }
+      if (claimed[j]) {
+        mine |= claimed[j];
         // Parent event: the outputs are written in vertex order after the level (emit).
-        const int slot = atomicAdd(a.evc + v, 1);
-        if (slot < kEventSlots) {
+        if (slot[j] < kEventSlots) {
           ClaimEvent ce;
           ce.u = uu[j];
           ce.pad = 0;
-          ce.mask = claimed;
-          a.ev[(size_t)v * kEventSlots + slot] = ce;
+          ce.mask = claimed[j];
+          a.ev[(size_t)v * kEventSlots + slot[j]] = ce;
         } else {
           const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
           if ((long long)o < a.ovf_cap) {
-            a.ovf[o] = OvfEvent{v, uu[j], claimed};
+            a.ovf[o] = OvfEvent{v, uu[j], claimed[j]};
           } else {
-            for (unsigned long long bits = claimed; bits; bits &= bits - 1) {  // no room: write now
+            for (unsigned long long bits = claimed[j]; bits; bits &= bits - 1) {  // no room: write now
               const int b = __ffsll((long long)bits) - 1;
               s_par[b][v] = uu[j];
             }
           }
         }
-        atomicOr(&s_alive, claimed);
-        first = atomicOr(Fn + v, claimed) == 0ull;
-        if (first) deg = (int32_t)(a.off[v + 1] - a.off[v]);
       }
-      const unsigned ball = __ballot_sync(0xffffffffu, first);
+    }
+    if (mine) atomicOr(&s_alive, mine);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const unsigned ball = __ballot_sync(0xffffffffu, first[j]);
       if (ball) {
         const int leader = __ffs(ball) - 1;
         int pos = 0;
         if (lane == leader) pos = atomicAdd(&s_nclaim, __popc(ball));
         pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (first) s_claim[pos + __popc(ball & lanemask_lt())] = make_int2(v, deg);
+        if (first[j]) s_claim[pos + __popc(ball & lanemask_lt())] = make_int2(vv[j], (int32_t)(o1[j] - o0[j]));
       }
     }
     __syncthreads();

@@ -332,21 +332,37 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
       }
       bits[j] = ok[j] ? bitmap[vv[j] >> 5] : 0xffffffffu;
     }
+    // Claims in phases so that the E atomics, then the E degree reads, are in flight
+    // together instead of one round trip after another.
+    bool claimed[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      const int32_t v = vv[j];
-      const uint32_t m = 1u << (v & 31);
-      bool claimed = false;
-      if (!(bits[j] & m)) claimed = !(atomicOr(bitmap + (v >> 5), m) & m);
-      int32_t deg = 0;
-      if (claimed) {
-        io.levels[v] = L;
-        io.parents[v] = uu[j];
-        deg = (int32_t)(off[v + 1] - off[v]);
-        if (io.fbm_out) atomicOr(io.fbm_out + (v >> 5), m);
-      }
-      push_claim(claimed, v, deg, s_claim, &sh.nclaim);
+      const uint32_t m = 1u << (vv[j] & 31);
+      claimed[j] = !(bits[j] & m);
+      if (claimed[j]) bits[j] = atomicOr(bitmap + (vv[j] >> 5), m);
     }
+    OffT o0[E], o1[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const uint32_t m = 1u << (vv[j] & 31);
+      claimed[j] = claimed[j] && !(bits[j] & m);
+      o0[j] = 0;
+      o1[j] = 0;
+      if (claimed[j]) {
+        o0[j] = off[vv[j]];
+        o1[j] = off[vv[j] + 1];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (claimed[j]) {
+        io.levels[vv[j]] = L;
+        io.parents[vv[j]] = uu[j];
+        if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) push_claim(claimed[j], vv[j], (int32_t)(o1[j] - o0[j]), s_claim, &sh.nclaim);
     __syncthreads();
     const int nc = sh.nclaim;
     if (nc > CLAIM - T) {
@@ -687,7 +703,8 @@ static int occupancy_t(int num_sms) {
   X(2, 512, 4, 4096)          \
   X(3, 128, 8, 2048)          \
   X(4, 256, 2, 2048)          \
-  X(5, 256, 16, 8192)
+  X(5, 256, 4, 1536)          \
+  X(6, 256, 2, 1024)
 
 const ExpandShape kExpandShapes[] = {
 #define X(id, b, e, c) {id, b, e, c},
