@@ -101,7 +101,8 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *     related work, Sec. 6) when frontier edges x ALPHA exceed the unexplored edges, and
  *     return to top-down once frontier vertices x BETA < n. Results are the same BFS
  *     (levels identical; parents valid). Default 0: every level top-down (Algorithm 3).
- *   BFS_OPT_ALPHA (default 14), BFS_OPT_BETA (default 24): the switching thresholds. */
+ *   BFS_OPT_ALPHA (default 8; swept on GB300: 8 beat 2, 4, 6, 14 on R-MAT and uniform graphs),
+ *   BFS_OPT_BETA (default 24): the switching thresholds. */
 #define BFS_OPT_LOOP 1
 #define BFS_OPT_BOTTOM_UP 2
 #define BFS_OPT_ALPHA 3
@@ -111,6 +112,14 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
 #define BFS_LOOP_HOST 2
 GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t g, int option, int64_t value);
 GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t g, int option, int64_t *value);
+
+/* Per-level profile of the last persistent search on this graph (BFS_LOOP_PERSISTENT):
+ * device time of each level (ms, from the device clock at each grid barrier), the size of
+ * the frontier it expanded, and whether it ran bottom-up. Writes min(levels, cap) entries
+ * (at most 64) of each non-NULL array; *n_levels = levels recorded. Waits for the graph's
+ * pending work. BFS_ERR_NOT_FOUND if no persistent search has run. */
+GBFS_API bfs_status bfs_level_profile(bfs_graph_t g, int cap, double *level_ms, int64_t *frontier,
+                                      int32_t *bottom_up, int *n_levels);
 
 /* Vertex and CSR-entry counts of a graph. */
 GBFS_API bfs_status bfs_graph_info(bfs_graph_t g, int64_t *n_vertices, int64_t *n_entries);

@@ -110,6 +110,8 @@ def lib():
                                ctypes.POINTER(ctypes.c_int)],
             "bfs_graph_set_shape": [_P, ctypes.c_int, ctypes.c_int],
             "bfs_graph_set_option": [_P, ctypes.c_int, i64],
+            "bfs_level_profile": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int)],
             "bfs_graph_get_option": [_P, ctypes.c_int, ctypes.POINTER(i64)],
             "bfs_graph_get_shape": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
             "bfs_tune": [_P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
@@ -270,6 +272,15 @@ def bfs_graph_get_option(graph: int, option: int) -> int:
     v = ctypes.c_int64()
     check(lib().bfs_graph_get_option(graph, int(option), ctypes.byref(v)))
     return v.value
+
+
+def bfs_level_profile(graph: int, cap: int = 64) -> list[dict]:
+    ms = (ctypes.c_double * cap)()
+    nf = (ctypes.c_int64 * cap)()
+    bu = (ctypes.c_int32 * cap)()
+    n = ctypes.c_int()
+    check(lib().bfs_level_profile(graph, int(cap), ms, nf, bu, ctypes.byref(n)))
+    return [{"ms": ms[i], "frontier": nf[i], "bottom_up": bool(bu[i])} for i in range(min(n.value, cap))]
 
 
 def bfs_shape_count(kind: int) -> int:

@@ -136,6 +136,7 @@ ExpandArgs<OffT> make_args(const bfs_graph_s* G, uint32_t* bitmap) {
   a.pk = g.pk;
   a.cond = 0;
   a.use_cond = 0;
+  a.probe_mode = G->probe_mode;
   return a;
 }
 
@@ -250,6 +251,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.alpha = G->alpha;
     pa.beta = G->beta;
     pa.allow_bottom_up = G->bottom_up;
+    pa.probe_mode = G->probe_mode;
     int& pg = G->pgrid[G->bottom_up ? 1 : 0];
     if (!pg) pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
     if ((e = launch_persistent<OffT>(G->shape, pa, pg, st)) != cudaSuccess)
@@ -506,6 +508,8 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
   G->host_loop = G->loop_mode == BFS_LOOP_HOST;
   const char* bu = std::getenv("GBFS_BOTTOM_UP");
   G->bottom_up = bu && std::atoi(bu) != 0;
+  const char* pm = std::getenv("GBFS_PROBE");
+  if (pm) G->probe_mode = std::atoi(pm) != 0;
   const char* sh = std::getenv("GBFS_SHAPE");
   G->shape = sh ? std::max(0, std::min(kNumExpandShapes - 1, std::atoi(sh))) : kDefaultShape;
   G->grid = g.off64 ? expand_grid<int64_t>(G->shape, g.num_sms) : expand_grid<int32_t>(G->shape, g.num_sms);
@@ -565,6 +569,26 @@ GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* val
     case BFS_OPT_BETA: *value = G->beta; return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");
+}
+
+GBFS_API bfs_status bfs_level_profile(bfs_graph_t G, int cap, double* level_ms, int64_t* frontier,
+                                      int32_t* bottom_up, int* n_levels) {
+  clear_last_error();
+  if (!G || !n_levels || cap < 0) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lock(G->mu);
+  if (!G->ws.ready || !G->ws.pctl_host) return fail(BFS_ERR_NOT_FOUND, "no persistent search has run on this graph");
+  if (G->last_done) cudaEventSynchronize(G->last_done);
+  const PCtl& c = *G->ws.pctl_host;
+  const int levels = std::min(std::max(c.depth, 0), kMaxLevelTimes);
+  unsigned long long prev = c.start_ns;
+  for (int i = 0; i < levels && i < cap; ++i) {
+    if (level_ms) level_ms[i] = (double)(c.level_ns[i] - prev) * 1e-6;
+    if (frontier) frontier[i] = c.level_nf[i];
+    if (bottom_up) bottom_up[i] = c.level_bu[i];
+    prev = c.level_ns[i];
+  }
+  *n_levels = levels;
+  return BFS_OK;
 }
 
 GBFS_API bfs_status bfs_graph_info(bfs_graph_t G, int64_t* n_vertices, int64_t* n_entries) {

@@ -198,6 +198,7 @@ struct LevelIO {
   int32_t* parents;
   uint32_t* fbm_out;                // next frontier as a bitmap (nullptr: not kept)
   int L;                            // level assigned to claimed vertices
+  int probe_mode;                   // bitmap pre-check: 0 default caching, 1 L2 only
   int64_t nf;                       // current frontier size
   OffT r;                           // current frontier's degree sum
 };
@@ -263,6 +264,7 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
   const int64_t nf = io.nf;
   const int64_t ntiles = ((int64_t)r + T - 1) / T;
   const int L = io.L;
+  const int probe_mode = io.probe_mode;
 
   if (threadIdx.x == 0) sh.nclaim = 0;
   for (int64_t tile = tile0; tile < ntiles; tile += tstride) {
@@ -330,7 +332,7 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
         atomicOr(err, kErrColumnRange);
         ok[j] = false;
       }
-      bits[j] = ok[j] ? bitmap[vv[j] >> 5] : 0xffffffffu;
+      bits[j] = ok[j] ? probe_load(bitmap + (vv[j] >> 5), probe_mode) : 0xffffffffu;
     }
     // Claims in phases so that the E atomics, then the E degree reads, are in flight
     // together instead of one round trip after another.
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
   io.parents = *(int32_t* volatile*)&ctl->parents;
   io.fbm_out = nullptr;
   io.L = L;
+  io.probe_mode = a.probe_mode;
   io.nf = a.pk.count(pc);
   io.r = (OffT)a.pk.edges(pc);
   td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, smem, sh, blockIdx.x,
@@ -456,77 +459,106 @@ __device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks) {
   __syncthreads();
 }
 
+// Appends a warp's buffered claims (buf[0..nc), nc <= 32 * P) to the next frontier with
+// one 64-bit atomic for the warp: lane i owns items [i P, i P + P); a warp scan of the
+// degrees gives each item its place in the next level's edge space.
+template <typename OffT, int P>
+__device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const LevelIO<OffT>& io, const int2* buf,
+                                           int nc) {
+  const int lane = threadIdx.x & 31;
+  const int lo = min(nc, lane * P), hi = min(nc, lo + P);
+  OffT mine = 0;
+  for (int i = lo; i < hi; ++i) mine += (OffT)buf[i].y;
+  const OffT inc = warp_inclusive_scan(mine);
+  const OffT total = __shfl_sync(0xffffffffu, inc, 31);
+  unsigned long long resv = 0;
+  if (lane == 0) resv = atomicAdd(io.counter_out, pk.make(nc, (long long)total));
+  resv = __shfl_sync(0xffffffffu, resv, 0);
+  const long long slot0 = pk.count(resv);
+  OffT run = (OffT)pk.edges(resv) + inc - mine;
+  for (int i = lo; i < hi; ++i) {
+    const int32_t v = buf[i].x;
+    const OffT d = (OffT)buf[i].y;
+    const int32_t slot = (int32_t)(slot0 + i);
+    io.out.v[slot] = v;
+    io.out.cum[slot] = run;
+    io.out.base[slot] = off[v] - run;
+    write_chunks(io.chunk_out, run, d, slot);
+    run += d;
+  }
+  __syncwarp();
+}
+
 // One bottom-up level (Beamer et al.'s step, the paper's related work, Sec. 6): every
 // unvisited vertex scans its row for a neighbour in the current frontier (a bitmap) and
-// stops at the first; warp w owns visited word w (32 vertices), so no atomics are needed
-// on the visited and next-frontier bitmaps. Claimed vertices are appended to the next
-// frontier queue exactly as in the top-down step.
+// stops at the first. Warp w takes visited word w (32 vertices), so no atomics are needed
+// on the visited and next-frontier bitmaps, and every warp appends its claimed vertices
+// through its own slice of the claim buffer with a warp-level flush: warps never wait for
+// one another inside the level. Claimed vertices enter the next frontier queue exactly as
+// in the top-down step.
 template <typename OffT, int BLOCK, int CLAIM>
 __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
                          const uint32_t* __restrict__ fbm_in, int64_t n, Packed pk, const LevelIO<OffT>& io,
-                         int2* s_claim, ExpandShared<OffT>& sh, int64_t cta0, int64_t cstride) {
+                         int2* s_claim, int64_t warp0, int64_t wstride) {
   constexpr int WARPS = BLOCK / 32;
+  constexpr int WCAP = CLAIM / WARPS;  // claim entries per warp
+  static_assert(WCAP >= 64, "per-warp claim buffer too small");
+  constexpr int P = (WCAP + 31) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int2* wbuf = s_claim + warp * WCAP;
   const int64_t nwords = (n + 31) / 32;
-  const int64_t rounds = (nwords + WARPS - 1) / WARPS;  // CTA-rounds of WARPS words
   const int L = io.L;
-  if (threadIdx.x == 0) sh.nclaim = 0;
-  __syncthreads();
-  for (int64_t rd = cta0; rd < rounds; rd += cstride) {
-    const int64_t w = rd * WARPS + warp;
+  int nc = 0;  // warp-uniform
+  for (int64_t w = warp0; w < nwords; w += wstride) {
     bool found = false;
-    int32_t v = 0, parent = 0, deg = 0;
-    if (w < nwords) {
-      const uint32_t vis = bitmap[w];
-      v = (int32_t)(w * 32 + lane);
-      if (v < n && !((vis >> lane) & 1u)) {
-        const OffT b = off[v], e = off[v + 1];
-        deg = (int32_t)(e - b);
-        OffT i = b;
-        for (; i + 4 <= e && !found; i += 4) {
-          int32_t u4[4];
+    int32_t parent = 0, deg = 0;
+    const uint32_t vis = bitmap[w];
+    const int32_t v = (int32_t)(w * 32 + lane);
+    if (v < n && !((vis >> lane) & 1u)) {
+      const OffT b = off[v], e = off[v + 1];
+      deg = (int32_t)(e - b);
+      OffT i = b;
+      for (; i + 4 <= e && !found; i += 4) {
+        int32_t u4[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) u4[j] = ld_nc(cols + i + j);
+        for (int j = 0; j < 4; ++j) u4[j] = ld_nc(cols + i + j);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t u = (uint32_t)u4[j];
-            if (!found && u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
-              found = true;
-              parent = (int32_t)u;
-            }
-          }
-        }
-        for (; i < e && !found; ++i) {
-          const uint32_t u = (uint32_t)ld_nc(cols + i);
-          if (u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t u = (uint32_t)u4[j];
+          if (!found && u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
             found = true;
             parent = (int32_t)u;
           }
         }
       }
+      for (; i < e && !found; ++i) {
+        const uint32_t u = (uint32_t)ld_nc(cols + i);
+        if (u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
+          found = true;
+          parent = (int32_t)u;
+        }
+      }
     }
     const unsigned claimed = __ballot_sync(0xffffffffu, found);
-    if (found) {
-      io.levels[v] = L;
-      io.parents[v] = parent;
-    }
-    if (lane == 0 && claimed) {
-      bitmap[w] |= claimed;
-      io.fbm_out[w] = claimed;
-    }
-    push_claim(found, v, deg, s_claim, &sh.nclaim);
-    __syncthreads();
-    const int nc = sh.nclaim;
-    if (nc > CLAIM - BLOCK) {
-      flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
-      __syncthreads();
-      if (threadIdx.x == 0) sh.nclaim = 0;
-      __syncthreads();
+    if (claimed) {
+      if (found) {
+        io.levels[v] = L;
+        io.parents[v] = parent;
+        wbuf[nc + __popc(claimed & lanemask_lt())] = make_int2(v, deg);
+      }
+      if (lane == 0) {
+        bitmap[w] = vis | claimed;
+        io.fbm_out[w] = claimed;
+      }
+      nc += __popc(claimed);
+      __syncwarp();
+      if (nc > WCAP - 32) {
+        warp_flush<OffT, P>(off, pk, io, wbuf, nc);
+        nc = 0;
+      }
     }
   }
-  __syncthreads();
-  const int nc = sh.nclaim;
-  if (nc > 0) flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
+  if (nc > 0) warp_flush<OffT, P>(off, pk, io, wbuf, nc);
   __syncthreads();
 }
 
@@ -577,16 +609,25 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_
     io.parents = a.parents;
     io.fbm_out = WITH_BU ? a.fbm[nxt3] : nullptr;
     io.L = it + 1;
+    io.probe_mode = a.probe_mode;
     io.nf = nf;
     io.r = (OffT)r;
     if (WITH_BU && bottom_up)
-      bu_level<OffT, BLOCK, CLAIM>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, s_claim, sh, blockIdx.x,
-                                   gridDim.x);
+      bu_level<OffT, BLOCK, CLAIM>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, s_claim,
+                                   (int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5),
+                                   (int64_t)gridDim.x * (BLOCK / 32));
     else
       td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &c->error, io, smem, sh, blockIdx.x,
                                       gridDim.x);
     grid_barrier(c, gridDim.x);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (it < kMaxLevelTimes) {
+        unsigned long long ns;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+        c->level_ns[it] = ns;
+        c->level_bu[it] = bottom_up ? 1 : 0;
+        c->level_nf[it] = nf;
+      }
       const long long nn = a.pk.count(*(volatile unsigned long long*)&c->counter[nxt3]);
       c->edges2 += r;
       if (nn > 0) {
@@ -633,6 +674,7 @@ __global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t 
     c->reached = 1;
     c->edges2 = 0;
     c->steps_bottom_up = 0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(c->start_ns));
   }
 }
 
@@ -704,7 +746,8 @@ static int occupancy_t(int num_sms) {
   X(3, 128, 8, 2048)          \
   X(4, 256, 2, 2048)          \
   X(5, 256, 4, 1536)          \
-  X(6, 256, 2, 1024)
+  X(6, 256, 2, 1024)          \
+  X(7, 128, 4, 1024)
 
 const ExpandShape kExpandShapes[] = {
 #define X(id, b, e, c) {id, b, e, c},

@@ -152,6 +152,7 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
   a.ctl = ws.ctl;
   a.pk = g.pk;
   a.use_cond = 0;
+  a.probe_mode = 1;
   const int grid = expand_grid<int32_t>(kDefaultShape, g.num_sms);
   Ctl c{};
   for (int64_t it = 0; it <= n_vertices; ++it) {

@@ -34,7 +34,8 @@ struct bfs_graph_s {
   bool host_loop = false;
   int loop_mode = 1;        // BFS_LOOP_PERSISTENT / BFS_LOOP_GRAPH / BFS_LOOP_HOST
   int bottom_up = 0;        // allow bottom-up levels (persistent loop only)
-  int alpha = 14, beta = 24;
+  int alpha = 8, beta = 24;
+  int probe_mode = 1;       // bitmap pre-check through L2 (1) or default caching (0)
   int pgrid[2] = {0, 0};    // CTAs of the persistent kernel (top-down only, with bottom-up)
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;

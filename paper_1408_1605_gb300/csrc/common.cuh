@@ -51,6 +51,7 @@ struct Ctl {
 
 // Control block of a persistent (one-launch) search: counters rotate by 3 so that level
 // it reads counter[it % 3], fills counter[(it + 1) % 3] and clears counter[(it + 2) % 3].
+constexpr int kMaxLevelTimes = 64;
 struct PCtl {
   unsigned long long counter[3];
   unsigned int bar_count;
@@ -61,6 +62,10 @@ struct PCtl {
   long long edges2;
   int steps_bottom_up;
   int pad;
+  unsigned long long start_ns;                  // device clock when the search was set up
+  unsigned long long level_ns[kMaxLevelTimes];  // device clock at the end of each level
+  long long level_nf[kMaxLevelTimes];           // frontier size of each level
+  int level_bu[kMaxLevelTimes];                 // 1 if the level ran bottom-up
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -74,6 +79,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // Read-only, non-coherent load of a column id (the const __restrict__ read-only path the
 // paper uses for the CSC arrays, Sec. 3.4.1).
 __device__ __forceinline__ int32_t ld_nc(const int32_t* p) { return __ldg(p); }
+
+// Visited-bitmap pre-check load (Algorithm 3 line 6). Mode 0: default caching (L1 may hold
+// a stale copy; harmless, the atomicOr decides). Mode 1: L2 only (ld.global.cg), so words
+// filled during the level are seen and fewer futile atomics are issued.
+__device__ __forceinline__ uint32_t probe_load(const uint32_t* p, int mode) {
+  return mode ? __ldcg(p) : *p;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_inclusive_scan(T x) {

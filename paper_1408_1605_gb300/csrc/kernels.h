@@ -62,6 +62,7 @@ struct ExpandArgs {
   Packed pk;
   cudaGraphConditionalHandle cond;
   int use_cond;
+  int probe_mode;   // bitmap pre-check: 0 default caching, 1 L2 only
 };
 
 template <typename OffT>
@@ -81,6 +82,7 @@ struct PersistArgs {
   int alpha;            // switch to bottom-up when frontier edges * alpha > unexplored edges
   int beta;             // back to top-down when frontier vertices * beta < n (and shrinking)
   int allow_bottom_up;
+  int probe_mode;
 };
 
 struct ExpandShape {

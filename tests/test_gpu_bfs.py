@@ -113,7 +113,7 @@ def test_grid3d_manhattan(torch_cuda, oracle_mod, graphs_mod):
         capi.bfs_graph_destroy(h)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("force64", [False, True])
 def test_rmat16_all_shapes(torch_cuda, oracle_mod, graphs_mod, shape, force64):
     """R-MAT scale 16, edge factor 16 (the small configuration): 16 seeded roots, every

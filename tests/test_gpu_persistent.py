@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 # (loop mode, bottom-up, alpha, beta)
 POLICIES = {
     "persistent-td": (0, 0, 14, 24),
-    "persistent-do": (0, 1, 14, 24),
+    "persistent-do": (0, 1, 8, 24),
     "persistent-bu-eager": (0, 1, 1 << 20, 1 << 20),  # bottom-up from the first growing level on
     "persistent-bu-flip": (0, 1, 1 << 20, 1),         # bottom-up while growing, top-down once shrinking
 }
@@ -132,3 +132,24 @@ def test_option_errors(torch_cuda, graphs_mod):
                 capi.bfs_graph_set_option(h, opt, val)
     finally:
         capi.bfs_graph_destroy(h)
+
+
+def test_level_profile_matches_oracle_level_sizes(torch_cuda, oracle_mod, graphs_mod):
+    """The per-level profile of a persistent search lists, for level i, the size of the
+    frontier it expanded: the number of vertices at hop distance i."""
+    from paper_1408_1605_gb300 import capi
+
+    g = graphs_mod.rmat(16, 16, seed=17)
+    r = int(graphs_mod.pick_roots(g, 1, 2)[0])
+    for policy in ("persistent-td", "persistent-do"):
+        h = _upload(capi, g, policy)
+        try:
+            st = _check(capi, oracle_mod, torch_cuda, h, g, r)
+            prof = capi.bfs_level_profile(h)
+            ref, _ = oracle_mod.bfs(g.offsets, g.cols, r)
+            assert len(prof) == st.depth
+            assert [p["frontier"] for p in prof] == np.bincount(ref[ref >= 0]).tolist()
+            assert sum(p["bottom_up"] for p in prof) == st.bottom_up_levels
+            assert all(p["ms"] >= 0 for p in prof) and sum(p["ms"] for p in prof) <= st.device_ms + 0.05
+        finally:
+            capi.bfs_graph_destroy(h)
