@@ -196,12 +196,15 @@ GBFS_API bfs_status bfs_run_noalloc(const int32_t *row_offsets, const int32_t *c
  * serving layer; every query runs as one bit-slot of a multi-source wave (see
  * bfs_run_batch) on its graph, and its result is identical to the same query run alone
  * (levels equal; parents a valid BFS tree).
- *   - Each added graph gets a wave of up to max_wave slots and its own CUDA stream; one
- *     scheduler thread runs every active wave one level at a time, so the waves of
- *     different graphs overlap on the device.
- *   - Between two levels, finished queries retire (their bit left every frontier) and
- *     pending queries are admitted into free slots in arrival order per graph, starting
- *     from their root at the current wave level; a wave is never restarted for admission.
+ *   - Each added graph gets waves_per_graph waves of up to max_wave slots; each wave has its
+ *     own CUDA stream and scheduler thread, so waves run concurrently on the device.
+ *   - A wave advances in bursts of levels (levels_per_round when it cannot admit, else
+ *     one). Between two bursts, finished queries retire (their bit left every frontier)
+ *     and pending queries of its graph are admitted into free slots in arrival order,
+ *     starting from their root at the current wave level; a wave is never restarted for
+ *     admission. Queries share row reads only while their searches are in step, so a
+ *     running wave admits only while its cohort is young (admit_window); otherwise an idle
+ *     wave of the graph starts a new cohort.
  *   - Admission is gated by memory_cap_bytes: the graphs' wave state plus, for each
  *     running query whose outputs are host memory, a device staging buffer of 8 bytes
  *     per vertex. A query waits in the queue until a slot and the memory are free.
@@ -212,8 +215,12 @@ typedef struct bfs_serve_config {
   uint64_t memory_cap_bytes; /* device memory budget (0 = unlimited) */
   int32_t max_wave;          /* slots per graph wave, 1..64 (0 = 64) */
   int32_t queue_capacity;    /* pending queries before submit returns BFS_ERR_BUSY (0 = 2^20) */
-  int32_t levels_per_round;  /* levels a wave with no pending query runs between two
+  int32_t levels_per_round;  /* levels a wave that cannot admit runs between two
                                 admission/retirement checks (0 = 8); 1 checks every level */
+  int32_t waves_per_graph;   /* waves (64-slot cohorts) per resident graph (0 = 2) */
+  int32_t admit_window;      /* a running wave admits only while its cohort is at most this
+                                many levels old (0 = 3); raised to a quarter of the graph's
+                                mean query depth on deep graphs */
   int32_t reserved;
 } bfs_serve_config;
 
@@ -233,8 +240,8 @@ typedef struct bfs_serve_report {
  * BFS_ERR_INVALID_ARG (max_wave outside [0, 64]), BFS_ERR_OOM. */
 GBFS_API bfs_status bfs_serve_create(const bfs_serve_config *cfg, bfs_server_t *out);
 
-/* Makes a graph resident in the server and allocates its wave state (about 44 bytes per
- * vertex). The graph handle must outlive the server. Graphs are added before the first
+/* Makes a graph resident in the server and allocates its waves' state (about 128 bytes
+ * per vertex per wave). The graph handle must outlive the server. Graphs are added before the first
  * submission, all on one device. Failures: BFS_ERR_INVALID_ARG, BFS_ERR_BUSY (already
  * serving), BFS_ERR_OOM (memory budget or device memory), BFS_ERR_CUDA. */
 GBFS_API bfs_status bfs_serve_add_graph(bfs_server_t srv, bfs_graph_t g, int *graph_id);

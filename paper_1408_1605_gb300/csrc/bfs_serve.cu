@@ -1,9 +1,9 @@
 // Serving loop: BFS queries on resident graphs with continuous batching.
 //
 // Each graph added to a server gets its own wave (multi-source state with 64 bit-slots,
-// see bfs_batch_kernels.cu) and its own CUDA stream. A scheduler thread runs the waves one
-// level at a time, all waves launched before any is waited on, so the waves of different
-// graphs overlap on the device. Between two levels it
+// see bfs_batch_kernels.cu), its own CUDA stream and its own scheduler thread, so the waves
+// of different graphs run concurrently on the device and a slow wave does not hold back a
+// fast one. A wave advances in bursts of levels; between two bursts its thread
 //   * retires slots whose bit left every frontier (the query is complete: its outputs are
 //     final), copying results to host buffers where the caller gave host memory;
 //   * admits pending queries into free slots, in arrival order per graph, as long as the
@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -56,19 +57,21 @@ struct ServeReq {
   Clock::time_point t_submit, t_admit, t_done;
 };
 
+struct ServeGraph;
+
 struct Wave {
   bfs_graph_s* G = nullptr;
+  ServeGraph* sg = nullptr;
   GraphDev g;
   BatchBufs b;
   cudaStream_t stream = nullptr;
   int grid = 0;
   int shape = 0;
   int burst = 1;                      // levels to run in the current scheduler round
-  bool active = false;
-  int t = 0;                          // frontier index the next expansion reads
+  std::atomic<bool> active{false};     // read by sibling waves' threads
+  std::atomic<int> t{0};              // frontier index the next expansion reads
   uint64_t used = 0;                  // occupied slot bits
   ServeReq* slot_req[kMaxWave] = {};
-  std::deque<ServeReq*> pending;
   WaveSlots* slots_host = nullptr;    // pinned
   BatchCtl* ctl_host = nullptr;       // pinned
   RootSeed* seeds_host = nullptr;     // pinned
@@ -77,16 +80,28 @@ struct Wave {
   unsigned long long pending_clear = 0;  // bits to clear from V before reuse
 };
 
+// A resident graph: its queue of pending queries, shared by its waves, and the mean depth
+// of its completed queries (deep graphs admit continuously, see young()).
+struct ServeGraph {
+  int id = 0;
+  GraphDev g;
+  std::deque<ServeReq*> pending;
+  std::vector<Wave*> waves;
+  double depth_sum = 0;
+  long long depth_n = 0;
+};
+
 }  // namespace gbfs
 
 struct bfs_server_s {
   bfs_serve_config cfg{};
   int device = -1;
-  std::vector<gbfs::Wave*> waves;
+  std::vector<gbfs::Wave*> waves;          // every wave of every graph
+  std::vector<gbfs::ServeGraph*> graphs;
   std::map<uint64_t, gbfs::ServeReq*> reqs;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::thread th;
+  std::vector<std::thread> threads;  // one scheduler thread per wave
   bool stop = false;
   bool started = false;
   uint64_t next_ticket = 1;
@@ -153,88 +168,113 @@ static void finish_req(bfs_server_s* S, ServeReq* r, bfs_status st, const std::s
   }
 }
 
-// One scheduler round: admission, seeding, one level of every active wave, retirement.
-static void scheduler_round(bfs_server_s* S) {
-  struct Admit {
-    Wave* w;
-    std::vector<ServeReq*> reqs;
-  };
-  std::vector<Admit> admits;
+// Queries admitted into a running wave at different levels share fewer row reads: on
+// graphs with few levels (R-MAT) the large levels of all roots cover the same vertices,
+// so a wave takes new queries only while its current cohort is young (at most `window`
+// levels old) and otherwise leaves them to an idle or younger wave of the same graph. On
+// deep graphs the window grows with the graph's mean query depth.
+static int admit_window(const bfs_server_s* S, const ServeGraph* sg) {
+  const int base = S->cfg.admit_window > 0 ? S->cfg.admit_window : 3;
+  const double mean_depth = sg->depth_n ? sg->depth_sum / (double)sg->depth_n : 0.0;
+  return std::max(base, (int)(mean_depth / 4.0));
+}
+
+static bool wave_can_admit(const bfs_server_s* S, const Wave* w, int cap_slots) {
+  bool slot_free = false;
+  for (int b = 0; b < cap_slots; ++b) slot_free |= !((w->used >> b) & 1ull);
+  if (!slot_free) return false;
+  return !w->active || w->t <= admit_window(S, w->sg);
+}
+
+// True when a sibling wave of the same graph is running a young cohort with room: an idle
+// wave then leaves the pending queries to it rather than starting a cohort of its own.
+static bool sibling_takes(const bfs_server_s* S, const Wave* w, int cap_slots) {
+  for (const Wave* x : w->sg->waves)
+    if (x != w && x->active && wave_can_admit(S, x, cap_slots)) return true;
+  return false;
+}
+
+// One round of a wave: admission, seeding, a burst of levels, retirement. Each wave has
+// its own scheduler thread, so a slow wave never holds back the others; the shared
+// request bookkeeping is guarded by the server lock.
+static void wave_round(bfs_server_s* S, Wave* w) {
+  std::vector<ServeReq*> admitted;
+  unsigned long long drop = 0;
   {
     std::unique_lock<std::mutex> lk(S->mu);
-    for (Wave* w : S->waves) {
-      // pending cancellations
-      for (auto it = w->pending.begin(); it != w->pending.end();) {
-        if ((*it)->cancel) {
-          finish_req(S, *it, BFS_ERR_CANCELLED, "cancelled before admission");
-          it = w->pending.erase(it);
-        } else {
-          ++it;
-        }
+    std::deque<ServeReq*>& pending = w->sg->pending;
+    // pending cancellations
+    for (auto it = pending.begin(); it != pending.end();) {
+      if ((*it)->cancel) {
+        finish_req(S, *it, BFS_ERR_CANCELLED, "cancelled before admission");
+        it = pending.erase(it);
+      } else {
+        ++it;
       }
-      Admit ad{w, {}};
-      const int cap_slots = std::max(1, std::min(kMaxWave, S->cfg.max_wave > 0 ? S->cfg.max_wave : kMaxWave));
-      while (!w->pending.empty()) {
-        int free_bit = -1;
-        for (int b = 0; b < cap_slots; ++b)
-          if (!((w->used >> b) & 1ull)) {
-            free_bit = b;
-            break;
-          }
-        if (free_bit < 0) break;
-        ServeReq* r = w->pending.front();
-        const size_t need = r->host_out ? (size_t)w->g.n * 8 : 0;
-        if (S->cfg.memory_cap_bytes && S->mem_fixed + S->mem_used + need > S->cfg.memory_cap_bytes)
-          break;  // FIFO: wait until running queries release memory
-        if (need) {
-          if (cudaMalloc(reinterpret_cast<void**>(&r->dev_lvl), (size_t)w->g.n * 4) != cudaSuccess ||
-              cudaMalloc(reinterpret_cast<void**>(&r->dev_par), (size_t)w->g.n * 4) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(r->dev_lvl);
-            r->dev_lvl = nullptr;
-            break;  // device memory is short: retry once slots complete
-          }
-          r->charged = need;
-          S->mem_used += need;
-          S->mem_peak = std::max(S->mem_peak, S->mem_used + S->mem_fixed);
-        } else {
-          r->dev_lvl = r->user_lvl;
-          r->dev_par = r->user_par;
+    }
+    const int cap_slots = std::max(1, std::min(kMaxWave, S->cfg.max_wave > 0 ? S->cfg.max_wave : kMaxWave));
+    const bool may_admit = wave_can_admit(S, w, cap_slots) && (w->active || !sibling_takes(S, w, cap_slots));
+    while (may_admit && !pending.empty()) {
+      int free_bit = -1;
+      for (int b = 0; b < cap_slots; ++b)
+        if (!((w->used >> b) & 1ull)) {
+          free_bit = b;
+          break;
         }
-        w->pending.pop_front();
-        r->slot = free_bit;
-        r->start = w->active ? w->t : 0;
-        r->state = kRunning;
-        r->t_admit = Clock::now();
-        w->used |= 1ull << free_bit;
-        w->slot_req[free_bit] = r;
-        ad.reqs.push_back(r);
-        ++S->running;
-        S->max_running = std::max(S->max_running, S->running);
+      if (free_bit < 0) break;
+      ServeReq* r = pending.front();
+      const size_t need = r->host_out ? (size_t)w->g.n * 8 : 0;
+      if (S->cfg.memory_cap_bytes && S->mem_fixed + S->mem_used + need > S->cfg.memory_cap_bytes)
+        break;  // FIFO: wait until running queries release memory
+      if (need) {
+        if (cudaMalloc(reinterpret_cast<void**>(&r->dev_lvl), (size_t)w->g.n * 4) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&r->dev_par), (size_t)w->g.n * 4) != cudaSuccess) {
+          cudaGetLastError();
+          cudaFree(r->dev_lvl);
+          r->dev_lvl = nullptr;
+          break;  // device memory is short: retry once slots complete
+        }
+        r->charged = need;
+        S->mem_used += need;
+        S->mem_peak = std::max(S->mem_peak, S->mem_used + S->mem_fixed);
+      } else {
+        r->dev_lvl = r->user_lvl;
+        r->dev_par = r->user_par;
       }
-      if (!ad.reqs.empty()) admits.push_back(ad);
-      // With nobody waiting for this wave (or no slot to admit into), run several levels
-      // before looking again: a root's bit never returns to a frontier once its search is
-      // done, so the alive mask after the burst still shows every query that finished in it.
-      const int lpr = S->cfg.levels_per_round > 0 ? S->cfg.levels_per_round : 8;
-      bool slot_free = false;
-      for (int b = 0; b < cap_slots; ++b) slot_free |= !((w->used >> b) & 1ull);
-      w->burst = (w->pending.empty() || !slot_free) ? lpr : 1;
+      pending.pop_front();
+      r->slot = free_bit;
+      r->start = w->active.load() ? w->t.load() : 0;
+      r->state = kRunning;
+      r->t_admit = Clock::now();
+      w->used |= 1ull << free_bit;
+      w->slot_req[free_bit] = r;
+      admitted.push_back(r);
+      ++S->running;
+      S->max_running = std::max(S->max_running, S->running);
+    }
+    // When this wave cannot take the queries that are waiting (none waiting, no slot, or
+    // its cohort is too old), run several levels before looking again: a root's bit never
+    // returns to a frontier once its search is done, so the alive mask after the burst
+    // still shows every query that finished in it.
+    const int lpr = S->cfg.levels_per_round > 0 ? S->cfg.levels_per_round : 8;
+    w->burst = (pending.empty() || !wave_can_admit(S, w, cap_slots)) ? lpr : 1;
+    for (int b = 0; b < kMaxWave; ++b) {
+      ServeReq* r = w->slot_req[b];
+      if (r && r->cancel && r->state == kRunning) drop |= 1ull << b;
     }
   }
-  // seeding (outside the lock; only this thread touches the waves' device state)
-  for (Admit& ad : admits) {
-    Wave* w = ad.w;
+  // seeding (outside the lock; only this wave's thread touches its device state)
+  if (!admitted.empty()) {
     const bool fresh = !w->active;
     if (fresh) {
       w->t = 0;
-      for (ServeReq* r : ad.reqs) r->start = 0;
+      for (ServeReq* r : admitted) r->start = 0;
     } else if (w->pending_clear) {
       launch_clear_bits(w->b.visited, w->g.n, w->pending_clear, w->g.num_sms, w->stream);
     }
     w->pending_clear = 0;
     std::map<int32_t, unsigned long long> masks;
-    for (ServeReq* r : ad.reqs) {
+    for (ServeReq* r : admitted) {
       w->slots_host->lvl[r->slot] = r->dev_lvl;
       w->slots_host->par[r->slot] = r->dev_par;
       w->slots_host->start[r->slot] = r->start;
@@ -253,89 +293,75 @@ static void scheduler_round(bfs_server_s* S) {
     w->active = true;
   }
   // running-query cancellation: drop the bits at this boundary (no later writes)
-  {
+  if (drop && w->active) {
+    launch_clear_bits(w->b.fmask[w->t.load() % 3], w->g.n, drop, w->g.num_sms, w->stream);
+    launch_clear_bits(w->b.visited, w->g.n, drop, w->g.num_sms, w->stream);
+    cudaStreamSynchronize(w->stream);
     std::unique_lock<std::mutex> lk(S->mu);
-    for (Wave* w : S->waves) {
-      unsigned long long drop = 0;
-      for (int b = 0; b < kMaxWave; ++b) {
-        ServeReq* r = w->slot_req[b];
-        if (r && r->cancel && r->state == kRunning) drop |= 1ull << b;
+    for (int b = 0; b < kMaxWave; ++b)
+      if ((drop >> b) & 1ull) {
+        finish_req(S, w->slot_req[b], BFS_ERR_CANCELLED, "cancelled while running");
+        w->slot_req[b] = nullptr;
+        w->used &= ~(1ull << b);
+        --S->running;
       }
-      if (drop && w->active) {
-        launch_clear_bits(w->b.fmask[w->t % 3], w->g.n, drop, w->g.num_sms, w->stream);
-        launch_clear_bits(w->b.visited, w->g.n, drop, w->g.num_sms, w->stream);
-        for (int b = 0; b < kMaxWave; ++b)
-          if ((drop >> b) & 1ull) {
-            cudaStreamSynchronize(w->stream);
-            finish_req(S, w->slot_req[b], BFS_ERR_CANCELLED, "cancelled while running");
-            w->slot_req[b] = nullptr;
-            w->used &= ~(1ull << b);
-            --S->running;
-          }
-      }
-    }
   }
-  // a burst of levels of every active wave; launch all, then wait for all
-  for (Wave* w : S->waves) {
-    if (!w->active) continue;
-    for (int i = 0; i < w->burst; ++i) {
-      if (w->g.off64)
-        wave_launch_level<int64_t>(w);
-      else
-        wave_launch_level<int32_t>(w);
-    }
-    cudaMemcpyAsync(w->ctl_host, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, w->stream);
+  if (!w->active) {
+    S->cv_done.notify_all();
+    return;
   }
-  for (Wave* w : S->waves) {
-    if (!w->active) continue;
-    cudaError_t e = cudaStreamSynchronize(w->stream);
-    std::vector<int> retire;
-    unsigned long long alive = 0;
-    if (e == cudaSuccess) {
-      const int t_expanded = w->t;  // first frontier of the burst
-      w->t = w->ctl_host->level - 1;
-      alive = w->ctl_host->alive[w->t & 1];
-      for (int b = 0; b < kMaxWave; ++b) {
-        ServeReq* r = w->slot_req[b];
-        if (r && r->start <= t_expanded && !((alive >> b) & 1ull)) retire.push_back(b);
-      }
-      if (!w->ctl_host->cont) w->active = false;
+  // a burst of levels
+  for (int i = 0; i < w->burst; ++i) {
+    if (w->g.off64)
+      wave_launch_level<int64_t>(w);
+    else
+      wave_launch_level<int32_t>(w);
+  }
+  cudaMemcpyAsync(w->ctl_host, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, w->stream);
+  cudaError_t e = cudaStreamSynchronize(w->stream);
+  std::vector<int> retire;
+  if (e == cudaSuccess) {
+    const int t_expanded = w->t;  // first frontier of the burst
+    w->t = w->ctl_host->level - 1;
+    const unsigned long long alive = w->ctl_host->alive[w->t.load() & 1];
+    for (int b = 0; b < kMaxWave; ++b) {
+      ServeReq* r = w->slot_req[b];
+      if (r && r->start <= t_expanded && !((alive >> b) & 1ull)) retire.push_back(b);
     }
+    if (!w->ctl_host->cont) w->active = false;
     // statistics and host copies of the retiring slots
-    if (e == cudaSuccess) {
-      for (int b : retire) {
-        ServeReq* r = w->slot_req[b];
-        if (w->g.off64)
-          launch_level_stats<int64_t>(reinterpret_cast<const int64_t*>(w->g.off), w->g.n, r->dev_lvl,
-                                      w->stats_dev + 3 * b, w->g.num_sms, w->stream);
-        else
-          launch_level_stats<int32_t>(reinterpret_cast<const int32_t*>(w->g.off), w->g.n, r->dev_lvl,
-                                      w->stats_dev + 3 * b, w->g.num_sms, w->stream);
-        cudaMemcpyAsync(w->stats_host + 3 * b, w->stats_dev + 3 * b, sizeof(long long) * 3, cudaMemcpyDeviceToHost,
-                        w->stream);
-        if (r->host_out) {
-          cudaMemcpyAsync(r->user_lvl, r->dev_lvl, (size_t)w->g.n * 4, cudaMemcpyDeviceToHost, w->stream);
-          cudaMemcpyAsync(r->user_par, r->dev_par, (size_t)w->g.n * 4, cudaMemcpyDeviceToHost, w->stream);
-        }
+    for (int b : retire) {
+      ServeReq* r = w->slot_req[b];
+      if (w->g.off64)
+        launch_level_stats<int64_t>(reinterpret_cast<const int64_t*>(w->g.off), w->g.n, r->dev_lvl,
+                                    w->stats_dev + 3 * b, w->g.num_sms, w->stream);
+      else
+        launch_level_stats<int32_t>(reinterpret_cast<const int32_t*>(w->g.off), w->g.n, r->dev_lvl,
+                                    w->stats_dev + 3 * b, w->g.num_sms, w->stream);
+      cudaMemcpyAsync(w->stats_host + 3 * b, w->stats_dev + 3 * b, sizeof(long long) * 3, cudaMemcpyDeviceToHost,
+                      w->stream);
+      if (r->host_out) {
+        cudaMemcpyAsync(r->user_lvl, r->dev_lvl, (size_t)w->g.n * 4, cudaMemcpyDeviceToHost, w->stream);
+        cudaMemcpyAsync(r->user_par, r->dev_par, (size_t)w->g.n * 4, cudaMemcpyDeviceToHost, w->stream);
       }
-      if (!retire.empty()) e = cudaStreamSynchronize(w->stream);
     }
-    std::unique_lock<std::mutex> lk(S->mu);
-    S->levels += w->burst;
-    if (e != cudaSuccess) {
-      const std::string msg = std::string("CUDA error in serving wave: ") + cudaGetErrorString(e);
-      cudaGetLastError();
-      for (int b = 0; b < kMaxWave; ++b)
-        if (w->slot_req[b]) {
-          finish_req(S, w->slot_req[b], BFS_ERR_CUDA, msg);
-          w->slot_req[b] = nullptr;
-          --S->running;
-        }
-      w->used = 0;
-      w->active = false;
-      S->fatal = msg;
-      continue;
-    }
+    if (!retire.empty()) e = cudaStreamSynchronize(w->stream);
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  S->levels += w->burst;
+  if (e != cudaSuccess) {
+    const std::string msg = std::string("CUDA error in serving wave: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    for (int b = 0; b < kMaxWave; ++b)
+      if (w->slot_req[b]) {
+        finish_req(S, w->slot_req[b], BFS_ERR_CUDA, msg);
+        w->slot_req[b] = nullptr;
+        --S->running;
+      }
+    w->used = 0;
+    w->active = false;
+    S->fatal = msg;
+  } else {
     for (int b : retire) {
       ServeReq* r = w->slot_req[b];
       r->stats.edges_traversed = w->stats_host[3 * b + 0] / 2;
@@ -344,6 +370,8 @@ static void scheduler_round(bfs_server_s* S) {
       r->stats.device_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_admit).count();
       r->stats.expand_ms = r->stats.device_ms;
       finish_req(S, r, BFS_OK, "");
+      w->sg->depth_sum += r->stats.depth;
+      ++w->sg->depth_n;
       w->slot_req[b] = nullptr;
       w->used &= ~(1ull << b);
       w->pending_clear |= 1ull << b;
@@ -354,26 +382,29 @@ static void scheduler_round(bfs_server_s* S) {
   S->cv_done.notify_all();
 }
 
-static void scheduler_main(bfs_server_s* S) {
+static void wave_main(bfs_server_s* S, Wave* w) {
   cudaSetDevice(S->device);
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      const int cap_slots = std::max(1, std::min(kMaxWave, S->cfg.max_wave > 0 ? S->cfg.max_wave : kMaxWave));
       auto busy = [&] {
-        for (Wave* w : S->waves)
-          if (w->active || !w->pending.empty()) return true;
-        return false;
+        if (w->active) return true;
+        if (w->sg->pending.empty()) return false;
+        for (ServeReq* r : w->sg->pending)
+          if (r->cancel) return true;
+        return S->stop || !sibling_takes(S, w, cap_slots);
       };
-      S->cv_work.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || busy(); });
-      if (S->stop && !busy()) break;
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || busy(); });
+      if (S->stop && !w->active) {  // drain: cancel what has not started, then leave
+        for (ServeReq* r : w->sg->pending) finish_req(S, r, BFS_ERR_CANCELLED, "server shutting down");
+        w->sg->pending.clear();
+        S->cv_done.notify_all();
+        break;
+      }
       if (!busy()) continue;
-      if (S->stop)  // drain: cancel what has not started
-        for (Wave* w : S->waves) {
-          for (ServeReq* r : w->pending) finish_req(S, r, BFS_ERR_CANCELLED, "server shutting down");
-          w->pending.clear();
-        }
     }
-    scheduler_round(S);
+    wave_round(S, w);
   }
 }
 
@@ -407,36 +438,52 @@ GBFS_API bfs_status bfs_serve_add_graph(bfs_server_t S, bfs_graph_t G, int* grap
   if (S->device >= 0 && G->g.device != S->device) return fail(BFS_ERR_INVALID_ARG, "graphs must share one device");
   cudaError_t e = cudaSetDevice(G->g.device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  const size_t need = batch_bufs_bytes(G->g);
+  const int n_waves = S->cfg.waves_per_graph > 0 ? S->cfg.waves_per_graph : 2;
+  const size_t need = batch_bufs_bytes(G->g) * (size_t)n_waves;
   if (S->cfg.memory_cap_bytes && S->mem_fixed + need > S->cfg.memory_cap_bytes)
     return fail(BFS_ERR_OOM, "the graph's wave state exceeds the server's memory budget");
-  auto* w = new (std::nothrow) Wave();
-  if (!w) return fail(BFS_ERR_OOM, "host allocation");
-  w->G = G;
-  w->g = G->g;
-  e = alloc_batch_bufs(w->g, w->b);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->slots_host), sizeof(WaveSlots), 0);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->ctl_host), sizeof(BatchCtl), 0);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->seeds_host), sizeof(RootSeed) * kMaxWave, 0);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->stats_host), sizeof(long long) * 3 * kMaxWave, 0);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&w->stats_dev), sizeof(long long) * 3 * kMaxWave);
-  if (e != cudaSuccess) {
-    free_wave(w);
-    return cuda_fail(e, "wave state");
+  auto* sg = new (std::nothrow) ServeGraph();
+  if (!sg) return fail(BFS_ERR_OOM, "host allocation");
+  sg->id = (int)S->graphs.size();
+  sg->g = G->g;
+  for (int i = 0; i < n_waves; ++i) {
+    auto* w = new (std::nothrow) Wave();
+    if (!w) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+      w->G = G;
+      w->sg = sg;
+      w->g = G->g;
+      e = alloc_batch_bufs(w->g, w->b);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->slots_host), sizeof(WaveSlots), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&w->ctl_host), sizeof(BatchCtl), 0);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(reinterpret_cast<void**>(&w->seeds_host), sizeof(RootSeed) * kMaxWave, 0);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(reinterpret_cast<void**>(&w->stats_host), sizeof(long long) * 3 * kMaxWave, 0);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&w->stats_dev), sizeof(long long) * 3 * kMaxWave);
+    if (e != cudaSuccess) {
+      free_wave(w);
+      for (Wave* x : sg->waves) free_wave(x);
+      delete sg;
+      return cuda_fail(e, "wave state");
+    }
+    for (int b = 0; b < kMaxWave; ++b) {
+      w->slots_host->lvl[b] = w->slots_host->par[b] = nullptr;
+      w->slots_host->start[b] = 0;
+    }
+    w->shape = G->batch_shape;
+    w->grid = w->g.off64 ? batch_expand_grid<int64_t>(w->shape, w->g.num_sms)
+                         : batch_expand_grid<int32_t>(w->shape, w->g.num_sms);
+    sg->waves.push_back(w);
   }
-  for (int b = 0; b < kMaxWave; ++b) {
-    w->slots_host->lvl[b] = w->slots_host->par[b] = nullptr;
-    w->slots_host->start[b] = 0;
-  }
-  w->shape = G->batch_shape;
-  w->grid = w->g.off64 ? batch_expand_grid<int64_t>(w->shape, w->g.num_sms)
-                       : batch_expand_grid<int32_t>(w->shape, w->g.num_sms);
   S->device = G->g.device;
   S->mem_fixed += need;
   S->mem_peak = std::max(S->mem_peak, S->mem_fixed + S->mem_used);
-  *graph_id = (int)S->waves.size();
-  S->waves.push_back(w);
+  for (Wave* w : sg->waves) S->waves.push_back(w);
+  S->graphs.push_back(sg);
+  *graph_id = sg->id;
   return BFS_OK;
 }
 
@@ -445,12 +492,12 @@ GBFS_API bfs_status bfs_serve_submit(bfs_server_t S, int graph_id, int32_t root,
   clear_last_error();
   if (!S || !levels || !parents || !ticket) return fail(BFS_ERR_INVALID_ARG, "NULL argument");
   std::unique_lock<std::mutex> lk(S->mu);
-  if (graph_id < 0 || graph_id >= (int)S->waves.size()) return fail(BFS_ERR_NOT_FOUND, "unknown graph id");
-  Wave* w = S->waves[graph_id];
-  if (root < 0 || root >= w->g.n) return fail(BFS_ERR_INVALID_ARG, "root outside [0, n)");
+  if (graph_id < 0 || graph_id >= (int)S->graphs.size()) return fail(BFS_ERR_NOT_FOUND, "unknown graph id");
+  ServeGraph* sg = S->graphs[graph_id];
+  if (root < 0 || root >= sg->g.n) return fail(BFS_ERR_INVALID_ARG, "root outside [0, n)");
   if (S->stop) return fail(BFS_ERR_CANCELLED, "server shutting down");
   size_t queued = 0;
-  for (Wave* x : S->waves) queued += x->pending.size();
+  for (ServeGraph* x : S->graphs) queued += x->pending.size();
   if ((int64_t)queued >= S->cfg.queue_capacity) {
     ++S->rejected;
     return fail(BFS_ERR_BUSY, "request queue is full");
@@ -477,13 +524,13 @@ GBFS_API bfs_status bfs_serve_submit(bfs_server_t S, int graph_id, int32_t root,
   }
   ++S->submitted;
   S->reqs[r->ticket] = r;
-  w->pending.push_back(r);
+  sg->pending.push_back(r);
   if (!S->started) {
     S->started = true;
-    S->th = std::thread(scheduler_main, S);
+    for (Wave* x : S->waves) S->threads.emplace_back(wave_main, S, x);
   }
   *ticket = r->ticket;
-  S->cv_work.notify_one();
+  S->cv_work.notify_all();
   return BFS_OK;
 }
 
@@ -530,7 +577,7 @@ GBFS_API bfs_status bfs_serve_cancel(bfs_server_t S, uint64_t ticket) {
   if (s != BFS_OK) return s;
   if (r->state != kDone) {
     r->cancel = true;
-    S->cv_work.notify_one();
+    S->cv_work.notify_all();
   }
   return BFS_OK;
 }
@@ -595,9 +642,11 @@ GBFS_API bfs_status bfs_serve_destroy(bfs_server_t S) {
     S->stop = true;
     S->cv_work.notify_all();
   }
-  if (S->th.joinable()) S->th.join();
+  for (auto& th : S->threads)
+    if (th.joinable()) th.join();
   if (S->device >= 0) cudaSetDevice(S->device);
   for (Wave* w : S->waves) free_wave(w);
+  for (ServeGraph* sg : S->graphs) delete sg;
   for (auto& kv : S->reqs) {
     if (kv.second->charged) {
       cudaFree(kv.second->dev_lvl);
