@@ -102,11 +102,16 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *     return to top-down once frontier vertices x BETA < n. Results are the same BFS
  *     (levels identical; parents valid). Default 0: every level top-down (Algorithm 3).
  *   BFS_OPT_ALPHA (default 8; swept on GB300: 8 beat 2, 4, 6, 14 on R-MAT and uniform graphs),
- *   BFS_OPT_BETA (default 24): the switching thresholds. */
+ *   BFS_OPT_BETA (default 24): the switching thresholds.
+ *   BFS_OPT_WAIT_LIMIT: polls a CTA makes at a grid barrier of a persistent search before it
+ *     gives up (default 2^27, seconds). On expiry the search stops and bfs_run returns
+ *     BFS_ERR_TIMEOUT; the device stays usable. 0 makes every wait give up at once (used to
+ *     test that path without hanging anything). */
 #define BFS_OPT_LOOP 1
 #define BFS_OPT_BOTTOM_UP 2
 #define BFS_OPT_ALPHA 3
 #define BFS_OPT_BETA 4
+#define BFS_OPT_WAIT_LIMIT 5
 #define BFS_LOOP_PERSISTENT 0
 #define BFS_LOOP_GRAPH 1
 #define BFS_LOOP_HOST 2

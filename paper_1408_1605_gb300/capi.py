@@ -28,6 +28,7 @@ BFS_OPT_LOOP = 1
 BFS_OPT_BOTTOM_UP = 2
 BFS_OPT_ALPHA = 3
 BFS_OPT_BETA = 4
+BFS_OPT_WAIT_LIMIT = 5
 BFS_LOOP_PERSISTENT = 0
 BFS_LOOP_GRAPH = 1
 BFS_LOOP_HOST = 2

@@ -252,6 +252,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.beta = G->beta;
     pa.allow_bottom_up = G->bottom_up;
     pa.probe_mode = G->probe_mode;
+    pa.spin_limit = G->wait_limit;
     int& pg = G->pgrid[G->bottom_up ? 1 : 0];
     if (!pg) pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
     if ((e = launch_persistent<OffT>(G->shape, pa, pg, st)) != cudaSuccess)
@@ -555,6 +556,10 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
       if (value < 1 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "alpha/beta outside [1, 2^20]");
       (option == BFS_OPT_ALPHA ? G->alpha : G->beta) = (int)value;
       return BFS_OK;
+    case BFS_OPT_WAIT_LIMIT:
+      if (value < 0 || value > (1ll << 40)) return fail(BFS_ERR_INVALID_ARG, "wait limit outside [0, 2^40]");
+      G->wait_limit = value;
+      return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");
 }
@@ -567,6 +572,7 @@ GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* val
     case BFS_OPT_BOTTOM_UP: *value = G->bottom_up; return BFS_OK;
     case BFS_OPT_ALPHA: *value = G->alpha; return BFS_OK;
     case BFS_OPT_BETA: *value = G->beta; return BFS_OK;
+    case BFS_OPT_WAIT_LIMIT: *value = G->wait_limit; return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");
 }

@@ -429,11 +429,10 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
 // Persistent search: every level in one cooperative launch, with a grid barrier between
 // levels and a per-level choice between the top-down step above and a bottom-up step.
 
-// Grid barrier (sense reversal) with a bounded wait: after kBarrierSpinLimit polls the CTA
-// records kErrTimeout and leaves; the search then stops at the next level boundary.
-constexpr long long kBarrierSpinLimit = 1ll << 27;
-
-__device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks) {
+// Grid barrier (sense reversal) with a bounded wait: after spin_limit polls the CTA records
+// kErrTimeout and leaves; every CTA then stops at the next level boundary (all later waits
+// are bounded too). A limit of 0 makes every arrival but the last give up at once.
+__device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks, long long spin_limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = &c->bar_gen;
@@ -447,7 +446,7 @@ __device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks) {
     } else {
       long long spins = 0;
       while (*gen == g) {
-        if (++spins > kBarrierSpinLimit) {
+        if (++spins > spin_limit) {
           atomicOr(&c->error, kErrTimeout);
           break;
         }
@@ -576,12 +575,22 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_
   long long seen_deg = 0;          // degree sum of every frontier so far (same on all CTAs)
   long long prev_nf = 0;
   bool bottom_up = false;
+  __shared__ long long s_nf, s_r;
+  __shared__ int s_stop;
   for (int it = 0;; ++it) {
     const int cur3 = it % 3, nxt3 = (it + 1) % 3, old3 = (it + 2) % 3;
-    const unsigned long long pc = *(volatile unsigned long long*)&c->counter[cur3];
-    const long long nf = a.pk.count(pc);
-    const long long r = a.pk.edges(pc);
-    if (nf == 0 || (*(volatile unsigned*)&c->error & kErrTimeout)) break;
+    // Loop control is read once per CTA and broadcast, so that every thread of the CTA takes
+    // the same path even when a barrier wait has expired and other CTAs are still writing.
+    if (threadIdx.x == 0) {
+      const unsigned long long pc = *(volatile unsigned long long*)&c->counter[cur3];
+      s_nf = a.pk.count(pc);
+      s_r = a.pk.edges(pc);
+      s_stop = s_nf == 0 || (*(volatile unsigned*)&c->error & kErrTimeout) != 0;
+    }
+    __syncthreads();
+    const long long nf = s_nf;
+    const long long r = s_r;
+    if (s_stop) break;
     seen_deg += r;
     // direction choice (Beamer's heuristic): bottom-up while the frontier's edges are a
     // large share of the unexplored ones, back to top-down once the frontier shrinks
@@ -619,7 +628,7 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_
     else
       td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &c->error, io, smem, sh, blockIdx.x,
                                       gridDim.x);
-    grid_barrier(c, gridDim.x);
+    grid_barrier(c, gridDim.x, a.spin_limit);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (it < kMaxLevelTimes) {
         unsigned long long ns;

@@ -83,6 +83,7 @@ struct PersistArgs {
   int beta;             // back to top-down when frontier vertices * beta < n (and shrinking)
   int allow_bottom_up;
   int probe_mode;
+  long long spin_limit;  // polls of a grid-barrier wait before it gives up (kErrTimeout)
 };
 
 struct ExpandShape {

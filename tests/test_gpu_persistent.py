@@ -153,3 +153,25 @@ def test_level_profile_matches_oracle_level_sizes(torch_cuda, oracle_mod, graphs
             assert all(p["ms"] >= 0 for p in prof) and sum(p["ms"] for p in prof) <= st.device_ms + 0.05
         finally:
             capi.bfs_graph_destroy(h)
+
+
+def test_barrier_wait_expiry_reports_timeout(torch_cuda, oracle_mod, graphs_mod):
+    """Failure detection without a fault: with a wait limit of 0 every grid-barrier wait but
+    the last arrival's gives up at once, the search stops and bfs_run reports
+    BFS_ERR_TIMEOUT; the same graph then searches correctly with the default limit."""
+    from paper_1408_1605_gb300 import capi
+
+    g = graphs_mod.rmat(14, 16, seed=23)
+    r = int(graphs_mod.pick_roots(g, 1, 4)[0])
+    h = _upload(capi, g, "persistent-td")
+    try:
+        default = capi.bfs_graph_get_option(h, capi.BFS_OPT_WAIT_LIMIT)
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_WAIT_LIMIT, 0)
+        lv = torch_cuda.empty(g.n, dtype=torch_cuda.int32, device="cuda")
+        with pytest.raises(capi.BfsError) as e:
+            capi.bfs_run(h, r, lv, lv.clone(), want_stats=True)
+        assert e.value.status == 5  # BFS_ERR_TIMEOUT
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_WAIT_LIMIT, default)
+        _check(capi, oracle_mod, torch_cuda, h, g, r)
+    finally:
+        capi.bfs_graph_destroy(h)
