@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool ordered = nn * 32 > a.n;
+  const bool ordered = nn * 8 > a.n;  // a full pass pays only when a large share of vertices was claimed
   const int64_t items = ordered ? (a.n + 31) / 32 : (nn + 31) / 32;
   for (int64_t w = gwarp; w < items; w += nwarps) {
     int32_t v = -1;
