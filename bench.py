@@ -59,15 +59,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, relabel: bool):
     """Per-launch DRAM bytes of the expansion kernel from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    was taken on the current kernel source and the same vertex order (else None)."""
     path = os.path.join(PROFILES, "k_expand_traffic.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     if not m_hash or m_hash.group(1) != kernel_source_hash():
+        return None
+    m_order = re.search(r"vertex_order:\s*(\S+)", text)
+    if (m_order.group(1) if m_order else "as-generated") != ("relabelled" if relabel else "as-generated"):
         return None
     m = re.search(rf"traffic_per_launch\[{re.escape(workload)}\]:\s*([0-9.eE+]+)", text)
     return float(m.group(1)) if m else None
@@ -196,9 +199,22 @@ def run_reference(args, wl, g, roots, rank):
     return 0
 
 
+def use_relabel(kind: str, mode: str) -> bool:
+    """Degree relabelling (BFS_RELABEL_DEGREE) pays on skewed degree distributions (R-MAT);
+    on uniform random graphs and grids it was measured slightly slower, so auto leaves them."""
+    return mode == "on" or (mode == "auto" and kind == "rmat")
+
+
+def create_graph(capi, g, relabel: bool) -> int:
+    return capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz,
+                                 capi.BFS_OFFSETS_INT64 | (capi.BFS_RELABEL_DEGREE if relabel else 0))
+
+
 def config_for(wl, g, args) -> dict:
     return {"workload": wl.name, "description": wl.description, "n_vertices": g.n, "csr_entries": g.nnz,
             "offsets": "int64" if g.nnz > 2**31 - 1 else "int32", "roots": args.steps,
+            "vertex_order": "relabelled by degree at graph creation" if use_relabel(wl.kind, args.relabel)
+            else "as generated",
             "l2_flush": "inputs larger than L2 (column array and per-root outputs exceed the 129 MB L2)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -220,6 +236,8 @@ def main() -> int:
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-levels-per-round", type=int, default=0)
+    ap.add_argument("--relabel", default="auto", choices=["auto", "on", "off"],
+                    help="BFS_RELABEL_DEGREE at graph creation (auto: R-MAT graphs only)")
     args = ap.parse_args()
     if args.mode == "serve":
         return run_serve(args)
@@ -259,8 +277,10 @@ def main() -> int:
     timed_roots = pool[args.warmup * world:][rank::world]
 
     t = time.perf_counter()
-    h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
-    log(f"[bench] upload {time.perf_counter() - t:.1f}s")
+    relabel = use_relabel(wl.kind, args.relabel)
+    h = create_graph(capi, g, relabel)
+    tune_class = wl.kind + ("-relabel" if relabel else "")
+    log(f"[bench] upload{' + relabel' if relabel else ''} {time.perf_counter() - t:.1f}s")
     off_bytes = 8 if g.nnz > 2**31 - 1 else 4
     lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
     pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
@@ -269,7 +289,7 @@ def main() -> int:
         from paper_1408_1605_gb300 import autotune
 
         tune_roots = pool[: max(3, min(len(pool), 3))]
-        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, wl.kind, g.n, tune_roots, lv, pr)
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, tune_class, g.n, tune_roots, lv, pr)
         shapes["single"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"],
                             "loop": ["persistent", "graph", "host"][rec.get("loop", 1)]}
         log(f"[bench] single-source shape {shapes['single']} ms per shape {rec.get('ms')}")
@@ -328,7 +348,7 @@ def main() -> int:
 
     batched = None
     if not args.no_batched:
-        batched = batched_leg(h, g, timed_roots, stats, None if args.no_autotune else wl.kind, shapes)
+        batched = batched_leg(h, g, timed_roots, stats, None if args.no_autotune else tune_class, shapes)
 
     # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks
     value, ms_step = hm, elapsed_ms / max(len(stats), 1)
@@ -346,7 +366,7 @@ def main() -> int:
 
     if rank == 0:
         peaks = load_peaks()
-        traffic = profiled_traffic(wl.name)
+        traffic = profiled_traffic(wl.name, relabel)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": len(stats),
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -429,7 +449,7 @@ def direction_leg(h, g, roots, single_stats, wl, args, lv, pr):
             "mean_device_ms": round(sum(s["device_ms"] for s in st) / len(st), 4),
             "mean_bottom_up_levels": round(sum(s["bottom_up_levels"] for s in st) / len(st), 2),
             "levels_equal_top_down_on_roots": 4, "levels_equal": ok, "parents_valid": parents_ok,
-            "note": "same BFS (levels identical, parents valid); large levels run bottom-up (SURVEY NEXT #1)"}
+            "note": "same BFS (levels identical, parents valid); large levels run bottom-up (Beamer direction switching)"}
 
 
 def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
@@ -486,7 +506,7 @@ def run_serve(args) -> int:
         t = time.perf_counter()
         g = WORKLOADS[nm].make()
         gs.append(g)
-        hs.append(capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64))
+        hs.append(create_graph(capi, g, use_relabel(WORKLOADS[nm].kind, args.relabel)))
         log(f"[serve] {nm}: n={g.n} nnz={g.nnz} ({time.perf_counter() - t:.1f}s)")
     n_buf = 96  # output buffers per graph, reused once their query completes
     pools = [[(torch.empty(g.n, dtype=torch.int32, device="cuda"), torch.empty(g.n, dtype=torch.int32, device="cuda"))
@@ -534,7 +554,8 @@ def run_serve(args) -> int:
                           "config": {"workload": "serve: rmat-s20, rmat-s24, grid3d-192, uniform-n8M-deg8",
                                      "roots": "seeded uniform per graph", "wave": 64,
                                      "levels_per_round": args.serve_levels_per_round or 8,
-                                     "memory_cap_bytes": 64 << 30},
+                                     "memory_cap_bytes": 64 << 30,
+                                     "relabel": args.relabel},
                           "rates": results}), flush=True)
     return 0
 
@@ -559,7 +580,7 @@ def run_multigraph(args) -> int:
     t = time.perf_counter()
     for i, sc in enumerate(scales):
         g = graphs.rmat(int(sc), 16, seed=20140806 + 300 + i)
-        h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
+        h = create_graph(capi, g, use_relabel("rmat", args.relabel))
         r = graphs.pick_roots(g, 64, graphs.root_seed(20140806 + 300 + i))
         lv = torch.empty((r.size, g.n), dtype=torch.int32, device="cuda")
         pr = torch.empty((r.size, g.n), dtype=torch.int32, device="cuda")
@@ -567,7 +588,8 @@ def run_multigraph(args) -> int:
     log(f"[multigraph] 32 graphs, scales {sorted(scales.tolist())}, built in {time.perf_counter() - t:.1f}s")
     chosen = {}
     for g, h, r, (lv, pr) in zip(gs, hs, roots, outs):
-        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, "rmat", g.n, r, lv, pr)
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, "rmat" + ("-relabel" if use_relabel("rmat", args.relabel)
+                                                                         else ""), g.n, r, lv, pr)
         chosen[int(round(np.log2(g.n)))] = rec["shape"]
     streams = [torch.cuda.Stream() for _ in range(4)]
 
@@ -618,7 +640,9 @@ def run_multigraph(args) -> int:
                           "dtype": "i32/i64",
                           "config": {"workload": "32 R-MAT graphs, scales U{14..20}, EF16, 64 roots each",
                                      "scales": sorted(int(x) for x in scales), "streams": 4,
-                                     "batch_shape_per_scale": chosen},
+                                     "batch_shape_per_scale": chosen,
+                                     "vertex_order": "relabelled by degree" if use_relabel("rmat", args.relabel)
+                                     else "as generated"},
                           "parity": {"roots_checked": checked, "ok": ok}}), flush=True)
     return 0 if ok else 1
 

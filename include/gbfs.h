@@ -63,6 +63,7 @@ typedef struct bfs_graph_s *bfs_graph_t;
 #define BFS_OFFSETS_INT32 0x4u /* row_offsets is int32[n_vertices + 1] (default) */
 #define BFS_OFFSETS_INT64 0x8u /* row_offsets is int64[n_vertices + 1] */
 #define BFS_VALIDATE 0x10u     /* also check every column id and the symmetry (O(n_entries)) */
+#define BFS_RELABEL_DEGREE 0x20u /* renumber vertices internally by degree (see bfs_graph_create) */
 
 /* Per-search statistics. edges_traversed is m_c, the TEPS numerator of Sec. 4: the
  * number of undirected input edges inside the traversed component, i.e. half the degree
@@ -81,6 +82,14 @@ typedef struct bfs_stats {
  *                BFS_*_PTRS. cols: int32 [n_entries]. n_vertices in [1, 2^31 - 1].
  *   Checked always: row_offsets[0] == 0, non-decreasing, row_offsets[n] == n_entries.
  *   Checked with BFS_VALIDATE: every column id in range and the CSR symmetric.
+ *   BFS_RELABEL_DEGREE: the library stores the graph with its vertices renumbered by
+ *     non-increasing degree (ties in input order) and every row sorted, so that in skewed
+ *     graphs the visited bits of the few vertices that end most edges share a small part of
+ *     the bitmap (the per-edge pre-check of Algorithm 3 line 6 then hits the L1 cache).
+ *     Done once here, on the device (two extra int32[n] maps; peak extra memory about
+ *     2 x n_entries x 4 bytes during the call). It is invisible to callers: roots, levels
+ *     and parents stay in the caller's numbering, and results are the same BFS (levels
+ *     identical; parents valid). bfs_expand is not available on such a graph.
  *   Failures: BFS_ERR_INVALID_ARG (NULL / sizes / flags), BFS_ERR_INVALID_GRAPH (checks
  *   above), BFS_ERR_OOM, BFS_ERR_CUDA. The call is synchronous on `stream`. */
 GBFS_API bfs_status bfs_graph_create(const void *row_offsets, const int32_t *cols, int64_t n_vertices,
@@ -106,12 +115,18 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *   BFS_OPT_WAIT_LIMIT: polls a CTA makes at a grid barrier of a persistent search before it
  *     gives up (default 2^27, seconds). On expiry the search stops and bfs_run returns
  *     BFS_ERR_TIMEOUT; the device stays usable. 0 makes every wait give up at once (used to
- *     test that path without hanging anything). */
+ *     test that path without hanging anything).
+ *   BFS_OPT_PROBE: how the visited-bit pre-check of each edge is loaded: 0 through L1
+ *     (default for BFS_RELABEL_DEGREE graphs; a stale L1 copy only costs a futile atomic),
+ *     1 from L2 only (default otherwise; sees the level's claims sooner).
+ *   BFS_OPT_RELABELED (read only): 1 if the graph was created with BFS_RELABEL_DEGREE. */
 #define BFS_OPT_LOOP 1
 #define BFS_OPT_BOTTOM_UP 2
 #define BFS_OPT_ALPHA 3
 #define BFS_OPT_BETA 4
 #define BFS_OPT_WAIT_LIMIT 5
+#define BFS_OPT_PROBE 6
+#define BFS_OPT_RELABELED 7
 #define BFS_LOOP_PERSISTENT 0
 #define BFS_LOOP_GRAPH 1
 #define BFS_LOOP_HOST 2
@@ -167,9 +182,9 @@ GBFS_API bfs_status bfs_run_batch(bfs_graph_t g, const int32_t *roots, int n_roo
  *   next_count int64 (device): receives their number.
  * `level` must be >= 1. The call synchronizes `stream` and returns after the level has
  * completed, so that range errors can be reported. Failures: BFS_ERR_INVALID_ARG (a
- * frontier vertex outside [0, n), or a frontier whose edge total exceeds the graph's
- * entry count), BFS_ERR_INVALID_GRAPH (a column id out of range), BFS_ERR_OOM,
- * BFS_ERR_CUDA. */
+ * frontier vertex outside [0, n), a frontier whose edge total exceeds the graph's entry
+ * count, or a graph created with BFS_RELABEL_DEGREE), BFS_ERR_INVALID_GRAPH (a column id
+ * out of range), BFS_ERR_OOM, BFS_ERR_CUDA. */
 GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n_frontier, int32_t level,
                                uint32_t *bitmap, int32_t *levels, int32_t *parents, int32_t *next,
                                int64_t *next_count, void *stream);

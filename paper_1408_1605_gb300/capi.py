@@ -24,11 +24,14 @@ BFS_DEVICE_PTRS = 0x2
 BFS_OFFSETS_INT32 = 0x4
 BFS_OFFSETS_INT64 = 0x8
 BFS_VALIDATE = 0x10
+BFS_RELABEL_DEGREE = 0x20
 BFS_OPT_LOOP = 1
 BFS_OPT_BOTTOM_UP = 2
 BFS_OPT_ALPHA = 3
 BFS_OPT_BETA = 4
 BFS_OPT_WAIT_LIMIT = 5
+BFS_OPT_PROBE = 6
+BFS_OPT_RELABELED = 7
 BFS_LOOP_PERSISTENT = 0
 BFS_LOOP_GRAPH = 1
 BFS_LOOP_HOST = 2

@@ -32,13 +32,14 @@ struct BatchCtl {
   unsigned long long ovf_count;   // parent events that did not fit the per-vertex slots
 };
 
-// Parent event of a claim: vertex u's edge claimed the bits `mask` of the claimed vertex.
+// Parent event of a claim: vertex u's edge claimed the bits `mask` of the claimed vertex
+// (u in caller ids, ready to be written out; the event array itself is indexed internally).
 struct ClaimEvent {
   int32_t u;
   int32_t pad;
   unsigned long long mask;
 };
-struct OvfEvent {
+struct OvfEvent {  // an event that did not fit the vertex's slots; v and u in caller ids
   int32_t v;
   int32_t u;
   unsigned long long mask;
@@ -65,6 +66,8 @@ struct BatchArgs {
   Packed pk;
   cudaGraphConditionalHandle cond;
   int use_cond;
+  const int32_t* new_id;          // caller -> internal vertex id (NULL: identity)
+  const int32_t* old_id;          // internal -> caller vertex id (NULL: identity)
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -116,14 +119,16 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.ovf_cap = b.ovf_cap;
   a.pk = g.pk;
   a.use_cond = 0;
+  a.new_id = g.new_id;
+  a.old_id = g.old_id;
   return a;
 }
 
 // Statistics of one output array: out[0] = degree sum of reached vertices (2 m_c),
 // out[1] = reached count, out[2] = max level + 1.
 template <typename OffT>
-void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long long* out, int num_sms,
-                        cudaStream_t st);
+void launch_level_stats(const OffT* off, const int32_t* new_id, int64_t n, const int32_t* levels, long long* out,
+                        int num_sms, cudaStream_t st);
 
 cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b);
 void free_batch_bufs(BatchBufs& b);
@@ -146,8 +151,8 @@ void launch_fill(int32_t* p, int64_t count, int32_t value, int num_sms, cudaStre
 template <typename OffT>
 void launch_batch_emit(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
-void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int n_slots, long long* stats,
-                        int num_sms, cudaStream_t st);
+void launch_batch_stats(const OffT* off, const int32_t* new_id, int64_t n, const WaveSlots* slots, int n_slots,
+                        long long* stats, int num_sms, cudaStream_t st);
 void launch_clear_bits(unsigned long long* visited, int64_t n, unsigned long long mask, int num_sms,
                        cudaStream_t st);
 

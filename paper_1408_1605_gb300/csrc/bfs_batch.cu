@@ -269,7 +269,7 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
   }
   if ((e = cudaEventRecord(S->ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if (stats)
-    launch_batch_stats<OffT>(reinterpret_cast<const OffT*>(g.off), g.n, S->b.slots, n_roots, S->b.stats, g.num_sms,
+    launch_batch_stats<OffT>(reinterpret_cast<const OffT*>(g.off), g.new_id, g.n, S->b.slots, n_roots, S->b.stats, g.num_sms,
                              st);
   if (host_out) {
     if ((e = cudaMemcpyAsync(levels, dl, per * n_roots * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

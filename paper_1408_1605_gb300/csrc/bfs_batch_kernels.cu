@@ -94,15 +94,16 @@ __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_see
   long long e = a.pk.edges(c->counter[cur]);
   const WaveSlots* sl = a.slots;
   for (int i = 0; i < n_seeds; ++i) {
-    const int32_t v = seeds[i].v;
+    const int32_t vc = seeds[i].v;                  // caller id (indexes the outputs)
+    const int32_t v = a.new_id ? a.new_id[vc] : vc;  // internal id
     const unsigned long long m = seeds[i].mask;
     a.visited[v] |= m;
     const unsigned long long old = a.fmask[q3][v];
     a.fmask[q3][v] = old | m;
     for (unsigned long long bits = m; bits; bits &= bits - 1) {
       const int b = __ffsll((long long)bits) - 1;
-      sl->lvl[b][v] = 0;
-      sl->par[b][v] = v;
+      sl->lvl[b][vc] = 0;
+      sl->par[b][vc] = vc;
     }
     if (old == 0) {
       const OffT o = a.off[v], d = a.off[v + 1] - o;
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
         const int32_t u = qv[klo + i];
         s_rel[i] = (int32_t)max(cum[klo + i] - e0, (OffT)0);
         s_base[i] = basep[klo + i];
-        s_u[i] = u;
+        s_u[i] = a.old_id ? __ldg(a.old_id + u) : u;  // only ever written out as a parent
         s_f[i] = F[u];
       }
       if (threadIdx.x == 0) s_rel[s] = 0x7fffffff;
@@ -264,8 +265,9 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
             const OffT e = e0 + er;
             const int32_t kk = binsearch_maxle(cum, (int64_t)klo, (int64_t)s_kend + 1, e);
             col[j] = basep[kk] + e;
-            uu[j] = qv[kk];
-            ff[j] = F[uu[j]];
+            const int32_t u = qv[kk];
+            uu[j] = a.old_id ? __ldg(a.old_id + u) : u;
+            ff[j] = F[u];
           }
         }
       }
@@ -321,12 +323,13 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
           a.ev[(size_t)v * kEventSlots + slot[j]] = ce;
         } else {
           const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
+          const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
           if ((long long)o < a.ovf_cap) {
-            a.ovf[o] = OvfEvent{v, uu[j], claimed[j]};
+            a.ovf[o] = OvfEvent{vc, uu[j], claimed[j]};
           } else {
             for (unsigned long long bits = claimed[j]; bits; bits &= bits - 1) {  // no room: write now
               const int b = __ffsll((long long)bits) - 1;
-              s_par[b][v] = uu[j];
+              s_par[b][vc] = uu[j];
             }
           }
         }
@@ -407,13 +410,19 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
   const bool ordered = nn * 8 > a.n;  // a full pass pays only when a large share of vertices was claimed
   const int64_t items = ordered ? (a.n + 31) / 32 : (nn + 31) / 32;
   for (int64_t w = gwarp; w < items; w += nwarps) {
-    int32_t v = -1;
-    if (ordered) {
-      const int64_t vv = w * 32 + lane;
-      if (vv < a.n) v = (int32_t)vv;
+    int32_t v = -1, vc = -1;  // internal id (masks, events) and caller id (outputs)
+    if (ordered) {  // consecutive caller ids: coalesced output rows
+      const int64_t x = w * 32 + lane;
+      if (x < a.n) {
+        vc = (int32_t)x;
+        v = a.new_id ? __ldg(a.new_id + vc) : vc;
+      }
     } else {
       const int64_t k = w * 32 + lane;
-      if (k < nn) v = a.qv[q3n][k];
+      if (k < nn) {
+        v = a.qv[q3n][k];
+        vc = a.old_id ? __ldg(a.old_id + v) : v;
+      }
     }
     const unsigned long long f = v >= 0 ? Fn[v] : 0ull;
     int ne = 0;
@@ -441,10 +450,10 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
       const int b = __ffsll((long long)any) - 1;
       any &= any - 1;
       if ((f >> b) & 1ull) {
-        s_lvl[b][v] = L - s_start[b];
+        s_lvl[b][vc] = L - s_start[b];
 #pragma unroll
         for (int k = 0; k < kEventSlots; ++k)
-          if ((em[k] >> b) & 1ull) s_par[b][v] = eu[k];
+          if ((em[k] >> b) & 1ull) s_par[b][vc] = eu[k];
       }
     }
   }
@@ -535,7 +544,8 @@ int batch_expand_grid(int shape, int num_sms) {
 // Per-slot statistics from the outputs: stats[3 b + 0] = sum of degrees of reached
 // vertices (2 m_c), [3 b + 1] = reached count, [3 b + 2] = max level + 1.
 template <typename OffT>
-__global__ void k_batch_stats(const OffT* __restrict__ off, int64_t n, const WaveSlots* slots, long long* stats) {
+__global__ void k_batch_stats(const OffT* __restrict__ off, const int32_t* __restrict__ new_id, int64_t n,
+                              const WaveSlots* slots, long long* stats) {
   __shared__ long long s_red[3][32];
   const int b = blockIdx.y;
   const int32_t* lv = slots->lvl[b];
@@ -543,7 +553,8 @@ __global__ void k_batch_stats(const OffT* __restrict__ off, int64_t n, const Wav
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t l = lv[v];
     if (l >= 0) {
-      e2 += (long long)(off[v + 1] - off[v]);
+      const int64_t x = new_id ? new_id[v] : v;  // the outputs are in caller ids
+      e2 += (long long)(off[x + 1] - off[x]);
       ++reached;
       depth = max(depth, (long long)l + 1);
     }
@@ -574,22 +585,23 @@ __global__ void k_batch_stats(const OffT* __restrict__ off, int64_t n, const Wav
 }
 
 template <typename OffT>
-void launch_batch_stats(const OffT* off, int64_t n, const WaveSlots* slots, int n_slots, long long* stats,
-                        int num_sms, cudaStream_t st) {
+void launch_batch_stats(const OffT* off, const int32_t* new_id, int64_t n, const WaveSlots* slots, int n_slots,
+                        long long* stats, int num_sms, cudaStream_t st) {
   cudaMemsetAsync(stats, 0, sizeof(long long) * 3 * n_slots, st);
   dim3 grid((unsigned)std::max(1, num_sms * 2 / std::max(1, n_slots / 8)), (unsigned)n_slots);
-  k_batch_stats<OffT><<<grid, 256, 0, st>>>(off, n, slots, stats);
+  k_batch_stats<OffT><<<grid, 256, 0, st>>>(off, new_id, n, slots, stats);
 }
 
 template <typename OffT>
-__global__ void k_level_stats(const OffT* __restrict__ off, int64_t n, const int32_t* __restrict__ lv,
-                              long long* out) {
+__global__ void k_level_stats(const OffT* __restrict__ off, const int32_t* __restrict__ new_id, int64_t n,
+                              const int32_t* __restrict__ lv, long long* out) {
   __shared__ long long s_red[3][32];
   long long e2 = 0, reached = 0, depth = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t l = lv[v];
     if (l >= 0) {
-      e2 += (long long)(off[v + 1] - off[v]);
+      const int64_t x = new_id ? new_id[v] : v;  // the outputs are in caller ids
+      e2 += (long long)(off[x + 1] - off[x]);
       ++reached;
       depth = max(depth, (long long)l + 1);
     }
@@ -620,10 +632,10 @@ __global__ void k_level_stats(const OffT* __restrict__ off, int64_t n, const int
 }
 
 template <typename OffT>
-void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long long* out, int num_sms,
-                        cudaStream_t st) {
+void launch_level_stats(const OffT* off, const int32_t* new_id, int64_t n, const int32_t* levels, long long* out,
+                        int num_sms, cudaStream_t st) {
   cudaMemsetAsync(out, 0, sizeof(long long) * 3, st);
-  k_level_stats<OffT><<<num_sms * 2, 256, 0, st>>>(off, n, levels, out);
+  k_level_stats<OffT><<<num_sms * 2, 256, 0, st>>>(off, new_id, n, levels, out);
 }
 
 #define INST(OffT)                                                                                          \
@@ -632,8 +644,10 @@ void launch_level_stats(const OffT* off, int64_t n, const int32_t* levels, long 
   template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
   template cudaError_t launch_batch_expand<OffT>(int, const BatchArgs<OffT>&, int, cudaStream_t);           \
   template int batch_expand_grid<OffT>(int, int);                                                           \
-  template void launch_batch_stats<OffT>(const OffT*, int64_t, const WaveSlots*, int, long long*, int, cudaStream_t); \
-  template void launch_level_stats<OffT>(const OffT*, int64_t, const int32_t*, long long*, int, cudaStream_t);
+  template void launch_batch_stats<OffT>(const OffT*, const int32_t*, int64_t, const WaveSlots*, int, long long*, int, \
+                                         cudaStream_t);                                                     \
+  template void launch_level_stats<OffT>(const OffT*, const int32_t*, int64_t, const int32_t*, long long*, int, \
+                                         cudaStream_t);
 INST(int32_t)
 INST(int64_t)
 #undef INST

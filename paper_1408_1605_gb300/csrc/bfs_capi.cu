@@ -137,6 +137,7 @@ ExpandArgs<OffT> make_args(const bfs_graph_s* G, uint32_t* bitmap) {
   a.cond = 0;
   a.use_cond = 0;
   a.probe_mode = G->probe_mode;
+  a.old_id = g.old_id;
   return a;
 }
 
@@ -253,6 +254,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.allow_bottom_up = G->bottom_up;
     pa.probe_mode = G->probe_mode;
     pa.spin_limit = G->wait_limit;
+    pa.old_id = G->g.old_id;
     int& pg = G->pgrid[G->bottom_up ? 1 : 0];
     if (!pg) pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
     if ((e = launch_persistent<OffT>(G->shape, pa, pg, st)) != cudaSuccess)
@@ -406,7 +408,8 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
   if (n_entries > 0 && !cols) return fail(BFS_ERR_INVALID_ARG, "cols is NULL");
   if (n_vertices < 1 || n_vertices > INT32_MAX) return fail(BFS_ERR_INVALID_ARG, "n_vertices outside [1, 2^31-1]");
   if (n_entries < 0) return fail(BFS_ERR_INVALID_ARG, "n_entries < 0");
-  const uint32_t known = BFS_HOST_PTRS | BFS_DEVICE_PTRS | BFS_OFFSETS_INT32 | BFS_OFFSETS_INT64 | BFS_VALIDATE;
+  const uint32_t known =
+      BFS_HOST_PTRS | BFS_DEVICE_PTRS | BFS_OFFSETS_INT32 | BFS_OFFSETS_INT64 | BFS_VALIDATE | BFS_RELABEL_DEGREE;
   if (flags & ~known) return fail(BFS_ERR_INVALID_ARG, "unknown flag bits");
   if ((flags & BFS_HOST_PTRS) && (flags & BFS_DEVICE_PTRS))
     return fail(BFS_ERR_INVALID_ARG, "BFS_HOST_PTRS and BFS_DEVICE_PTRS both set");
@@ -498,6 +501,18 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
     delete G;
     return cuda_fail(e, "graph upload");
   }
+  const char* rl = std::getenv("GBFS_RELABEL");  // overrides the flag (experiments)
+  const bool relabel = rl ? std::atoi(rl) != 0 : (flags & BFS_RELABEL_DEGREE) != 0;
+  if (relabel && (e = relabel_by_degree(g, st)) != cudaSuccess) {
+    cudaFree(g.off);
+    cudaFree(g.cols);
+    delete G;
+    return e == cudaErrorMemoryAllocation ? fail(BFS_ERR_OOM, "relabelling: device allocation")
+                                          : cuda_fail(e, "relabelling");
+  }
+  // Bitmap pre-check: relabelled graphs concentrate the probes on the hub words, which L1
+  // serves best; otherwise the L2-only load sees claims made during the level sooner.
+  G->probe_mode = g.new_id ? 0 : 1;
   const char* hl = std::getenv("GBFS_HOST_LOOP");
   G->host_loop = hl && std::atoi(hl) != 0;
   const char* lm = std::getenv("GBFS_LOOP");
@@ -533,6 +548,8 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t G) {
     free_single_ws(G->ws);
     cudaFree(G->g.off);
     cudaFree(G->g.cols);
+    cudaFree(G->g.new_id);
+    cudaFree(G->g.old_id);
   }
   delete G;
   return BFS_OK;
@@ -560,6 +577,14 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
       if (value < 0 || value > (1ll << 40)) return fail(BFS_ERR_INVALID_ARG, "wait limit outside [0, 2^40]");
       G->wait_limit = value;
       return BFS_OK;
+    case BFS_OPT_PROBE:
+      if (value < 0 || value > 1) return fail(BFS_ERR_INVALID_ARG, "probe mode outside [0, 1]");
+      if (G->probe_mode != (int)value) {
+        if (G->last_done) cudaEventSynchronize(G->last_done);
+        G->probe_mode = (int)value;
+        set_single_shape(G, G->shape);  // the captured level loop holds the old mode
+      }
+      return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");
 }
@@ -573,6 +598,8 @@ GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* val
     case BFS_OPT_ALPHA: *value = G->alpha; return BFS_OK;
     case BFS_OPT_BETA: *value = G->beta; return BFS_OK;
     case BFS_OPT_WAIT_LIMIT: *value = G->wait_limit; return BFS_OK;
+    case BFS_OPT_PROBE: *value = G->probe_mode; return BFS_OK;
+    case BFS_OPT_RELABELED: *value = G->g.new_id != nullptr; return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");
 }
@@ -629,6 +656,8 @@ GBFS_API bfs_status bfs_expand(bfs_graph_t G, const int32_t* frontier, int64_t n
   if (n_frontier > 0 && !frontier) return fail(BFS_ERR_INVALID_ARG, "frontier is NULL");
   if (!bitmap || !levels || !parents || !next || !next_count) return fail(BFS_ERR_INVALID_ARG, "NULL output");
   if (level < 1) return fail(BFS_ERR_INVALID_ARG, "level must be >= 1");
+  if (G->g.new_id)
+    return fail(BFS_ERR_INVALID_ARG, "bfs_expand works in the graph's own numbering: create it without BFS_RELABEL_DEGREE");
   std::lock_guard<std::mutex> lock(G->mu);
   cudaError_t e = cudaSetDevice(G->g.device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");

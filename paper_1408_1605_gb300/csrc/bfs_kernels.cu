@@ -35,24 +35,25 @@ namespace gbfs {
 // Frontier construction helpers
 
 template <typename OffT>
-__global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t root, int32_t* levels,
-                              int32_t* parents, uint32_t* bitmap, FrontierBuf<OffT> f0, int32_t* chunk0,
-                              Ctl* ctl, Packed pk) {
+__global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t root, const int32_t* new_id,
+                              int32_t* levels, int32_t* parents, uint32_t* bitmap, FrontierBuf<OffT> f0,
+                              int32_t* chunk0, Ctl* ctl, Packed pk) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = tid; i < n; i += stride) {
+  for (int64_t i = tid; i < n; i += stride) {  // outputs are indexed by caller ids
     const bool is_root = i == root;
     levels[i] = is_root ? 0 : -1;
     parents[i] = is_root ? root : -1;
   }
+  const int32_t rn = new_id ? new_id[root] : root;  // the root's internal id
   const int64_t nw = (n + 31) / 32;
-  for (int64_t w = tid; w < nw; w += stride) bitmap[w] = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
-  const OffT o0 = off[root], deg = off[root + 1] - o0;
+  for (int64_t w = tid; w < nw; w += stride) bitmap[w] = (w == (rn >> 5)) ? (1u << (rn & 31)) : 0u;
+  const OffT o0 = off[rn], deg = off[rn + 1] - o0;
   // chunk starts of the root's row, spread over the grid (a hub root spans many chunks)
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
   for (int64_t c = tid; c < nchunks; c += stride) chunk0[c] = 0;
   if (tid == 0) {
-    f0.v[0] = root;
+    f0.v[0] = rn;
     f0.cum[0] = 0;
     f0.base[0] = o0;
     ctl->counter[0] = pk.make(1, (long long)deg);
@@ -199,6 +200,7 @@ struct LevelIO {
   uint32_t* fbm_out;                // next frontier as a bitmap (nullptr: not kept)
   int L;                            // level assigned to claimed vertices
   int probe_mode;                   // bitmap pre-check: 0 default caching, 1 L2 only
+  const int32_t* old_id;            // internal -> caller id for the outputs (NULL: identity)
   int64_t nf;                       // current frontier size
   OffT r;                           // current frontier's degree sum
 };
@@ -285,7 +287,8 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
         const OffT c = io.in.cum[klo + i];
         s_rel[i] = (int32_t)max(c - e0, (OffT)0);
         s_base[i] = io.in.base[klo + i];
-        s_u[i] = io.in.v[klo + i];
+        const int32_t u = io.in.v[klo + i];
+        s_u[i] = io.old_id ? __ldg(io.old_id + u) : u;  // only ever written out as a parent
       }
       if (threadIdx.x == 0) s_rel[s] = 0x7fffffff;  // sentinel
       __syncthreads();
@@ -318,7 +321,8 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
             const OffT e = e0 + er;
             const int32_t kk = binsearch_maxle(io.in.cum, (int64_t)klo, (int64_t)kend + 1, e);
             col[j] = io.in.base[kk] + e;
-            uu[j] = io.in.v[kk];
+            const int32_t u = io.in.v[kk];
+            uu[j] = io.old_id ? __ldg(io.old_id + u) : u;
           }
         }
       }
@@ -344,22 +348,25 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
       if (claimed[j]) bits[j] = atomicOr(bitmap + (vv[j] >> 5), m);
     }
     OffT o0[E], o1[E];
+    int32_t ov[E];  // caller id of the claimed vertex
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const uint32_t m = 1u << (vv[j] & 31);
       claimed[j] = claimed[j] && !(bits[j] & m);
       o0[j] = 0;
       o1[j] = 0;
+      ov[j] = vv[j];
       if (claimed[j]) {
         o0[j] = off[vv[j]];
         o1[j] = off[vv[j] + 1];
+        if (io.old_id) ov[j] = __ldg(io.old_id + vv[j]);
       }
     }
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       if (claimed[j]) {
-        io.levels[vv[j]] = L;
-        io.parents[vv[j]] = uu[j];
+        io.levels[ov[j]] = L;
+        io.parents[ov[j]] = uu[j];
         if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
       }
     }
@@ -398,6 +405,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
   io.fbm_out = nullptr;
   io.L = L;
   io.probe_mode = a.probe_mode;
+  io.old_id = a.old_id;
   io.nf = a.pk.count(pc);
   io.r = (OffT)a.pk.edges(pc);
   td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, smem, sh, blockIdx.x,
@@ -541,8 +549,9 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
     const unsigned claimed = __ballot_sync(0xffffffffu, found);
     if (claimed) {
       if (found) {
-        io.levels[v] = L;
-        io.parents[v] = parent;
+        const int32_t ov = io.old_id ? __ldg(io.old_id + v) : v;
+        io.levels[ov] = L;
+        io.parents[ov] = io.old_id ? __ldg(io.old_id + parent) : parent;
         wbuf[nc + __popc(claimed & lanemask_lt())] = make_int2(v, deg);
       }
       if (lane == 0) {
@@ -619,6 +628,7 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_
     io.fbm_out = WITH_BU ? a.fbm[nxt3] : nullptr;
     io.L = it + 1;
     io.probe_mode = a.probe_mode;
+    io.old_id = a.old_id;
     io.nf = nf;
     io.r = (OffT)r;
     if (WITH_BU && bottom_up)
@@ -648,29 +658,30 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_
 }
 
 template <typename OffT>
-__global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t root, int32_t* levels,
-                               int32_t* parents, uint32_t* bitmap, uint32_t* fbm0, uint32_t* fbm1, uint32_t* fbm2,
-                               FrontierBuf<OffT> f0, int32_t* chunk0, PCtl* c, Packed pk) {
+__global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t root, const int32_t* new_id,
+                               int32_t* levels, int32_t* parents, uint32_t* bitmap, uint32_t* fbm0, uint32_t* fbm1,
+                               uint32_t* fbm2, FrontierBuf<OffT> f0, int32_t* chunk0, PCtl* c, Packed pk) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = tid; i < n; i += stride) {
+  for (int64_t i = tid; i < n; i += stride) {  // outputs are indexed by caller ids
     const bool is_root = i == root;
     levels[i] = is_root ? 0 : -1;
     parents[i] = is_root ? root : -1;
   }
+  const int32_t rn = new_id ? new_id[root] : root;  // the root's internal id
   const int64_t nw = (n + 31) / 32;
   for (int64_t w = tid; w < nw; w += stride) {
-    const uint32_t rb = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
+    const uint32_t rb = (w == (rn >> 5)) ? (1u << (rn & 31)) : 0u;
     bitmap[w] = rb;
     fbm0[w] = rb;
     fbm1[w] = 0u;
     fbm2[w] = 0u;
   }
-  const OffT o0 = off[root], deg = off[root + 1] - o0;
+  const OffT o0 = off[rn], deg = off[rn + 1] - o0;
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
   for (int64_t ch = tid; ch < nchunks; ch += stride) chunk0[ch] = 0;
   if (tid == 0) {
-    f0.v[0] = root;
+    f0.v[0] = rn;
     f0.cum[0] = 0;
     f0.base[0] = o0;
     c->counter[0] = pk.make(1, (long long)deg);
@@ -705,8 +716,8 @@ void launch_init_single(const GraphDev& g, int32_t root, int32_t* levels, int32_
                         cudaStream_t st) {
   const int block = 256;
   const int grid = g.num_sms * 8;
-  k_init_single<OffT><<<grid, block, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, levels, parents,
-                                               ws.bitmap, ws.fr<OffT>(0), ws.chunk[0], ws.ctl, g.pk);
+  k_init_single<OffT><<<grid, block, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, g.new_id, levels,
+                                               parents, ws.bitmap, ws.fr<OffT>(0), ws.chunk[0], ws.ctl, g.pk);
 }
 
 template <typename OffT>
@@ -818,8 +829,8 @@ int persistent_grid(int shape, int num_sms, bool with_bu) {
 template <typename OffT>
 void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
                          cudaStream_t st) {
-  k_init_persist<OffT><<<g.num_sms * 8, 256, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, levels,
-                                                      parents, ws.bitmap, ws.fbm[0], ws.fbm[1], ws.fbm[2],
+  k_init_persist<OffT><<<g.num_sms * 8, 256, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, g.new_id,
+                                                      levels, parents, ws.bitmap, ws.fbm[0], ws.fbm[1], ws.fbm[2],
                                                       ws.fr<OffT>(0), ws.chunk[0], ws.pctl, g.pk);
 }
 

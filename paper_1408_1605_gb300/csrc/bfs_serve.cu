@@ -333,10 +333,10 @@ static void wave_round(bfs_server_s* S, Wave* w) {
     for (int b : retire) {
       ServeReq* r = w->slot_req[b];
       if (w->g.off64)
-        launch_level_stats<int64_t>(reinterpret_cast<const int64_t*>(w->g.off), w->g.n, r->dev_lvl,
+        launch_level_stats<int64_t>(reinterpret_cast<const int64_t*>(w->g.off), w->g.new_id, w->g.n, r->dev_lvl,
                                     w->stats_dev + 3 * b, w->g.num_sms, w->stream);
       else
-        launch_level_stats<int32_t>(reinterpret_cast<const int32_t*>(w->g.off), w->g.n, r->dev_lvl,
+        launch_level_stats<int32_t>(reinterpret_cast<const int32_t*>(w->g.off), w->g.new_id, w->g.n, r->dev_lvl,
                                     w->stats_dev + 3 * b, w->g.num_sms, w->stream);
       cudaMemcpyAsync(w->stats_host + 3 * b, w->stats_dev + 3 * b, sizeof(long long) * 3, cudaMemcpyDeviceToHost,
                       w->stream);

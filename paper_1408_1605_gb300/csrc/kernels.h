@@ -22,7 +22,15 @@ struct GraphDev {
   void* off = nullptr;      // OffT[n + 1]
   int32_t* cols = nullptr;  // int32[nnz]
   Packed pk{};
+  // Degree relabelling (BFS_RELABEL_DEGREE): off / cols hold the renumbered graph, new_id
+  // maps a caller id to the internal one and old_id back. Both NULL when not relabelled.
+  int32_t* new_id = nullptr;
+  int32_t* old_id = nullptr;
 };
+
+// Renumbers g by non-increasing degree on the device (replaces off / cols, sets new_id /
+// old_id). Synchronous on st.
+cudaError_t relabel_by_degree(GraphDev& g, cudaStream_t st);
 
 // Work buffers of single-source searches on one graph (reused across calls).
 struct SingleWs {
@@ -63,6 +71,7 @@ struct ExpandArgs {
   cudaGraphConditionalHandle cond;
   int use_cond;
   int probe_mode;   // bitmap pre-check: 0 default caching, 1 L2 only
+  const int32_t* old_id;  // internal -> caller vertex id (NULL: identity)
 };
 
 template <typename OffT>
@@ -84,6 +93,7 @@ struct PersistArgs {
   int allow_bottom_up;
   int probe_mode;
   long long spin_limit;  // polls of a grid-barrier wait before it gives up (kErrTimeout)
+  const int32_t* old_id;  // internal -> caller vertex id (NULL: identity)
 };
 
 struct ExpandShape {
