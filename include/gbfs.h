@@ -308,8 +308,12 @@ GBFS_API bfs_status bfs_serve_destroy(bfs_server_t srv);
 /* Number of compiled shapes of a kernel kind (0 for an unknown kind). */
 GBFS_API int bfs_shape_count(int kind);
 
-/* Shape parameters: CTA size, edges per thread, claim-buffer entries per CTA. */
-GBFS_API bfs_status bfs_shape_info(int kind, int shape, int *block, int *edges_per_thread, int *claim_buffer);
+/* Shape parameters: CTA size, edges per thread, claim-buffer entries, and the tiling:
+ * *warp_tiles = 0 when a CTA expands tiles of block x edges_per_thread edges (claim buffer
+ * per CTA), 1 when every warp expands its own tiles of 32 x edges_per_thread edges (claim
+ * buffer per warp; no CTA-wide barrier inside a level). Any output pointer may be NULL. */
+GBFS_API bfs_status bfs_shape_info(int kind, int shape, int *block, int *edges_per_thread, int *claim_buffer,
+                                   int *warp_tiles);
 
 /* Selects the shape a graph's later searches use (waits for the graph's pending work). A
  * server takes a graph's batch shape when the graph is added. */

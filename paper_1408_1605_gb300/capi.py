@@ -112,7 +112,7 @@ def lib():
             "bfs_serve_stats": [_P, ctypes.POINTER(bfs_serve_report)],
             "bfs_serve_destroy": [_P],
             "bfs_shape_info": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                               ctypes.POINTER(ctypes.c_int)],
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
             "bfs_graph_set_shape": [_P, ctypes.c_int, ctypes.c_int],
             "bfs_graph_set_option": [_P, ctypes.c_int, i64],
             "bfs_level_profile": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -294,9 +294,10 @@ def bfs_shape_count(kind: int) -> int:
 
 
 def bfs_shape_info(kind: int, shape: int) -> dict:
-    b, e, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    check(lib().bfs_shape_info(int(kind), int(shape), ctypes.byref(b), ctypes.byref(e), ctypes.byref(c)))
-    return {"block": b.value, "edges_per_thread": e.value, "claim_buffer": c.value}
+    b, e, c, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().bfs_shape_info(int(kind), int(shape), ctypes.byref(b), ctypes.byref(e), ctypes.byref(c),
+                               ctypes.byref(w)))
+    return {"block": b.value, "edges_per_thread": e.value, "claim_buffer": c.value, "warp_tiles": w.value}
 
 
 def bfs_graph_set_shape(graph: int, kind: int, shape: int) -> None:

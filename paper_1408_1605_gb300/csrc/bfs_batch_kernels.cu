@@ -513,7 +513,7 @@ static int batch_grid_t(int num_sms) {
   X(3, 512, 2, 2048)
 
 const ExpandShape kBatchShapes[] = {
-#define X(id, b, e, c) {id, b, e, c},
+#define X(id, b, e, c) {id, b, e, c, 0},
     GBFS_BATCH_SHAPES(X)
 #undef X
 };

@@ -234,6 +234,36 @@ __device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const L
   }
 }
 
+// Appends a warp's buffered claims (buf[0..nc), nc <= 32 * P) to the next frontier with
+// one 64-bit atomic for the warp: lane i owns items [i P, i P + P); a warp scan of the
+// degrees gives each item its place in the next level's edge space.
+template <typename OffT, int P>
+__device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const LevelIO<OffT>& io, const int2* buf,
+                                           int nc) {
+  const int lane = threadIdx.x & 31;
+  const int lo = min(nc, lane * P), hi = min(nc, lo + P);
+  OffT mine = 0;
+  for (int i = lo; i < hi; ++i) mine += (OffT)buf[i].y;
+  const OffT inc = warp_inclusive_scan(mine);
+  const OffT total = __shfl_sync(0xffffffffu, inc, 31);
+  unsigned long long resv = 0;
+  if (lane == 0) resv = atomicAdd(io.counter_out, pk.make(nc, (long long)total));
+  resv = __shfl_sync(0xffffffffu, resv, 0);
+  const long long slot0 = pk.count(resv);
+  OffT run = (OffT)pk.edges(resv) + inc - mine;
+  for (int i = lo; i < hi; ++i) {
+    const int32_t v = buf[i].x;
+    const OffT d = (OffT)buf[i].y;
+    const int32_t slot = (int32_t)(slot0 + i);
+    io.out.v[slot] = v;
+    io.out.cum[slot] = run;
+    io.out.base[slot] = off[v] - run;
+    write_chunks(io.chunk_out, run, d, slot);
+    run += d;
+  }
+  __syncwarp();
+}
+
 // Warp-aggregated push of this thread's claim (if any) into the CTA buffer.
 __device__ __forceinline__ void push_claim(bool claimed, int32_t v, int32_t deg, int2* s_claim, int* nclaim) {
   const unsigned ball = __ballot_sync(0xffffffffu, claimed);
@@ -386,8 +416,172 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
   __syncthreads();
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
-__global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
+// Shared state of one warp in the warp-tile variant of the top-down step.
+template <typename OffT, int E, int WCAP>
+struct WarpTileSmem {
+  static constexpr int TW = 32 * E;  // edges per warp tile
+  int2 claim[WCAP];                  // claimed (vertex, degree), flushed by the warp alone
+  OffT base[TW + 1];                 // staged frontier entries of the tile
+  int32_t u[TW + 1];                 // their caller ids (parents to write)
+  int32_t kmap[TW];                  // tile edge -> staged entry that starts there (or -1)
+};
+
+// The top-down step with warp-sized tiles: warp w expands tiles w, w + W, ... of 32 E
+// edges on its own, so no CTA-wide barrier is needed inside a level. The mapping of edge e
+// to the frontier entry k = max{k : cum[k] <= e} (Algorithm 3 line 2) is built per tile
+// without searching: every staged entry marks the tile edge where its row starts, and an
+// inclusive max-scan over the tile's edges (lane l holds edges l, l + 32, ...) gives each
+// edge the last entry that started at or before it. The rest (column reads, pre-check,
+// atomicOr claim, level / parent writes, fused append and degree scan) is the CTA-tile
+// step's, with the claims appended through the warp's own buffer.
+template <typename OffT, int E, int WCAP>
+__device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
+                              int64_t n, Packed pk, unsigned* err, const LevelIO<OffT>& io,
+                              WarpTileSmem<OffT, E, WCAP>& sm, int64_t tile0, int64_t tstride) {
+  constexpr int TW = WarpTileSmem<OffT, E, WCAP>::TW;
+  static_assert(TW % kChunk == 0, "warp tiles must start on chunk-index boundaries");
+  static_assert(WCAP >= TW && WCAP % 32 == 0, "claim buffer must hold one full tile");
+  constexpr int P = WCAP / 32;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const OffT r = io.r;
+  const int64_t nf = io.nf;
+  const int64_t ntiles = ((int64_t)r + TW - 1) / TW;
+  const int L = io.L;
+  const int probe_mode = io.probe_mode;
+  int nc = 0;  // claims buffered (warp-uniform)
+  for (int64_t tile = tile0; tile < ntiles; tile += tstride) {
+    const OffT e0 = (OffT)(tile * TW);
+    const int cnt = (int)min((OffT)TW, r - e0);
+    const int32_t klo = io.chunk_in[e0 / kChunk];
+    const int32_t kend = (e0 + cnt < r) ? io.chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+    const int s = kend - klo + 1;
+    const bool fast = s <= TW + 1;
+    int kk[E];
+    __syncwarp();  // the previous tile's shared-memory reads are done
+    if (fast) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) sm.kmap[lane + 32 * j] = -1;
+      __syncwarp();
+      for (int i = lane; i < s; i += 32) {
+        const OffT c = io.in.cum[klo + i];
+        const int32_t u = io.in.v[klo + i];
+        sm.base[i] = io.in.base[klo + i];
+        sm.u[i] = io.old_id ? __ldg(io.old_id + u) : u;
+        const OffT rel = c - e0;  // entry klo starts at or before the tile: rel <= 0
+        if (rel < (OffT)TW) atomicMax(&sm.kmap[rel > 0 ? (int)rel : 0], i);
+      }
+      __syncwarp();
+      int carry = -1;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        int x = sm.kmap[lane + 32 * j];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(full, x, d);
+          if (lane >= d) x = max(x, y);
+        }
+        x = max(x, carry);
+        kk[j] = x;
+        carry = __shfl_sync(full, x, 31);
+      }
+    }
+    int32_t vv[E], uu[E];
+    OffT col[E];
+    bool ok[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int er = lane + 32 * j;
+      ok[j] = er < cnt;
+      uu[j] = 0;
+      col[j] = 0;
+      if (ok[j]) {
+        if (fast) {
+          col[j] = sm.base[kk[j]] + e0 + er;
+          uu[j] = sm.u[kk[j]];
+        } else {
+          // many zero-degree frontier entries: search the global scan directly
+          const OffT e = e0 + er;
+          const int32_t k = binsearch_maxle(io.in.cum, (int64_t)klo, (int64_t)kend + 1, e);
+          col[j] = io.in.base[k] + e;
+          const int32_t u = io.in.v[k];
+          uu[j] = io.old_id ? __ldg(io.old_id + u) : u;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) vv[j] = ok[j] ? ld_nc(cols + col[j]) : 0;
+    uint32_t bits[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (ok[j] && (uint32_t)vv[j] >= (uint64_t)n) {
+        atomicOr(err, kErrColumnRange);
+        ok[j] = false;
+      }
+      bits[j] = ok[j] ? probe_load(bitmap + (vv[j] >> 5), probe_mode) : 0xffffffffu;
+    }
+    bool claimed[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const uint32_t m = 1u << (vv[j] & 31);
+      claimed[j] = !(bits[j] & m);
+      if (claimed[j]) bits[j] = atomicOr(bitmap + (vv[j] >> 5), m);
+    }
+    OffT o0[E], o1[E];
+    int32_t ov[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const uint32_t m = 1u << (vv[j] & 31);
+      claimed[j] = claimed[j] && !(bits[j] & m);
+      o0[j] = 0;
+      o1[j] = 0;
+      ov[j] = vv[j];
+      if (claimed[j]) {
+        o0[j] = off[vv[j]];
+        o1[j] = off[vv[j] + 1];
+        if (io.old_id) ov[j] = __ldg(io.old_id + vv[j]);
+      }
+    }
+    unsigned ball[E];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (claimed[j]) {
+        io.levels[ov[j]] = L;
+        io.parents[ov[j]] = uu[j];
+        if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
+      }
+      ball[j] = __ballot_sync(full, claimed[j]);
+      tot += __popc(ball[j]);
+    }
+    if (tot) {
+      if (nc + tot > WCAP) {
+        __syncwarp();
+        warp_flush<OffT, P>(off, pk, io, sm.claim, nc);
+        nc = 0;
+      }
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        if (claimed[j]) sm.claim[nc + __popc(ball[j] & lanemask_lt())] = make_int2(vv[j], (int32_t)(o1[j] - o0[j]));
+        nc += __popc(ball[j]);
+      }
+    }
+  }
+  __syncwarp();
+  if (nc > 0) warp_flush<OffT, P>(off, pk, io, sm.claim, nc);
+}
+
+// Dynamic shared memory of an expansion shape: CTA tiles (staging + CTA claim buffer) or
+// warp tiles (one WarpTileSmem per warp, CLAIM = claim entries per warp).
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+struct ShapeSmem {
+  static constexpr size_t bytes =
+      WT ? (BLOCK / 32) * sizeof(WarpTileSmem<OffT, E, CLAIM>) : ExpandSmem<OffT, BLOCK, E, CLAIM>::bytes;
+};
+
+// Registers are held to what 48 (E <= 4) or 32 resident warps per SM allow.
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+__global__ void __launch_bounds__(BLOCK, (E <= 4 ? 1536 : 1024) / BLOCK) k_expand(ExpandArgs<OffT> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ExpandShared<OffT> sh;
   Ctl* ctl = a.ctl;
@@ -408,8 +602,16 @@ __global__ void __launch_bounds__(BLOCK) k_expand(ExpandArgs<OffT> a) {
   io.old_id = a.old_id;
   io.nf = a.pk.count(pc);
   io.r = (OffT)a.pk.edges(pc);
-  td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, smem, sh, blockIdx.x,
-                                  gridDim.x);
+  if constexpr (WT) {
+    auto* wsm = reinterpret_cast<WarpTileSmem<OffT, E, CLAIM>*>(smem) + (threadIdx.x >> 5);
+    td_level_warp<OffT, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, *wsm,
+                                  (int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5),
+                                  (int64_t)gridDim.x * (BLOCK / 32));
+    __syncthreads();
+  } else {
+    td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, smem, sh, blockIdx.x,
+                                    gridDim.x);
+  }
 
   // Level epilogue by the last CTA to finish: close the level and prepare the next.
   if (threadIdx.x == 0) {
@@ -466,36 +668,6 @@ __device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks, long lon
   __syncthreads();
 }
 
-// Appends a warp's buffered claims (buf[0..nc), nc <= 32 * P) to the next frontier with
-// one 64-bit atomic for the warp: lane i owns items [i P, i P + P); a warp scan of the
-// degrees gives each item its place in the next level's edge space.
-template <typename OffT, int P>
-__device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const LevelIO<OffT>& io, const int2* buf,
-                                           int nc) {
-  const int lane = threadIdx.x & 31;
-  const int lo = min(nc, lane * P), hi = min(nc, lo + P);
-  OffT mine = 0;
-  for (int i = lo; i < hi; ++i) mine += (OffT)buf[i].y;
-  const OffT inc = warp_inclusive_scan(mine);
-  const OffT total = __shfl_sync(0xffffffffu, inc, 31);
-  unsigned long long resv = 0;
-  if (lane == 0) resv = atomicAdd(io.counter_out, pk.make(nc, (long long)total));
-  resv = __shfl_sync(0xffffffffu, resv, 0);
-  const long long slot0 = pk.count(resv);
-  OffT run = (OffT)pk.edges(resv) + inc - mine;
-  for (int i = lo; i < hi; ++i) {
-    const int32_t v = buf[i].x;
-    const OffT d = (OffT)buf[i].y;
-    const int32_t slot = (int32_t)(slot0 + i);
-    io.out.v[slot] = v;
-    io.out.cum[slot] = run;
-    io.out.base[slot] = off[v] - run;
-    write_chunks(io.chunk_out, run, d, slot);
-    run += d;
-  }
-  __syncwarp();
-}
-
 // One bottom-up level (Beamer et al.'s step, the paper's related work, Sec. 6): every
 // unvisited vertex scans its row for a neighbour in the current frontier (a bitmap) and
 // stops at the first. Warp w takes visited word w (32 vertices), so no atomics are needed
@@ -503,16 +675,13 @@ __device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const Lev
 // through its own slice of the claim buffer with a warp-level flush: warps never wait for
 // one another inside the level. Claimed vertices enter the next frontier queue exactly as
 // in the top-down step.
-template <typename OffT, int BLOCK, int CLAIM>
+template <typename OffT, int WCAP>
 __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
                          const uint32_t* __restrict__ fbm_in, int64_t n, Packed pk, const LevelIO<OffT>& io,
-                         int2* s_claim, int64_t warp0, int64_t wstride) {
-  constexpr int WARPS = BLOCK / 32;
-  constexpr int WCAP = CLAIM / WARPS;  // claim entries per warp
+                         int2* wbuf, int64_t warp0, int64_t wstride) {
   static_assert(WCAP >= 64, "per-warp claim buffer too small");
   constexpr int P = (WCAP + 31) / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int2* wbuf = s_claim + warp * WCAP;
+  const int lane = threadIdx.x & 31;
   const int64_t nwords = (n + 31) / 32;
   const int L = io.L;
   int nc = 0;  // warp-uniform
@@ -571,13 +740,18 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
 }
 
 // WITH_BU = false compiles the top-down-only variant (fewer registers, more resident CTAs).
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WITH_BU>
-__global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_persistent(PersistArgs<OffT> a) {
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WITH_BU, bool WT>
+__global__ void __launch_bounds__(BLOCK, (WITH_BU || E > 4 ? 1024 : 1536) / BLOCK) k_bfs_persistent(PersistArgs<OffT> a) {
   using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
+  using W = WarpTileSmem<OffT, E, CLAIM>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ExpandShared<OffT> sh;
   PCtl* c = a.ctl;
-  int2* s_claim = reinterpret_cast<int2*>(smem + S::off_claim);
+  const int warp = threadIdx.x >> 5;
+  W* wsm = reinterpret_cast<W*>(smem) + warp;
+  // bottom-up claim buffer of this warp: its warp-tile buffer, or its slice of the CTA's
+  constexpr int BU_WCAP = WT ? CLAIM : CLAIM / (BLOCK / 32);
+  int2* bu_buf = WT ? wsm->claim : reinterpret_cast<int2*>(smem + S::off_claim) + warp * BU_WCAP;
   const int64_t nwords = (a.n + 31) / 32;
   const int64_t gtid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * BLOCK;
@@ -632,9 +806,11 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU ? 1024 : 1536) / BLOCK) k_bfs_
     io.nf = nf;
     io.r = (OffT)r;
     if (WITH_BU && bottom_up)
-      bu_level<OffT, BLOCK, CLAIM>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, s_claim,
-                                   (int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5),
-                                   (int64_t)gridDim.x * (BLOCK / 32));
+      bu_level<OffT, BU_WCAP>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, bu_buf,
+                              (int64_t)blockIdx.x * (BLOCK / 32) + warp, (int64_t)gridDim.x * (BLOCK / 32));
+    else if constexpr (WT)
+      td_level_warp<OffT, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &c->error, io, *wsm,
+                                    (int64_t)blockIdx.x * (BLOCK / 32) + warp, (int64_t)gridDim.x * (BLOCK / 32));
     else
       td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &c->error, io, smem, sh, blockIdx.x,
                                       gridDim.x);
@@ -734,81 +910,87 @@ void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, i
   k_scan_final<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.fr<OffT>(cur), ws.chunk[cur], ws.ctl);
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 static cudaError_t launch_expand_t(const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
-  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = k_expand<OffT, BLOCK, E, CLAIM>;
+  constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
+  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT>;
   static bool attr_set = false;  // per template instance; set once per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  kern<<<grid, BLOCK, S::bytes, st>>>(a);
+  kern<<<grid, BLOCK, bytes, st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 static int occupancy_t(int num_sms) {
-  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = k_expand<OffT, BLOCK, E, CLAIM>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
+  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
   return std::max(1, per_sm) * num_sms;
 }
 
-// Table of compiled shapes (BLOCK, E, CLAIM); the autotuner chooses among them.
+// Table of compiled shapes (BLOCK, E, CLAIM, tiles): tiles 0 = one tile of BLOCK x E edges
+// per CTA (CLAIM = CTA claim buffer), 1 = one tile of 32 x E edges per warp (CLAIM = claim
+// buffer per warp). The autotuner chooses among them.
 #define GBFS_EXPAND_SHAPES(X) \
-  X(0, 256, 4, 2048)          \
-  X(1, 256, 8, 4096)          \
-  X(2, 512, 4, 4096)          \
-  X(3, 128, 8, 2048)          \
-  X(4, 256, 2, 2048)          \
-  X(5, 256, 4, 1536)          \
-  X(6, 256, 2, 1024)          \
-  X(7, 128, 4, 1024)
+  X(0, 256, 4, 2048, 0)       \
+  X(1, 256, 8, 4096, 0)       \
+  X(2, 512, 4, 4096, 0)       \
+  X(3, 128, 8, 2048, 0)       \
+  X(4, 256, 2, 2048, 0)       \
+  X(5, 256, 4, 1536, 0)       \
+  X(6, 256, 2, 1024, 0)       \
+  X(7, 128, 4, 1024, 0)       \
+  X(8, 128, 4, 128, 1)        \
+  X(9, 256, 4, 256, 1)        \
+  X(10, 128, 8, 256, 1)       \
+  X(11, 256, 8, 256, 1)
 
 const ExpandShape kExpandShapes[] = {
-#define X(id, b, e, c) {id, b, e, c},
+#define X(id, b, e, c, w) {id, b, e, c, w},
     GBFS_EXPAND_SHAPES(X)
 #undef X
 };
 const int kNumExpandShapes = sizeof(kExpandShapes) / sizeof(kExpandShapes[0]);
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
-  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = a.allow_bottom_up ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true>
-                                : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false>;
+  constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
+  auto kern = a.allow_bottom_up ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT>
+                                : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT>;
   static bool attr_set[2] = {false, false};
   if (!attr_set[a.allow_bottom_up ? 1 : 0]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     attr_set[a.allow_bottom_up ? 1 : 0] = true;
   }
   PersistArgs<OffT> copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(BLOCK), params, S::bytes,
-                                     st);
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(BLOCK), params, bytes, st);
 }
 
 // All CTAs of a cooperative launch must be resident at once: occupancy x SMs.
-template <typename OffT, int BLOCK, int E, int CLAIM>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 static int persistent_grid_t(int num_sms, bool with_bu) {
-  using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = with_bu ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true> : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
+  auto kern = with_bu ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT>
+                      : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
   return std::max(1, per_sm) * num_sms;
 }
 
 template <typename OffT>
 cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
-#define X(id, b, e, c) \
-  case id: return launch_persistent_t<OffT, b, e, c>(a, grid, st);
+#define X(id, b, e, c, w) \
+  case id: return launch_persistent_t<OffT, b, e, c, w != 0>(a, grid, st);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -818,8 +1000,8 @@ cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, c
 template <typename OffT>
 int persistent_grid(int shape, int num_sms, bool with_bu) {
   switch (shape) {
-#define X(id, b, e, c) \
-  case id: return persistent_grid_t<OffT, b, e, c>(num_sms, with_bu);
+#define X(id, b, e, c, w) \
+  case id: return persistent_grid_t<OffT, b, e, c, w != 0>(num_sms, with_bu);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -837,8 +1019,8 @@ void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32
 template <typename OffT>
 cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
-#define X(id, b, e, c) \
-  case id: return launch_expand_t<OffT, b, e, c>(a, grid, st);
+#define X(id, b, e, c, w) \
+  case id: return launch_expand_t<OffT, b, e, c, w != 0>(a, grid, st);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -848,8 +1030,8 @@ cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaSt
 template <typename OffT>
 int expand_grid(int shape, int num_sms) {
   switch (shape) {
-#define X(id, b, e, c) \
-  case id: return occupancy_t<OffT, b, e, c>(num_sms);
+#define X(id, b, e, c, w) \
+  case id: return occupancy_t<OffT, b, e, c, w != 0>(num_sms);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }

@@ -21,13 +21,15 @@ GBFS_API int bfs_shape_count(int kind) {
   return kind == BFS_KERNEL_SINGLE ? kNumExpandShapes : kind == BFS_KERNEL_BATCH ? kNumBatchShapes : 0;
 }
 
-GBFS_API bfs_status bfs_shape_info(int kind, int shape, int* block, int* edges_per_thread, int* claim_buffer) {
+GBFS_API bfs_status bfs_shape_info(int kind, int shape, int* block, int* edges_per_thread, int* claim_buffer,
+                                   int* warp_tiles) {
   clear_last_error();
   const ExpandShape* t = kind == BFS_KERNEL_SINGLE ? kExpandShapes : kind == BFS_KERNEL_BATCH ? kBatchShapes : nullptr;
   if (!t || shape < 0 || shape >= bfs_shape_count(kind)) return fail(BFS_ERR_INVALID_ARG, "unknown kernel kind or shape");
   if (block) *block = t[shape].block;
   if (edges_per_thread) *edges_per_thread = t[shape].e;
   if (claim_buffer) *claim_buffer = t[shape].claim;
+  if (warp_tiles) *warp_tiles = t[shape].warp_tiles;
   return BFS_OK;
 }
 

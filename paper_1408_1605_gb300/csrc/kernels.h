@@ -10,7 +10,7 @@ namespace gbfs {
 
 // Granularity of the precomputed per-tile binary-search answers (chunk index). Every
 // expansion tile size is a multiple of it.
-constexpr int kChunk = 256;
+constexpr int kChunk = 128;
 
 // Device copy of a graph: offsets are int32 when the entry count allows, else int64.
 struct GraphDev {
@@ -98,6 +98,7 @@ struct PersistArgs {
 
 struct ExpandShape {
   int id, block, e, claim;
+  int warp_tiles;  // 1: each warp expands its own tiles of 32 x e edges (claim = per warp)
 };
 extern const ExpandShape kExpandShapes[];
 extern const int kNumExpandShapes;

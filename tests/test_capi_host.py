@@ -108,7 +108,9 @@ def test_shape_tables(capi):
         for s in range(n):
             info = capi.bfs_shape_info(kind, s)
             assert info["block"] % 32 == 0 and info["edges_per_thread"] >= 1
-            assert info["claim_buffer"] >= info["block"] * info["edges_per_thread"]
+            tile = (32 if info["warp_tiles"] else info["block"]) * info["edges_per_thread"]
+            assert info["claim_buffer"] >= tile and tile % 128 == 0
+            assert info["warp_tiles"] in (0, 1) and (kind == capi.BFS_KERNEL_SINGLE or not info["warp_tiles"])
     assert capi.bfs_shape_count(7) == 0
     with pytest.raises(capi.BfsError):
         capi.bfs_shape_info(0, 99)
