@@ -53,7 +53,7 @@ __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t r
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
   for (int64_t c = tid; c < nchunks; c += stride) chunk0[c] = 0;
   if (tid == 0) {
-    f0.v[0] = rn;
+    f0.v[0] = root;  // the queue holds caller ids
     f0.cum[0] = 0;
     f0.base[0] = o0;
     ctl->counter[0] = pk.make(1, (long long)deg);
@@ -226,7 +226,7 @@ __device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const L
     const int32_t v = s_claim[i].x;
     const OffT d = (OffT)s_claim[i].y;
     const int32_t slot = (int32_t)(slot0 + i);
-    io.out.v[slot] = v;
+    io.out.v[slot] = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
     io.out.cum[slot] = run;
     io.out.base[slot] = off[v] - run;
     write_chunks(io.chunk_out, run, d, slot);
@@ -255,7 +255,7 @@ __device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const Lev
     const int32_t v = buf[i].x;
     const OffT d = (OffT)buf[i].y;
     const int32_t slot = (int32_t)(slot0 + i);
-    io.out.v[slot] = v;
+    io.out.v[slot] = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
     io.out.cum[slot] = run;
     io.out.base[slot] = off[v] - run;
     write_chunks(io.chunk_out, run, d, slot);
@@ -317,8 +317,7 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
         const OffT c = io.in.cum[klo + i];
         s_rel[i] = (int32_t)max(c - e0, (OffT)0);
         s_base[i] = io.in.base[klo + i];
-        const int32_t u = io.in.v[klo + i];
-        s_u[i] = io.old_id ? __ldg(io.old_id + u) : u;  // only ever written out as a parent
+        s_u[i] = io.in.v[klo + i];
       }
       if (threadIdx.x == 0) s_rel[s] = 0x7fffffff;  // sentinel
       __syncthreads();
@@ -351,8 +350,7 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
             const OffT e = e0 + er;
             const int32_t kk = binsearch_maxle(io.in.cum, (int64_t)klo, (int64_t)kend + 1, e);
             col[j] = io.in.base[kk] + e;
-            const int32_t u = io.in.v[kk];
-            uu[j] = io.old_id ? __ldg(io.old_id + u) : u;
+            uu[j] = io.in.v[kk];
           }
         }
       }
@@ -450,6 +448,8 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
   const int L = io.L;
   const int probe_mode = io.probe_mode;
   int nc = 0;  // claims buffered (warp-uniform)
+  // (Loading the next tile's entry range and staged entries one tile ahead was measured:
+  // no faster, and slower once it made the kernel spill.)
   for (int64_t tile = tile0; tile < ntiles; tile += tstride) {
     const OffT e0 = (OffT)(tile * TW);
     const int cnt = (int)min((OffT)TW, r - e0);
@@ -465,9 +465,8 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       __syncwarp();
       for (int i = lane; i < s; i += 32) {
         const OffT c = io.in.cum[klo + i];
-        const int32_t u = io.in.v[klo + i];
         sm.base[i] = io.in.base[klo + i];
-        sm.u[i] = io.old_id ? __ldg(io.old_id + u) : u;
+        sm.u[i] = io.in.v[klo + i];
         const OffT rel = c - e0;  // entry klo starts at or before the tile: rel <= 0
         if (rel < (OffT)TW) atomicMax(&sm.kmap[rel > 0 ? (int)rel : 0], i);
       }
@@ -504,8 +503,7 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
           const OffT e = e0 + er;
           const int32_t k = binsearch_maxle(io.in.cum, (int64_t)klo, (int64_t)kend + 1, e);
           col[j] = io.in.base[k] + e;
-          const int32_t u = io.in.v[k];
-          uu[j] = io.old_id ? __ldg(io.old_id + u) : u;
+          uu[j] = io.in.v[k];
         }
       }
     }
@@ -579,9 +577,9 @@ struct ShapeSmem {
       WT ? (BLOCK / 32) * sizeof(WarpTileSmem<OffT, E, CLAIM>) : ExpandSmem<OffT, BLOCK, E, CLAIM>::bytes;
 };
 
-// Registers are held to what 48 (E <= 4) or 32 resident warps per SM allow.
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
-__global__ void __launch_bounds__(BLOCK, (E <= 4 ? 1536 : 1024) / BLOCK) k_expand(ExpandArgs<OffT> a) {
+// TPS: resident threads per SM the registers are sized for (the launch bound).
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
+__global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand(ExpandArgs<OffT> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ExpandShared<OffT> sh;
   Ctl* ctl = a.ctl;
@@ -740,8 +738,9 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
 }
 
 // WITH_BU = false compiles the top-down-only variant (fewer registers, more resident CTAs).
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WITH_BU, bool WT>
-__global__ void __launch_bounds__(BLOCK, (WITH_BU || E > 4 ? 1024 : 1536) / BLOCK) k_bfs_persistent(PersistArgs<OffT> a) {
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WITH_BU, bool WT, int TPS>
+__global__ void __launch_bounds__(BLOCK, (WITH_BU && TPS > 1024 ? 1024 : TPS) / BLOCK)
+    k_bfs_persistent(PersistArgs<OffT> a) {
   using S = ExpandSmem<OffT, BLOCK, E, CLAIM>;
   using W = WarpTileSmem<OffT, E, CLAIM>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -857,7 +856,7 @@ __global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t 
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
   for (int64_t ch = tid; ch < nchunks; ch += stride) chunk0[ch] = 0;
   if (tid == 0) {
-    f0.v[0] = rn;
+    f0.v[0] = root;  // the queue holds caller ids
     f0.cum[0] = 0;
     f0.base[0] = o0;
     c->counter[0] = pk.make(1, (long long)deg);
@@ -910,10 +909,10 @@ void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, i
   k_scan_final<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.fr<OffT>(cur), ws.chunk[cur], ws.ctl);
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static cudaError_t launch_expand_t(const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
-  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT>;
+  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT, TPS>;
   static bool attr_set = false;  // per template instance; set once per process
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -924,45 +923,43 @@ static cudaError_t launch_expand_t(const ExpandArgs<OffT>& a, int grid, cudaStre
   return cudaGetLastError();
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static int occupancy_t(int num_sms) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
-  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT>;
+  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT, TPS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
   return std::max(1, per_sm) * num_sms;
 }
 
-// Table of compiled shapes (BLOCK, E, CLAIM, tiles): tiles 0 = one tile of BLOCK x E edges
-// per CTA (CLAIM = CTA claim buffer), 1 = one tile of 32 x E edges per warp (CLAIM = claim
-// buffer per warp). The autotuner chooses among them.
-#define GBFS_EXPAND_SHAPES(X) \
-  X(0, 256, 4, 2048, 0)       \
-  X(1, 256, 8, 4096, 0)       \
-  X(2, 512, 4, 4096, 0)       \
-  X(3, 128, 8, 2048, 0)       \
-  X(4, 256, 2, 2048, 0)       \
-  X(5, 256, 4, 1536, 0)       \
-  X(6, 256, 2, 1024, 0)       \
-  X(7, 128, 4, 1024, 0)       \
-  X(8, 128, 4, 128, 1)        \
-  X(9, 256, 4, 256, 1)        \
-  X(10, 128, 8, 256, 1)       \
-  X(11, 256, 8, 256, 1)
+// Table of compiled shapes (BLOCK, E, CLAIM, tiles, TPS): tiles 0 = one tile of BLOCK x E
+// edges per CTA (CLAIM = CTA claim buffer), 1 = one tile of 32 x E edges per warp (CLAIM =
+// claim buffer per warp); TPS = resident threads per SM the registers are sized for. The
+// autotuner chooses among them.
+#define GBFS_EXPAND_SHAPES(X)  \
+  X(0, 256, 4, 2048, 0, 1536)  \
+  X(1, 256, 4, 1536, 0, 1536)  \
+  X(2, 256, 2, 1024, 0, 1536)  \
+  X(3, 128, 4, 1024, 0, 1536)  \
+  X(4, 128, 4, 128, 1, 1536)   \
+  X(5, 128, 4, 128, 1, 1024)   \
+  X(6, 128, 8, 256, 1, 1024)   \
+  X(7, 128, 4, 128, 1, 1280)   \
+  X(8, 128, 4, 256, 1, 1280)
 
 const ExpandShape kExpandShapes[] = {
-#define X(id, b, e, c, w) {id, b, e, c, w},
+#define X(id, b, e, c, w, t) {id, b, e, c, w},
     GBFS_EXPAND_SHAPES(X)
 #undef X
 };
 const int kNumExpandShapes = sizeof(kExpandShapes) / sizeof(kExpandShapes[0]);
 
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
-  auto kern = a.allow_bottom_up ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT>
-                                : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT>;
+  auto kern = a.allow_bottom_up ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT, TPS>
+                                : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT, TPS>;
   static bool attr_set[2] = {false, false};
   if (!attr_set[a.allow_bottom_up ? 1 : 0]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -975,11 +972,11 @@ static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cud
 }
 
 // All CTAs of a cooperative launch must be resident at once: occupancy x SMs.
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static int persistent_grid_t(int num_sms, bool with_bu) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
-  auto kern = with_bu ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT>
-                      : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT>;
+  auto kern = with_bu ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT, TPS>
+                      : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT, TPS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
@@ -989,8 +986,8 @@ static int persistent_grid_t(int num_sms, bool with_bu) {
 template <typename OffT>
 cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
-#define X(id, b, e, c, w) \
-  case id: return launch_persistent_t<OffT, b, e, c, w != 0>(a, grid, st);
+#define X(id, b, e, c, w, t) \
+  case id: return launch_persistent_t<OffT, b, e, c, w != 0, t>(a, grid, st);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -1000,8 +997,8 @@ cudaError_t launch_persistent(int shape, const PersistArgs<OffT>& a, int grid, c
 template <typename OffT>
 int persistent_grid(int shape, int num_sms, bool with_bu) {
   switch (shape) {
-#define X(id, b, e, c, w) \
-  case id: return persistent_grid_t<OffT, b, e, c, w != 0>(num_sms, with_bu);
+#define X(id, b, e, c, w, t) \
+  case id: return persistent_grid_t<OffT, b, e, c, w != 0, t>(num_sms, with_bu);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -1019,8 +1016,8 @@ void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32
 template <typename OffT>
 cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
-#define X(id, b, e, c, w) \
-  case id: return launch_expand_t<OffT, b, e, c, w != 0>(a, grid, st);
+#define X(id, b, e, c, w, t) \
+  case id: return launch_expand_t<OffT, b, e, c, w != 0, t>(a, grid, st);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }
@@ -1030,8 +1027,8 @@ cudaError_t launch_expand(int shape, const ExpandArgs<OffT>& a, int grid, cudaSt
 template <typename OffT>
 int expand_grid(int shape, int num_sms) {
   switch (shape) {
-#define X(id, b, e, c, w) \
-  case id: return occupancy_t<OffT, b, e, c, w != 0>(num_sms);
+#define X(id, b, e, c, w, t) \
+  case id: return occupancy_t<OffT, b, e, c, w != 0, t>(num_sms);
     GBFS_EXPAND_SHAPES(X)
 #undef X
   }

@@ -27,6 +27,8 @@ struct Packed {
 // Frontier in the form the expansion consumes: vertex ids, the exclusive scan of their
 // degrees (cum[k] = sum of deg(v[j]) for j < k) and base[k] = off[v[k]] - cum[k], so edge
 // e of the level's edge space (cum[k] <= e < cum[k + 1]) is column entry base[k] + e.
+// The expansion needs v[k] only as the parent it writes, so on a degree-relabelled graph
+// v holds caller ids while base is computed from the internal id.
 template <typename OffT>
 struct FrontierBuf {
   int32_t* v;

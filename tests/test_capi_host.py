@@ -112,6 +112,8 @@ def test_shape_tables(capi):
             assert info["claim_buffer"] >= tile and tile % 128 == 0
             assert info["warp_tiles"] in (0, 1) and (kind == capi.BFS_KERNEL_SINGLE or not info["warp_tiles"])
     assert capi.bfs_shape_count(7) == 0
+    # tests/test_gpu_bfs.py runs every single-source shape: keep its list in step
+    assert capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE) == 9
     with pytest.raises(capi.BfsError):
         capi.bfs_shape_info(0, 99)
 

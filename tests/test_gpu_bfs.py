@@ -113,7 +113,7 @@ def test_grid3d_manhattan(torch_cuda, oracle_mod, graphs_mod):
         capi.bfs_graph_destroy(h)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("shape", list(range(9)))
 @pytest.mark.parametrize("force64", [False, True])
 def test_rmat16_all_shapes(torch_cuda, oracle_mod, graphs_mod, shape, force64):
     """R-MAT scale 16, edge factor 16 (the small configuration): 16 seeded roots, every
@@ -124,7 +124,7 @@ def test_rmat16_all_shapes(torch_cuda, oracle_mod, graphs_mod, shape, force64):
     roots = graphs_mod.pick_roots(g, 16, graphs_mod.root_seed(graphs_mod.GRAPH_SEED_BASE + 0))
     h = _upload(capi, g, force64, shape=shape)
     try:
-        for r in roots[: 16 if shape == 1 else 4]:
+        for r in roots[: 16 if shape == 7 else 4]:
             check_root(capi, oracle_mod, torch_cuda, h, g, int(r))
     finally:
         capi.bfs_graph_destroy(h)
