@@ -695,7 +695,7 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
       for (; i + 4 <= e && !found; i += 4) {
         int32_t u4[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) u4[j] = ld_nc(cols + i + j);
+        for (int j = 0; j < 4; ++j) u4[j] = __ldg(cols + i + j);  // one L1 fill for the four
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const uint32_t u = (uint32_t)u4[j];
@@ -706,7 +706,7 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
         }
       }
       for (; i < e && !found; ++i) {
-        const uint32_t u = (uint32_t)ld_nc(cols + i);
+        const uint32_t u = (uint32_t)__ldg(cols + i);
         if (u < (uint64_t)n && ((fbm_in[u >> 5] >> (u & 31)) & 1u)) {
           found = true;
           parent = (int32_t)u;
