@@ -86,7 +86,9 @@ bfs_status ensure_single_ws(bfs_graph_s* G) {
     if ((s = device_alloc(&ws.v[i], (size_t)g.n, "frontier"))) goto bad;
     if ((s = device_alloc(reinterpret_cast<char**>(&ws.cum[i]), (size_t)g.n * osz, "frontier scan"))) goto bad;
     if ((s = device_alloc(reinterpret_cast<char**>(&ws.base[i]), (size_t)g.n * osz, "frontier base"))) goto bad;
-    if ((s = device_alloc(&ws.chunk[i], (size_t)ws.chunk_cap, "chunk index"))) goto bad;
+    // tile descriptors: 16 bytes for either offset width
+    static_assert(sizeof(TileDesc<int32_t>) == 16 && sizeof(TileDesc<int64_t>) == 16, "descriptor size");
+    if ((s = device_alloc(reinterpret_cast<char**>(&ws.chunk[i]), (size_t)ws.chunk_cap * 16, "chunk index"))) goto bad;
   }
   if ((s = device_alloc(&ws.ctl, 1, "control block"))) goto bad;
   if ((s = device_alloc(&ws.pctl, 1, "control block"))) goto bad;
@@ -130,8 +132,8 @@ ExpandArgs<OffT> make_args(const bfs_graph_s* G, uint32_t* bitmap) {
   a.n = g.n;
   a.fr[0] = ws.fr<OffT>(0);
   a.fr[1] = ws.fr<OffT>(1);
-  a.chunk[0] = ws.chunk[0];
-  a.chunk[1] = ws.chunk[1];
+  a.chunk[0] = ws.desc<OffT>(0);
+  a.chunk[1] = ws.desc<OffT>(1);
   a.ctl = ws.ctl;
   a.pk = g.pk;
   a.cond = 0;
@@ -243,8 +245,8 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.nnz = G->g.nnz;
     pa.fr[0] = ws.fr<OffT>(0);
     pa.fr[1] = ws.fr<OffT>(1);
-    pa.chunk[0] = ws.chunk[0];
-    pa.chunk[1] = ws.chunk[1];
+    pa.chunk[0] = ws.desc<OffT>(0);
+    pa.chunk[1] = ws.desc<OffT>(1);
     pa.ctl = ws.pctl;
     pa.pk = G->g.pk;
     pa.levels = dl;

@@ -37,7 +37,7 @@ namespace gbfs {
 template <typename OffT>
 __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t root, const int32_t* new_id,
                               int32_t* levels, int32_t* parents, uint32_t* bitmap, FrontierBuf<OffT> f0,
-                              int32_t* chunk0, Ctl* ctl, Packed pk) {
+                              TileDesc<OffT>* chunk0, Ctl* ctl, Packed pk) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < n; i += stride) {  // outputs are indexed by caller ids
@@ -51,7 +51,7 @@ __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t r
   const OffT o0 = off[rn], deg = off[rn + 1] - o0;
   // chunk starts of the root's row, spread over the grid (a hub root spans many chunks)
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
-  for (int64_t c = tid; c < nchunks; c += stride) chunk0[c] = 0;
+  for (int64_t c = tid; c < nchunks; c += stride) chunk0[c] = TileDesc<OffT>{0, root, o0 + (OffT)(c * kChunk)};
   if (tid == 0) {
     f0.v[0] = root;  // the queue holds caller ids
     f0.cum[0] = 0;
@@ -134,7 +134,7 @@ __global__ void k_scan_top(OffT* partial, int nparts, int64_t nf, Ctl* ctl, Pack
 
 template <typename OffT>
 __global__ void k_scan_final(const OffT* __restrict__ off, int64_t n, const int32_t* __restrict__ front,
-                             int64_t nf, const OffT* partial, FrontierBuf<OffT> f, int32_t* chunk,
+                             int64_t nf, const OffT* partial, FrontierBuf<OffT> f, TileDesc<OffT>* chunk,
                              const Ctl* ctl) {
   __shared__ OffT s_warp[33];
   if (ctl->error & kErrCounterOverflow) return;  // reported by k_scan_top; nothing to expand
@@ -159,7 +159,7 @@ __global__ void k_scan_final(const OffT* __restrict__ off, int64_t n, const int3
       f.v[i] = v;
       f.cum[i] = c;
       f.base[i] = o - c;
-      write_chunks(chunk, c, d, (int32_t)i);
+      write_descs(chunk, c, d, (int32_t)i, v, o - c);
     }
     carry += total;
   }
@@ -192,8 +192,8 @@ struct ExpandShared {
 template <typename OffT>
 struct LevelIO {
   FrontierBuf<OffT> in, out;
-  const int32_t* chunk_in;
-  int32_t* chunk_out;
+  const TileDesc<OffT>* chunk_in;
+  TileDesc<OffT>* chunk_out;
   unsigned long long* counter_out;  // packed (count, edges) of the next frontier
   int32_t* levels;
   int32_t* parents;
@@ -226,10 +226,12 @@ __device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const L
     const int32_t v = s_claim[i].x;
     const OffT d = (OffT)s_claim[i].y;
     const int32_t slot = (int32_t)(slot0 + i);
-    io.out.v[slot] = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
+    const int32_t vc = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
+    const OffT b = off[v] - run;
+    io.out.v[slot] = vc;
     io.out.cum[slot] = run;
-    io.out.base[slot] = off[v] - run;
-    write_chunks(io.chunk_out, run, d, slot);
+    io.out.base[slot] = b;
+    write_descs(io.chunk_out, run, d, slot, vc, b);
     run += d;
   }
 }
@@ -255,10 +257,12 @@ __device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const Lev
     const int32_t v = buf[i].x;
     const OffT d = (OffT)buf[i].y;
     const int32_t slot = (int32_t)(slot0 + i);
-    io.out.v[slot] = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
+    const int32_t vc = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
+    const OffT b = off[v] - run;
+    io.out.v[slot] = vc;
     io.out.cum[slot] = run;
-    io.out.base[slot] = off[v] - run;
-    write_chunks(io.chunk_out, run, d, slot);
+    io.out.base[slot] = b;
+    write_descs(io.chunk_out, run, d, slot, vc, b);
     run += d;
   }
   __syncwarp();
@@ -304,8 +308,8 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
     const int cnt = (int)min((OffT)T, r - e0);
     __syncthreads();  // the previous tile's shared-memory reads are done
     if (threadIdx.x == 0) {
-      sh.klo = io.chunk_in[e0 / kChunk];
-      sh.kend = (e0 + cnt < r) ? io.chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+      sh.klo = io.chunk_in[e0 / kChunk].k;
+      sh.kend = (e0 + cnt < r) ? io.chunk_in[(e0 + cnt) / kChunk].k : (int32_t)(nf - 1);
     }
     __syncthreads();
     const int klo = sh.klo;
@@ -453,13 +457,17 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
   for (int64_t tile = tile0; tile < ntiles; tile += tstride) {
     const OffT e0 = (OffT)(tile * TW);
     const int cnt = (int)min((OffT)TW, r - e0);
-    const int32_t klo = io.chunk_in[e0 / kChunk];
-    const int32_t kend = (e0 + cnt < r) ? io.chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+    const TileDesc<OffT> d0 = io.chunk_in[e0 / kChunk];
+    const int32_t klo = d0.k;
+    const int32_t kend = (e0 + cnt < r) ? io.chunk_in[(e0 + cnt) / kChunk].k : (int32_t)(nf - 1);
+    // A tile inside one row (the entry of its first edge also holds the edge after it)
+    // needs no staging: its descriptor gives the column entry and the parent.
+    const bool one_row = klo == kend;
     const int s = kend - klo + 1;
     const bool fast = s <= TW + 1;
     int kk[E];
     __syncwarp();  // the previous tile's shared-memory reads are done
-    if (fast) {
+    if (fast && !one_row) {
 #pragma unroll
       for (int j = 0; j < E; ++j) sm.kmap[lane + 32 * j] = -1;
       __syncwarp();
@@ -495,7 +503,10 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       uu[j] = 0;
       col[j] = 0;
       if (ok[j]) {
-        if (fast) {
+        if (one_row) {
+          col[j] = d0.col + er;
+          uu[j] = d0.u;
+        } else if (fast) {
           col[j] = sm.base[kk[j]] + e0 + er;
           uu[j] = sm.u[kk[j]];
         } else {
@@ -540,17 +551,20 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
         if (io.old_id) ov[j] = __ldg(io.old_id + vv[j]);
       }
     }
-    unsigned ball[E];
+    // From here on a claim is only (vertex, degree): few registers stay live across a flush.
+    int32_t dg[E];
+    unsigned cm = 0;  // bit j: edge j claimed its vertex
     int tot = 0;
 #pragma unroll
     for (int j = 0; j < E; ++j) {
+      dg[j] = (int32_t)(o1[j] - o0[j]);
       if (claimed[j]) {
         io.levels[ov[j]] = L;
         io.parents[ov[j]] = uu[j];
         if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
+        cm |= 1u << j;
       }
-      ball[j] = __ballot_sync(full, claimed[j]);
-      tot += __popc(ball[j]);
+      tot += __popc(__ballot_sync(full, claimed[j]));
     }
     if (tot) {
       if (nc + tot > WCAP) {
@@ -560,8 +574,10 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       }
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        if (claimed[j]) sm.claim[nc + __popc(ball[j] & lanemask_lt())] = make_int2(vv[j], (int32_t)(o1[j] - o0[j]));
-        nc += __popc(ball[j]);
+        const bool c = (cm >> j) & 1u;
+        const unsigned b = __ballot_sync(full, c);
+        if (c) sm.claim[nc + __popc(b & lanemask_lt())] = make_int2(vv[j], dg[j]);
+        nc += __popc(b);
       }
     }
   }
@@ -835,7 +851,7 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU && TPS > 1024 ? 1024 : TPS) / 
 template <typename OffT>
 __global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t root, const int32_t* new_id,
                                int32_t* levels, int32_t* parents, uint32_t* bitmap, uint32_t* fbm0, uint32_t* fbm1,
-                               uint32_t* fbm2, FrontierBuf<OffT> f0, int32_t* chunk0, PCtl* c, Packed pk) {
+                               uint32_t* fbm2, FrontierBuf<OffT> f0, TileDesc<OffT>* chunk0, PCtl* c, Packed pk) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < n; i += stride) {  // outputs are indexed by caller ids
@@ -854,7 +870,7 @@ __global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t 
   }
   const OffT o0 = off[rn], deg = off[rn + 1] - o0;
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
-  for (int64_t ch = tid; ch < nchunks; ch += stride) chunk0[ch] = 0;
+  for (int64_t ch = tid; ch < nchunks; ch += stride) chunk0[ch] = TileDesc<OffT>{0, root, o0 + (OffT)(ch * kChunk)};
   if (tid == 0) {
     f0.v[0] = root;  // the queue holds caller ids
     f0.cum[0] = 0;
@@ -892,7 +908,7 @@ void launch_init_single(const GraphDev& g, int32_t root, int32_t* levels, int32_
   const int block = 256;
   const int grid = g.num_sms * 8;
   k_init_single<OffT><<<grid, block, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, g.new_id, levels,
-                                               parents, ws.bitmap, ws.fr<OffT>(0), ws.chunk[0], ws.ctl, g.pk);
+                                               parents, ws.bitmap, ws.fr<OffT>(0), ws.desc<OffT>(0), ws.ctl, g.pk);
 }
 
 template <typename OffT>
@@ -906,7 +922,8 @@ void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, i
   k_scan_partials<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.ctl);
   const long long max_edges = std::min<long long>((long long)g.pk.mask, (ws.chunk_cap - 1) * (long long)kChunk);
   k_scan_top<OffT><<<1, 1024, 0, st>>>(partial, parts, nf, ws.ctl, g.pk, level, levels, parents, max_edges);
-  k_scan_final<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.fr<OffT>(cur), ws.chunk[cur], ws.ctl);
+  k_scan_final<OffT><<<parts, 256, 0, st>>>(off, g.n, front, nf, partial, ws.fr<OffT>(cur), ws.desc<OffT>(cur),
+                                            ws.ctl);
 }
 
 template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
@@ -1010,7 +1027,7 @@ void launch_init_persist(const GraphDev& g, int32_t root, int32_t* levels, int32
                          cudaStream_t st) {
   k_init_persist<OffT><<<g.num_sms * 8, 256, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, g.new_id,
                                                       levels, parents, ws.bitmap, ws.fbm[0], ws.fbm[1], ws.fbm[2],
-                                                      ws.fr<OffT>(0), ws.chunk[0], ws.pctl, g.pk);
+                                                      ws.fr<OffT>(0), ws.desc<OffT>(0), ws.pctl, g.pk);
 }
 
 template <typename OffT>

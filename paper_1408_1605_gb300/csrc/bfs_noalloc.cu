@@ -7,7 +7,7 @@
 // to fail with out-of-memory in the middle of a request.
 //
 // Limits: n_vertices <= kNoAllocMaxVertices and n_entries <= kNoAllocMaxEntries, int32
-// offsets. The array (about 6.3 MB) is held by every GPU that loads the library until the
+// offsets. The array (about 7.4 MB) is held by every GPU that loads the library until the
 // process exits.
 #include <cuda_runtime.h>
 
@@ -37,7 +37,7 @@ constexpr size_t kOffCum1 = kOffCum0 + kVecBytes;
 constexpr size_t kOffBase0 = kOffCum1 + kVecBytes;
 constexpr size_t kOffBase1 = kOffBase0 + kVecBytes;
 constexpr size_t kOffChunk0 = kOffBase1 + kVecBytes;
-constexpr size_t kChunkBytes = align256(sizeof(int32_t) * kChunkCap);
+constexpr size_t kChunkBytes = align256(sizeof(TileDesc<int32_t>) * kChunkCap);
 constexpr size_t kOffChunk1 = kOffChunk0 + kChunkBytes;
 constexpr size_t kOffCtl = kOffChunk1 + kChunkBytes;
 constexpr size_t kOffCheck = kOffCtl + align256(sizeof(Ctl));
@@ -122,8 +122,8 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
   ws.cum[1] = s + kOffCum1;
   ws.base[0] = s + kOffBase0;
   ws.base[1] = s + kOffBase1;
-  ws.chunk[0] = reinterpret_cast<int32_t*>(s + kOffChunk0);
-  ws.chunk[1] = reinterpret_cast<int32_t*>(s + kOffChunk1);
+  ws.chunk[0] = s + kOffChunk0;
+  ws.chunk[1] = s + kOffChunk1;
   ws.chunk_cap = kChunkCap;
   ws.ctl = reinterpret_cast<Ctl*>(s + kOffCtl);
   unsigned* check = reinterpret_cast<unsigned*>(s + kOffCheck);
@@ -147,8 +147,8 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
   a.n = n_vertices;
   a.fr[0] = ws.fr<int32_t>(0);
   a.fr[1] = ws.fr<int32_t>(1);
-  a.chunk[0] = ws.chunk[0];
-  a.chunk[1] = ws.chunk[1];
+  a.chunk[0] = ws.desc<int32_t>(0);
+  a.chunk[1] = ws.desc<int32_t>(1);
   a.ctl = ws.ctl;
   a.pk = g.pk;
   a.use_cond = 0;

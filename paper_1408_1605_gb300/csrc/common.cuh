@@ -36,6 +36,18 @@ struct FrontierBuf {
   OffT* base;
 };
 
+// Tile descriptor of the chunk index: for every kChunk-th edge c * kChunk of a level's
+// edge space, k = max{k : cum[k] <= c * kChunk} (the binary-search answer of Algorithm 3
+// line 2), plus what a tile that lies inside row k alone needs: the parent to write (the
+// caller id u of entry k) and col = base[k] + c * kChunk, the column entry of that edge.
+// Written by whoever appends entry k to the frontier.
+template <typename OffT>
+struct alignas(16) TileDesc {
+  int32_t k;
+  int32_t u;
+  OffT col;
+};
+
 // Per-search control block in device memory. Two counters alternate by level parity:
 // counter[cur] describes the frontier being expanded, counter[nxt] collects the next one.
 struct Ctl {

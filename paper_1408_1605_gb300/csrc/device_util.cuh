@@ -15,6 +15,17 @@ __device__ __forceinline__ void write_chunks(int32_t* chunk, OffT cum, OffT deg,
   for (; c * kChunk < end; ++c) chunk[c] = k;
 }
 
+// Tile descriptors of frontier entry k (degree deg at scan position cum, column base
+// base = off[v] - cum, caller id u) for every chunk boundary inside its edge range.
+template <typename OffT>
+__device__ __forceinline__ void write_descs(TileDesc<OffT>* desc, OffT cum, OffT deg, int32_t k, int32_t u,
+                                            OffT base) {
+  if (deg <= 0) return;
+  OffT c = (cum + kChunk - 1) / kChunk;
+  const OffT end = cum + deg;
+  for (; c * kChunk < end; ++c) desc[c] = TileDesc<OffT>{k, u, base + c * kChunk};
+}
+
 // Exclusive scan of one value per thread across the block; *total receives the sum.
 // s_warp needs 33 entries. Every thread of the block must call it.
 template <typename OffT>

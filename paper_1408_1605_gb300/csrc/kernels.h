@@ -39,7 +39,7 @@ struct SingleWs {
   int32_t* v[2] = {nullptr, nullptr};
   void* cum[2] = {nullptr, nullptr};
   void* base[2] = {nullptr, nullptr};
-  int32_t* chunk[2] = {nullptr, nullptr};
+  void* chunk[2] = {nullptr, nullptr};  // TileDesc<OffT>[chunk_cap] (the chunk index)
   int64_t chunk_cap = 0;       // entries per chunk array
   Ctl* ctl = nullptr;
   void* scan_partial = nullptr;
@@ -56,6 +56,10 @@ struct SingleWs {
   FrontierBuf<OffT> fr(int i) const {
     return FrontierBuf<OffT>{v[i], reinterpret_cast<OffT*>(cum[i]), reinterpret_cast<OffT*>(base[i])};
   }
+  template <typename OffT>
+  TileDesc<OffT>* desc(int i) const {
+    return reinterpret_cast<TileDesc<OffT>*>(chunk[i]);
+  }
 };
 
 template <typename OffT>
@@ -65,7 +69,7 @@ struct ExpandArgs {
   uint32_t* bitmap;
   int64_t n;
   FrontierBuf<OffT> fr[2];
-  int32_t* chunk[2];
+  TileDesc<OffT>* chunk[2];
   Ctl* ctl;
   Packed pk;
   cudaGraphConditionalHandle cond;
@@ -83,7 +87,7 @@ struct PersistArgs {
   int64_t n;
   int64_t nnz;
   FrontierBuf<OffT> fr[2];
-  int32_t* chunk[2];
+  TileDesc<OffT>* chunk[2];
   PCtl* ctl;
   Packed pk;
   int32_t* levels;
