@@ -538,17 +538,26 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
     }
     OffT o0[E], o1[E];
     int32_t ov[E];
+    unsigned wc = 0;  // bit j: some lane of the warp claimed with edge j (warp-uniform)
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const uint32_t m = 1u << (vv[j] & 31);
       claimed[j] = claimed[j] && !(bits[j] & m);
+      if (__any_sync(full, claimed[j])) wc |= 1u << j;
+    }
+    // Most edges of a large level find their vertex visited: the claim work below is
+    // skipped by a warp-uniform branch wherever no lane of the warp claimed.
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
       o0[j] = 0;
       o1[j] = 0;
       ov[j] = vv[j];
-      if (claimed[j]) {
-        o0[j] = off[vv[j]];
-        o1[j] = off[vv[j] + 1];
-        if (io.old_id) ov[j] = __ldg(io.old_id + vv[j]);
+      if ((wc >> j) & 1u) {
+        if (claimed[j]) {
+          o0[j] = off[vv[j]];
+          o1[j] = off[vv[j] + 1];
+          if (io.old_id) ov[j] = __ldg(io.old_id + vv[j]);
+        }
       }
     }
     // From here on a claim is only (vertex, degree): few registers stay live across a flush.
@@ -558,13 +567,15 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       dg[j] = (int32_t)(o1[j] - o0[j]);
-      if (claimed[j]) {
-        io.levels[ov[j]] = L;
-        io.parents[ov[j]] = uu[j];
-        if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
-        cm |= 1u << j;
+      if ((wc >> j) & 1u) {
+        if (claimed[j]) {
+          io.levels[ov[j]] = L;
+          io.parents[ov[j]] = uu[j];
+          if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
+          cm |= 1u << j;
+        }
+        tot += __popc(__ballot_sync(full, claimed[j]));
       }
-      tot += __popc(__ballot_sync(full, claimed[j]));
     }
     if (tot) {
       if (nc + tot > WCAP) {
