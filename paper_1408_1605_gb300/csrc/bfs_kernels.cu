@@ -236,16 +236,24 @@ __device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const L
   }
 }
 
+// A claim buffered by a warp: everything the append needs, so that it reads nothing more
+// from the graph: the vertex's caller id, its degree and its row offset off[v].
+template <typename OffT>
+struct ClaimRec {
+  int32_t vc;
+  int32_t deg;
+  OffT o0;
+};
+
 // Appends a warp's buffered claims (buf[0..nc), nc <= 32 * P) to the next frontier with
 // one 64-bit atomic for the warp: lane i owns items [i P, i P + P); a warp scan of the
 // degrees gives each item its place in the next level's edge space.
 template <typename OffT, int P>
-__device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const LevelIO<OffT>& io, const int2* buf,
-                                           int nc) {
+__device__ __forceinline__ void warp_flush(Packed pk, const LevelIO<OffT>& io, const ClaimRec<OffT>* buf, int nc) {
   const int lane = threadIdx.x & 31;
   const int lo = min(nc, lane * P), hi = min(nc, lo + P);
   OffT mine = 0;
-  for (int i = lo; i < hi; ++i) mine += (OffT)buf[i].y;
+  for (int i = lo; i < hi; ++i) mine += (OffT)buf[i].deg;
   const OffT inc = warp_inclusive_scan(mine);
   const OffT total = __shfl_sync(0xffffffffu, inc, 31);
   unsigned long long resv = 0;
@@ -254,15 +262,14 @@ __device__ __forceinline__ void warp_flush(const OffT* off, Packed pk, const Lev
   const long long slot0 = pk.count(resv);
   OffT run = (OffT)pk.edges(resv) + inc - mine;
   for (int i = lo; i < hi; ++i) {
-    const int32_t v = buf[i].x;
-    const OffT d = (OffT)buf[i].y;
+    const ClaimRec<OffT> c = buf[i];
+    const OffT d = (OffT)c.deg;
     const int32_t slot = (int32_t)(slot0 + i);
-    const int32_t vc = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
-    const OffT b = off[v] - run;
-    io.out.v[slot] = vc;
+    const OffT b = c.o0 - run;
+    io.out.v[slot] = c.vc;  // caller id (only ever written out as a parent)
     io.out.cum[slot] = run;
     io.out.base[slot] = b;
-    write_descs(io.chunk_out, run, d, slot, vc, b);
+    write_descs(io.chunk_out, run, d, slot, c.vc, b);
     run += d;
   }
   __syncwarp();
@@ -422,7 +429,7 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
 template <typename OffT, int E, int WCAP>
 struct WarpTileSmem {
   static constexpr int TW = 32 * E;  // edges per warp tile
-  int2 claim[WCAP];                  // claimed (vertex, degree), flushed by the warp alone
+  ClaimRec<OffT> claim[WCAP];        // claims, appended by the warp alone
   OffT base[TW + 1];                 // staged frontier entries of the tile
   int32_t u[TW + 1];                 // their caller ids (parents to write)
   int32_t kmap[TW];                  // tile edge -> staged entry that starts there (or -1)
@@ -539,11 +546,20 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
     OffT o0[E], o1[E];
     int32_t ov[E];
     unsigned wc = 0;  // bit j: some lane of the warp claimed with edge j (warp-uniform)
+    int tot = 0;      // claims of the warp in this tile
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const uint32_t m = 1u << (vv[j] & 31);
       claimed[j] = claimed[j] && !(bits[j] & m);
-      if (__any_sync(full, claimed[j])) wc |= 1u << j;
+      const unsigned b = __ballot_sync(full, claimed[j]);
+      if (b) wc |= 1u << j;
+      tot += __popc(b);
+    }
+    // Room for this tile's claims first, while few registers are live.
+    if (nc + tot > WCAP) {
+      __syncwarp();
+      warp_flush<OffT, P>(pk, io, sm.claim, nc);
+      nc = 0;
     }
     // Most edges of a large level find their vertex visited: the claim work below is
     // skipped by a warp-uniform branch wherever no lane of the warp claimed.
@@ -560,40 +576,23 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
         }
       }
     }
-    // From here on a claim is only (vertex, degree): few registers stay live across a flush.
-    int32_t dg[E];
-    unsigned cm = 0;  // bit j: edge j claimed its vertex
-    int tot = 0;
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      dg[j] = (int32_t)(o1[j] - o0[j]);
       if ((wc >> j) & 1u) {
         if (claimed[j]) {
           io.levels[ov[j]] = L;
           io.parents[ov[j]] = uu[j];
           if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
-          cm |= 1u << j;
         }
-        tot += __popc(__ballot_sync(full, claimed[j]));
-      }
-    }
-    if (tot) {
-      if (nc + tot > WCAP) {
-        __syncwarp();
-        warp_flush<OffT, P>(off, pk, io, sm.claim, nc);
-        nc = 0;
-      }
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const bool c = (cm >> j) & 1u;
-        const unsigned b = __ballot_sync(full, c);
-        if (c) sm.claim[nc + __popc(b & lanemask_lt())] = make_int2(vv[j], dg[j]);
+        const unsigned b = __ballot_sync(full, claimed[j]);
+        if (claimed[j])
+          sm.claim[nc + __popc(b & lanemask_lt())] = ClaimRec<OffT>{ov[j], (int32_t)(o1[j] - o0[j]), o0[j]};
         nc += __popc(b);
       }
     }
   }
   __syncwarp();
-  if (nc > 0) warp_flush<OffT, P>(off, pk, io, sm.claim, nc);
+  if (nc > 0) warp_flush<OffT, P>(pk, io, sm.claim, nc);
 }
 
 // Dynamic shared memory of an expansion shape: CTA tiles (staging + CTA claim buffer) or
@@ -703,7 +702,7 @@ __device__ __forceinline__ void grid_barrier(PCtl* c, unsigned nblocks, long lon
 template <typename OffT, int WCAP>
 __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
                          const uint32_t* __restrict__ fbm_in, int64_t n, Packed pk, const LevelIO<OffT>& io,
-                         int2* wbuf, int64_t warp0, int64_t wstride) {
+                         ClaimRec<OffT>* wbuf, int64_t warp0, int64_t wstride) {
   static_assert(WCAP >= 64, "per-warp claim buffer too small");
   constexpr int P = (WCAP + 31) / 32;
   const int lane = threadIdx.x & 31;
@@ -713,10 +712,12 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
   for (int64_t w = warp0; w < nwords; w += wstride) {
     bool found = false;
     int32_t parent = 0, deg = 0;
+    OffT b = 0;
     const uint32_t vis = bitmap[w];
     const int32_t v = (int32_t)(w * 32 + lane);
     if (v < n && !((vis >> lane) & 1u)) {
-      const OffT b = off[v], e = off[v + 1];
+      b = off[v];
+      const OffT e = off[v + 1];
       deg = (int32_t)(e - b);
       OffT i = b;
       for (; i + 4 <= e && !found; i += 4) {
@@ -746,7 +747,7 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
         const int32_t ov = io.old_id ? __ldg(io.old_id + v) : v;
         io.levels[ov] = L;
         io.parents[ov] = io.old_id ? __ldg(io.old_id + parent) : parent;
-        wbuf[nc + __popc(claimed & lanemask_lt())] = make_int2(v, deg);
+        wbuf[nc + __popc(claimed & lanemask_lt())] = ClaimRec<OffT>{ov, deg, b};
       }
       if (lane == 0) {
         bitmap[w] = vis | claimed;
@@ -755,12 +756,12 @@ __device__ void bu_level(const OffT* __restrict__ off, const int32_t* __restrict
       nc += __popc(claimed);
       __syncwarp();
       if (nc > WCAP - 32) {
-        warp_flush<OffT, P>(off, pk, io, wbuf, nc);
+        warp_flush<OffT, P>(pk, io, wbuf, nc);
         nc = 0;
       }
     }
   }
-  if (nc > 0) warp_flush<OffT, P>(off, pk, io, wbuf, nc);
+  if (nc > 0) warp_flush<OffT, P>(pk, io, wbuf, nc);
   __syncthreads();
 }
 
@@ -776,8 +777,9 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU && TPS > 1024 ? 1024 : TPS) / 
   const int warp = threadIdx.x >> 5;
   W* wsm = reinterpret_cast<W*>(smem) + warp;
   // bottom-up claim buffer of this warp: its warp-tile buffer, or its slice of the CTA's
-  constexpr int BU_WCAP = WT ? CLAIM : CLAIM / (BLOCK / 32);
-  int2* bu_buf = WT ? wsm->claim : reinterpret_cast<int2*>(smem + S::off_claim) + warp * BU_WCAP;
+  constexpr int BU_WCAP = WT ? CLAIM : (int)(CLAIM * sizeof(int2) / sizeof(ClaimRec<OffT>)) / (BLOCK / 32);
+  ClaimRec<OffT>* bu_buf =
+      WT ? wsm->claim : reinterpret_cast<ClaimRec<OffT>*>(smem + S::off_claim) + warp * BU_WCAP;
   const int64_t nwords = (a.n + 31) / 32;
   const int64_t gtid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * BLOCK;
