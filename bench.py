@@ -213,8 +213,8 @@ def create_graph(capi, g, relabel: bool) -> int:
 def config_for(wl, g, args) -> dict:
     return {"workload": wl.name, "description": wl.description, "n_vertices": g.n, "csr_entries": g.nnz,
             "offsets": "int64" if g.nnz > 2**31 - 1 else "int32", "roots": args.steps,
-            "vertex_order": "relabelled by degree at graph creation" if use_relabel(wl.kind, args.relabel)
-            else "as generated",
+            "vertex_order": "as generated (the oracle's input)" if args.impl == "reference"
+            else "relabelled by degree at graph creation" if use_relabel(wl.kind, args.relabel) else "as generated",
             "l2_flush": "inputs larger than L2 (column array and per-root outputs exceed the 129 MB L2)",
             "parallelism": f"replicas x{args.gpus}"}
 

@@ -193,7 +193,7 @@ GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n
  * memory at call time: code whose framework allocator owns all device memory, loops in
  * which cudaMalloc / cudaFree would synchronize the device, services that must not fail
  * with out-of-memory mid-request. The paper has no counterpart; the search is the same
- * as bfs_run's, with every work buffer in one static device array (about 6.3 MB, held by
+ * as bfs_run's, with every work buffer in one static device array (about 7.4 MB, held by
  * every GPU that loads the library until the process exits).
  *   row_offsets int32[n_vertices + 1], cols int32[n_entries]: device memory, a symmetric
  *     CSR as for bfs_graph_create (the offsets are checked on the device; column ids are
