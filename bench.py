@@ -160,6 +160,28 @@ def alg_bytes_expand(m_c: int, n_c: int, off_bytes: int) -> int:
     return 8 * m_c + per_vertex * n_c
 
 
+def replica_roots(pool, warmup: int, world: int, rank: int):
+    """Each rank is an independent replica (a single search does not shard without a
+    per-level exchange): the pool's first warmup x world roots warm the ranks up and the
+    rest are dealt round-robin, so the ranks' timed roots are disjoint and cover the pool."""
+    return pool[: warmup * world][rank::world], pool[warmup * world:][rank::world]
+
+
+def aggregate_replicas(hm: float, e2e_hm: float, ms_step: float, world: int, device="cuda"):
+    """Whole-job figures of the replica ranks: the sum of their harmonic-mean GTEPS (every
+    rank searches its own roots: weak scaling) and the slowest rank's time per step. No data
+    path collective; one all_gather of three numbers after the timed region."""
+    if world <= 1:
+        return hm, e2e_hm, ms_step
+    import torch
+
+    t = torch.tensor([hm, e2e_hm, ms_step], dtype=torch.float64, device=device)
+    gathered = [torch.zeros_like(t) for _ in range(world)]
+    torch.distributed.all_gather(gathered, t)
+    return (float(sum(x[0] for x in gathered)), float(sum(x[1] for x in gathered)),
+            float(max(x[2] for x in gathered)))
+
+
 def run_reference(args, wl, g, roots, rank):
     """The reference arm: the CPU oracle as it stands, one thread, on the same graph and
     roots; steps are bounded by a wall-clock budget so the run ends within minutes."""
@@ -261,7 +283,7 @@ def main() -> int:
     need = (args.warmup + args.steps) * world
     pool = np.resize(pool, need) if pool.size < need else pool[:need]
     if args.impl == "reference":
-        timed_roots = pool[args.warmup * world:][rank::world]
+        _, timed_roots = replica_roots(pool, args.warmup, world, rank)
         return run_reference(args, wl, g, timed_roots, rank)
 
     import torch
@@ -273,8 +295,7 @@ def main() -> int:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    warm_roots = pool[: args.warmup * world][rank::world]
-    timed_roots = pool[args.warmup * world:][rank::world]
+    warm_roots, timed_roots = replica_roots(pool, args.warmup, world, rank)
 
     t = time.perf_counter()
     relabel = use_relabel(wl.kind, args.relabel)
@@ -351,14 +372,7 @@ def main() -> int:
         batched = batched_leg(h, g, timed_roots, stats, None if args.no_autotune else tune_class, shapes)
 
     # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks
-    value, ms_step = hm, elapsed_ms / max(len(stats), 1)
-    if world > 1:
-        t_hm = torch.tensor([hm, e2e_hm, ms_step], dtype=torch.float64, device="cuda")
-        gathered = [torch.zeros_like(t_hm) for _ in range(world)]
-        torch.distributed.all_gather(gathered, t_hm)
-        value = float(sum(x[0] for x in gathered))
-        e2e_hm = float(sum(x[1] for x in gathered))
-        ms_step = float(max(x[2] for x in gathered))
+    value, e2e_hm, ms_step = aggregate_replicas(hm, e2e_hm, elapsed_ms / max(len(stats), 1), world)
 
     parity, cpu_baseline = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,0 +1,68 @@
+"""The N > 1 path of bench.py on CPU: replicas only (a single search does not shard without a
+per-level exchange). Roots are dealt to ranks disjointly, the whole-job value is the sum of
+the ranks' harmonic means and the step time the slowest rank's, gathered once after the
+timed region (world size 2, gloo, 127.0.0.1); the reference arm runs on rank 0 only."""
+import os
+import socket
+import types
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_replica_roots_disjoint_and_covering():
+    pool = np.arange(1000, 1100, dtype=np.int32)
+    for world in (1, 2, 3, 4):
+        warm = [bench.replica_roots(pool, 3, world, r)[0] for r in range(world)]
+        timed = [bench.replica_roots(pool, 3, world, r)[1] for r in range(world)]
+        assert sorted(np.concatenate(warm).tolist()) == pool[: 3 * world].tolist()
+        assert sorted(np.concatenate(timed).tolist()) == pool[3 * world:].tolist()
+        for r in range(world):
+            assert len(warm[r]) == 3
+            for q in range(r + 1, world):
+                assert not set(timed[r].tolist()) & set(timed[q].tolist())
+
+
+def test_aggregate_single_rank_is_identity():
+    assert bench.aggregate_replicas(1.5, 2.5, 3.5, 1) == (1.5, 2.5, 3.5)
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        hm, e2e, ms = 10.0 * (rank + 1), 1.0 * (rank + 1), 5.0 + 3.0 * rank
+        got = bench.aggregate_replicas(hm, e2e, ms, world, device="cpu")
+        with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+            f.write(" ".join(repr(x) for x in got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_aggregate_gloo_world_size_2(tmp_path):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    if not torch.distributed.is_available() or not torch.distributed.is_gloo_available():
+        pytest.skip("gloo backend not available")
+    mp.spawn(_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for rank in range(2):
+        vals = [float(x) for x in (tmp_path / f"rank{rank}.txt").read_text().split()]
+        assert vals == [30.0, 3.0, 8.0]  # sum of values, sum of e2e, max of step times
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    args = types.SimpleNamespace(steps=4, warmup=1, gpus=2, impl="reference", relabel="auto")
+    # rank 1 returns before touching the graph or the oracle
+    assert bench.run_reference(args, wl=None, g=None, roots=np.arange(4), rank=1) == 0
