@@ -222,16 +222,22 @@ __device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const L
   const unsigned long long resv = sh.resv;
   const long long slot0 = pk.count(resv);
   run += (OffT)pk.edges(resv);
-  for (int i = lo; i < hi; ++i) {
-    const int32_t v = s_claim[i].x;
-    const OffT d = (OffT)s_claim[i].y;
+  for (int t = 0; t < P; ++t) {  // uniform trip count: the descriptor writes are warp-collective
+    const int i = lo + t;
+    const bool valid = i < hi;
+    OffT d = 0, b = 0;
+    int32_t vc = 0;
     const int32_t slot = (int32_t)(slot0 + i);
-    const int32_t vc = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
-    const OffT b = off[v] - run;
-    io.out.v[slot] = vc;
-    io.out.cum[slot] = run;
-    io.out.base[slot] = b;
-    write_descs(io.chunk_out, run, d, slot, vc, b);
+    if (valid) {
+      const int32_t v = s_claim[i].x;
+      d = (OffT)s_claim[i].y;
+      vc = io.old_id ? __ldg(io.old_id + v) : v;  // caller id (only ever written out as a parent)
+      b = off[v] - run;
+      io.out.v[slot] = vc;
+      io.out.cum[slot] = run;
+      io.out.base[slot] = b;
+    }
+    write_descs_warp(io.chunk_out, valid, run, d, slot, vc, b);
     run += d;
   }
 }
@@ -261,15 +267,20 @@ __device__ __forceinline__ void warp_flush(Packed pk, const LevelIO<OffT>& io, c
   resv = __shfl_sync(0xffffffffu, resv, 0);
   const long long slot0 = pk.count(resv);
   OffT run = (OffT)pk.edges(resv) + inc - mine;
-  for (int i = lo; i < hi; ++i) {
-    const ClaimRec<OffT> c = buf[i];
+  for (int t = 0; t < P; ++t) {  // uniform trip count: the descriptor writes are warp-collective
+    const int i = lo + t;
+    const bool valid = i < hi;
+    ClaimRec<OffT> c{0, 0, 0};
+    if (valid) c = buf[i];
     const OffT d = (OffT)c.deg;
     const int32_t slot = (int32_t)(slot0 + i);
     const OffT b = c.o0 - run;
-    io.out.v[slot] = c.vc;  // caller id (only ever written out as a parent)
-    io.out.cum[slot] = run;
-    io.out.base[slot] = b;
-    write_descs(io.chunk_out, run, d, slot, c.vc, b);
+    if (valid) {
+      io.out.v[slot] = c.vc;  // caller id (only ever written out as a parent)
+      io.out.cum[slot] = run;
+      io.out.base[slot] = b;
+    }
+    write_descs_warp(io.chunk_out, valid, run, d, slot, c.vc, b);
     run += d;
   }
   __syncwarp();
