@@ -74,56 +74,73 @@ void launch_clear_bits(unsigned long long* visited, int64_t n, unsigned long lon
 }
 
 // Adds roots to the frontier the next expansion will read (frontier t = level - 1). With
-// fresh != 0 a new wave starts at frontier 0. One thread: at most 64 roots.
+// fresh != 0 a new wave starts at frontier 0. Thread 0 places the (at most 64) roots; then
+// the block writes the chunk index of their rows (a hub root's row spans many chunks).
 template <typename OffT>
 __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_seeds, int fresh) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  BatchCtl* c = a.ctl;
-  if (fresh) {
-    c->counter[0] = c->counter[1] = 0;
-    c->done[0] = c->done[1] = 0;
-    c->level = 1;
-    c->cont = 1;
-    c->prev_count = 0;
-    c->error = 0;
-    c->alive[0] = c->alive[1] = 0;
-  }
-  const int t = c->level - 1;
-  const int cur = t & 1, q3 = t % 3;
-  long long cnt = a.pk.count(c->counter[cur]);
-  long long e = a.pk.edges(c->counter[cur]);
-  const WaveSlots* sl = a.slots;
-  for (int i = 0; i < n_seeds; ++i) {
-    const int32_t vc = seeds[i].v;                  // caller id (indexes the outputs)
-    const int32_t v = a.new_id ? a.new_id[vc] : vc;  // internal id
-    const unsigned long long m = seeds[i].mask;
-    a.visited[v] |= m;
-    const unsigned long long old = a.fmask[q3][v];
-    a.fmask[q3][v] = old | m;
-    for (unsigned long long bits = m; bits; bits &= bits - 1) {
-      const int b = __ffsll((long long)bits) - 1;
-      sl->lvl[b][vc] = 0;
-      sl->par[b][vc] = vc;
+  __shared__ OffT s_cum[kMaxWave], s_deg[kMaxWave];
+  __shared__ int32_t s_k[kMaxWave];
+  __shared__ int s_new, s_cur;
+  if (threadIdx.x == 0) {
+    BatchCtl* c = a.ctl;
+    if (fresh) {
+      c->counter[0] = c->counter[1] = 0;
+      c->done[0] = c->done[1] = 0;
+      c->level = 1;
+      c->cont = 1;
+      c->prev_count = 0;
+      c->error = 0;
+      c->alive[0] = c->alive[1] = 0;
     }
-    if (old == 0) {
-      const OffT o = a.off[v], d = a.off[v + 1] - o;
-      a.qv[q3][cnt] = v;
-      a.cum[cur][cnt] = (OffT)e;
-      a.base[cur][cnt] = o - (OffT)e;
-      write_chunks(a.chunk[cur], (OffT)e, d, (int32_t)cnt);
-      ++cnt;
-      e += (long long)d;
+    const int t = c->level - 1;
+    const int cur = t & 1, q3 = t % 3;
+    long long cnt = a.pk.count(c->counter[cur]);
+    long long e = a.pk.edges(c->counter[cur]);
+    const WaveSlots* sl = a.slots;
+    int added = 0;
+    for (int i = 0; i < n_seeds; ++i) {
+      const int32_t vc = seeds[i].v;                  // caller id (indexes the outputs)
+      const int32_t v = a.new_id ? a.new_id[vc] : vc;  // internal id
+      const unsigned long long m = seeds[i].mask;
+      a.visited[v] |= m;
+      const unsigned long long old = a.fmask[q3][v];
+      a.fmask[q3][v] = old | m;
+      for (unsigned long long bits = m; bits; bits &= bits - 1) {
+        const int b = __ffsll((long long)bits) - 1;
+        sl->lvl[b][vc] = 0;
+        sl->par[b][vc] = vc;
+      }
+      if (old == 0) {
+        const OffT o = a.off[v], d = a.off[v + 1] - o;
+        a.qv[q3][cnt] = v;
+        a.cum[cur][cnt] = (OffT)e;
+        a.base[cur][cnt] = o - (OffT)e;
+        s_cum[added] = (OffT)e;
+        s_deg[added] = d;
+        s_k[added] = (int32_t)cnt;
+        ++added;
+        ++cnt;
+        e += (long long)d;
+      }
     }
+    c->counter[cur] = a.pk.make(cnt, e);
+    c->cont = cnt > 0;
+    s_new = added;
+    s_cur = cur;
   }
-  c->counter[cur] = a.pk.make(cnt, e);
-  c->cont = cnt > 0;
+  __syncthreads();
+  int32_t* chunk = a.chunk[s_cur];
+  for (int r = 0; r < s_new; ++r) {
+    const OffT c0 = (s_cum[r] + kChunk - 1) / kChunk, c1 = (s_cum[r] + s_deg[r] + kChunk - 1) / kChunk;
+    for (OffT ch = c0 + (OffT)threadIdx.x; ch < c1; ch += (OffT)blockDim.x) chunk[ch] = s_k[r];
+  }
 }
 
 template <typename OffT>
 void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int n_seeds, int wave_level,
                        bool fresh, cudaStream_t st) {
   (void)wave_level;
-  k_batch_seed<OffT><<<1, 32, 0, st>>>(a, seeds_dev, n_seeds, fresh ? 1 : 0);
+  k_batch_seed<OffT><<<1, 256, 0, st>>>(a, seeds_dev, n_seeds, fresh ? 1 : 0);
 }
 
 template <typename OffT, int BLOCK, int E, int CLAIM>
@@ -152,14 +169,19 @@ __device__ __forceinline__ void batch_flush(const BatchArgs<OffT>& a, int nxt, i
   const unsigned long long resv = *s_resv;
   const long long slot0 = a.pk.count(resv);
   run += (OffT)a.pk.edges(resv);
-  for (int i = lo; i < hi; ++i) {
-    const int32_t v = s_claim[i].x;
-    const OffT d = (OffT)s_claim[i].y;
+  for (int t = 0; t < P; ++t) {  // uniform trip count: the chunk writes are warp-collective
+    const int i = lo + t;
+    const bool valid = i < hi;
+    OffT d = 0;
     const int32_t slot = (int32_t)(slot0 + i);
-    a.qv[q3n][slot] = v;
-    a.cum[nxt][slot] = run;
-    a.base[nxt][slot] = a.off[v] - run;
-    write_chunks(a.chunk[nxt], run, d, slot);
+    if (valid) {
+      const int32_t v = s_claim[i].x;
+      d = (OffT)s_claim[i].y;
+      a.qv[q3n][slot] = v;
+      a.cum[nxt][slot] = run;
+      a.base[nxt][slot] = a.off[v] - run;
+    }
+    write_chunks_warp(a.chunk[nxt], valid, run, d, slot);
     run += d;
   }
 }

@@ -26,6 +26,28 @@ __device__ __forceinline__ void write_descs(TileDesc<OffT>* desc, OffT cum, OffT
   for (; c * kChunk < end; ++c) desc[c] = TileDesc<OffT>{k, u, base + c * kChunk};
 }
 
+// Warp-collective version of write_chunks for one entry per lane (valid lanes only): entries
+// crossing more than 32 chunk boundaries are written by the whole warp. Every lane of the
+// warp must call it.
+template <typename OffT>
+__device__ __forceinline__ void write_chunks_warp(int32_t* chunk, bool valid, OffT cum, OffT deg, int32_t k) {
+  OffT c0 = 0, c1 = 0;
+  if (valid && deg > 0) {
+    c0 = (cum + kChunk - 1) / kChunk;
+    c1 = (cum + deg + kChunk - 1) / kChunk;
+  }
+  const bool big = c1 - c0 > 32;
+  if (!big)
+    for (OffT c = c0; c < c1; ++c) chunk[c] = k;
+  const int lane = threadIdx.x & 31;
+  for (unsigned bm = __ballot_sync(0xffffffffu, big); bm; bm &= bm - 1) {
+    const int src = __ffs(bm) - 1;
+    const OffT s0 = __shfl_sync(0xffffffffu, c0, src), s1 = __shfl_sync(0xffffffffu, c1, src);
+    const int32_t sk = __shfl_sync(0xffffffffu, k, src);
+    for (OffT c = s0 + lane; c < s1; c += 32) chunk[c] = sk;
+  }
+}
+
 // Warp-collective version of write_descs for one entry per lane (valid lanes only): an
 // entry whose edge range crosses more than 32 chunk boundaries (a hub row) has its
 // descriptors written by the whole warp instead of serially by its own lane. Every lane of
