@@ -441,19 +441,17 @@ template <typename OffT, int E, int WCAP>
 struct WarpTileSmem {
   static constexpr int TW = 32 * E;  // edges per warp tile
   ClaimRec<OffT> claim[WCAP];        // claims, appended by the warp alone
-  OffT base[TW + 1];                 // staged frontier entries of the tile
-  int32_t u[TW + 1];                 // their caller ids (parents to write)
-  int32_t kmap[TW];                  // tile edge -> staged entry that starts there (or -1)
 };
 
 // The top-down step with warp-sized tiles: warp w expands tiles w, w + W, ... of 32 E
 // edges on its own, so no CTA-wide barrier is needed inside a level. The mapping of edge e
-// to the frontier entry k = max{k : cum[k] <= e} (Algorithm 3 line 2) is built per tile
-// without searching: every staged entry marks the tile edge where its row starts, and an
-// inclusive max-scan over the tile's edges (lane l holds edges l, l + 32, ...) gives each
-// edge the last entry that started at or before it. The rest (column reads, pre-check,
-// atomicOr claim, level / parent writes, fused append and degree scan) is the CTA-tile
-// step's, with the claims appended through the warp's own buffer.
+// to the frontier entry k = max{k : cum[k] <= e} (Algorithm 3 line 2): a tile inside one row
+// takes it from its descriptor; a tile over at most 32 entries holds them one per lane and
+// finds k with a five-step binary search over the lanes (shuffles, no shared memory); a tile
+// over more entries searches the global scan. The rest (column reads, pre-check, atomicOr
+// claim, level / parent writes, fused append and degree scan) is the CTA-tile step's, with
+// the claims appended through the warp's own buffer. Shared memory holds only that buffer,
+// which leaves the most L1 to the bitmap probes.
 template <typename OffT, int E, int WCAP>
 __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __restrict__ cols, uint32_t* bitmap,
                               int64_t n, Packed pk, unsigned* err, const LevelIO<OffT>& io,
@@ -482,34 +480,16 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
     // needs no staging: its descriptor gives the column entry and the parent.
     const bool one_row = klo == kend;
     const int s = kend - klo + 1;
-    const bool fast = s <= TW + 1;
-    int kk[E];
-    __syncwarp();  // the previous tile's shared-memory reads are done
-    if (fast && !one_row) {
-#pragma unroll
-      for (int j = 0; j < E; ++j) sm.kmap[lane + 32 * j] = -1;
-      __syncwarp();
-      for (int i = lane; i < s; i += 32) {
-        const OffT c = io.in.cum[klo + i];
-        sm.base[i] = io.in.base[klo + i];
-        sm.u[i] = io.in.v[klo + i];
-        const OffT rel = c - e0;  // entry klo starts at or before the tile: rel <= 0
-        if (rel < (OffT)TW) atomicMax(&sm.kmap[rel > 0 ? (int)rel : 0], i);
-      }
-      __syncwarp();
-      int carry = -1;
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        int x = sm.kmap[lane + 32 * j];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int y = __shfl_up_sync(full, x, d);
-          if (lane >= d) x = max(x, y);
-        }
-        x = max(x, carry);
-        kk[j] = x;
-        carry = __shfl_sync(full, x, 31);
-      }
+    // Up to 32 entries: lane i holds entry klo + i in registers (where its row starts in the
+    // tile, its column base and caller id); no shared memory is used for staging.
+    const bool fast = s <= 32;
+    int32_t e_rel = 0x7fffffff, e_u = 0;
+    OffT e_base = 0;
+    if (fast && !one_row && lane < s) {
+      const OffT c = io.in.cum[klo + lane];
+      e_rel = (int32_t)max(c - e0, (OffT)0);  // entry klo starts at or before the tile
+      e_base = io.in.base[klo + lane];
+      e_u = io.in.v[klo + lane];
     }
     int32_t vv[E], uu[E];
     OffT col[E];
@@ -520,15 +500,25 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       ok[j] = er < cnt;
       uu[j] = 0;
       col[j] = 0;
+      if (!one_row && fast) {
+        // k = max{i : rel_i <= er} by a binary search over the lanes (rel_0 = 0 <= er)
+        int k = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int rc = __shfl_sync(full, e_rel, k + step);
+          if (rc <= er) k += step;
+        }
+        const OffT b = __shfl_sync(full, e_base, k);
+        const int32_t u = __shfl_sync(full, e_u, k);
+        col[j] = b + e0 + er;
+        uu[j] = u;
+      }
       if (ok[j]) {
         if (one_row) {
           col[j] = d0.col + er;
           uu[j] = d0.u;
-        } else if (fast) {
-          col[j] = sm.base[kk[j]] + e0 + er;
-          uu[j] = sm.u[kk[j]];
-        } else {
-          // many zero-degree frontier entries: search the global scan directly
+        } else if (!fast) {
+          // more than 32 entries (short rows): search the global scan directly
           const OffT e = e0 + er;
           const int32_t k = binsearch_maxle(io.in.cum, (int64_t)klo, (int64_t)kend + 1, e);
           col[j] = io.in.base[k] + e;
