@@ -252,6 +252,8 @@ def main() -> int:
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-waves", type=int, default=0,
+                    help="64-root waves in the batched leg (default: 4 on R-MAT s22, i.e. 256 roots; else 1)")
     ap.add_argument("--no-direction", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "serve", "multigraph"])
     ap.add_argument("--no-autotune", action="store_true")
@@ -312,7 +314,8 @@ def main() -> int:
         tune_roots = pool[: max(3, min(len(pool), 3))]
         rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, tune_class, g.n, tune_roots, lv, pr)
         shapes["single"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"],
-                            "loop": ["persistent", "graph", "host"][rec.get("loop", 1)]}
+                            "loop": ["persistent", "graph", "host"][rec.get("loop", 1)],
+                            "persist_ctas_per_sm": rec.get("persist_ctas", 0)}
         log(f"[bench] single-source shape {shapes['single']} ms per shape {rec.get('ms')}")
     for r in warm_roots:
         capi.bfs_run(h, int(r), lv, pr, want_stats=True)
@@ -369,7 +372,13 @@ def main() -> int:
 
     batched = None
     if not args.no_batched:
-        batched = batched_leg(h, g, timed_roots, stats, None if args.no_autotune else tune_class, shapes)
+        waves = args.batch_waves or (4 if wl.name == "rmat-s22-ef16" else 1)
+        if waves * 64 <= len(timed_roots):
+            broots, bstats = timed_roots[: waves * 64], stats[: waves * 64]
+        else:  # more roots than the timed ones: same seeded draw, single-source times taken here
+            broots = wl.pick_roots(g, waves * 64)
+            bstats = [capi.bfs_run(h, int(r), lv, pr, want_stats=True).as_dict() for r in broots]
+        batched = batched_leg(h, g, broots, bstats, None if args.no_autotune else tune_class, shapes)
 
     # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks
     value, e2e_hm, ms_step = aggregate_replicas(hm, e2e_hm, elapsed_ms / max(len(stats), 1), world)
@@ -426,7 +435,8 @@ def direction_leg(h, g, roots, single_stats, wl, args, lv, pr):
     from paper_1408_1605_gb300 import capi
 
     saved = (capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP), capi.bfs_graph_get_option(h, capi.BFS_OPT_BOTTOM_UP),
-             capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE))
+             capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE),
+             capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS))
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
     shape_ms = None
     if not args.no_autotune:
@@ -459,6 +469,7 @@ def direction_leg(h, g, roots, single_stats, wl, args, lv, pr):
     capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, saved[0])
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, saved[1])
     capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_SINGLE, saved[2])
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_PERSIST_CTAS, saved[3])
     return {"value": round(harmonic_mean(teps), 3), "unit": UNIT, "steps": len(st), "shape": shape,
             "mean_device_ms": round(sum(s["device_ms"] for s in st) / len(st), 4),
             "mean_bottom_up_levels": round(sum(s["bottom_up_levels"] for s in st) / len(st), 2),
@@ -468,7 +479,8 @@ def direction_leg(h, g, roots, single_stats, wl, args, lv, pr):
 
 def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
     """The same roots as 64-root waves (bfs_run_batch): aggregate GTEPS of the waves against
-    the aggregate of the single-source searches (sum m_c / sum time for both)."""
+    the aggregate of the single-source searches of exactly these roots (sum m_c / sum time
+    for both)."""
     import torch
 
     from paper_1408_1605_gb300 import capi
@@ -496,7 +508,8 @@ def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
     agg = edges / (ms * 1e-3)
     del lv, pr
     torch.cuda.empty_cache()
-    return {"waves": waves, "roots_per_wave": wave, "aggregate_gteps": round(agg / 1e9, 3),
+    assert len(single_stats) == len(roots)
+    return {"waves": waves, "roots_per_wave": wave, "roots": len(roots), "aggregate_gteps": round(agg / 1e9, 3),
             "single_source_aggregate_gteps": round(single_agg / 1e9, 3), "ratio": round(agg / single_agg, 3),
             "ms_per_wave": round(ms / waves, 3)}
 

@@ -119,7 +119,10 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *   BFS_OPT_PROBE: how the visited-bit pre-check of each edge is loaded: 0 through L1
  *     (default for BFS_RELABEL_DEGREE graphs; a stale L1 copy only costs a futile atomic),
  *     1 from L2 only (default otherwise; sees the level's claims sooner).
- *   BFS_OPT_RELABELED (read only): 1 if the graph was created with BFS_RELABEL_DEGREE. */
+ *   BFS_OPT_RELABELED (read only): 1 if the graph was created with BFS_RELABEL_DEGREE.
+ *   BFS_OPT_PERSIST_CTAS: CTAs per SM of a persistent search (0, the default: as many as
+ *     fit). Fewer CTAs make each level boundary cheaper, which pays on graphs of hundreds
+ *     of small levels (3D grids); large levels want them all. */
 #define BFS_OPT_LOOP 1
 #define BFS_OPT_BOTTOM_UP 2
 #define BFS_OPT_ALPHA 3
@@ -127,6 +130,7 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
 #define BFS_OPT_WAIT_LIMIT 5
 #define BFS_OPT_PROBE 6
 #define BFS_OPT_RELABELED 7
+#define BFS_OPT_PERSIST_CTAS 8
 #define BFS_LOOP_PERSISTENT 0
 #define BFS_LOOP_GRAPH 1
 #define BFS_LOOP_HOST 2
@@ -322,10 +326,12 @@ GBFS_API bfs_status bfs_graph_get_shape(bfs_graph_t g, int kind, int *shape);
 
 /* Times the candidates of `kind` on this graph and keeps the fastest.
  *   BFS_KERNEL_SINGLE: candidates c = loop x shape: c < count uses BFS_LOOP_GRAPH with shape
- *     c, c >= count BFS_LOOP_PERSISTENT with shape c - count (with BFS_OPT_BOTTOM_UP set,
- *     only the persistent ones; the others report -1). One warm-up search, then one
- *     bfs_run per root; ms_per_shape[c] = mean device ms per root. The winner's loop mode
- *     and shape are set on the graph. ms_per_shape: NULL or double[2 * count].
+ *     c, count <= c < 2 count BFS_LOOP_PERSISTENT with shape c - count and as many CTAs as
+ *     fit, 2 count <= c < 3 count BFS_LOOP_PERSISTENT with shape c - 2 count and 2 CTAs per
+ *     SM (BFS_OPT_PERSIST_CTAS; with BFS_OPT_BOTTOM_UP set, only the persistent ones; the
+ *     others report -1). One warm-up search, then one bfs_run per root; ms_per_shape[c] =
+ *     mean device ms per root. The winner's loop mode, CTAs per SM and shape are set on the
+ *     graph. ms_per_shape: NULL or double[3 * count].
  *   BFS_KERNEL_BATCH: candidates = shapes; n_roots <= 64; one warm-up wave and one timed
  *     wave per shape; ms_per_shape[s] = device ms per wave (double[count]).
  * count = bfs_shape_count(kind); best_shape: NULL or the winning candidate index.

@@ -61,6 +61,7 @@ def apply_or_tune(graph: int, kind: int, graph_class: str, n_vertices: int, root
     if rec is not None and not force and 0 <= rec.get("shape", -1) < count:
         if kind == capi.BFS_KERNEL_SINGLE and "loop" in rec:
             capi.bfs_graph_set_option(graph, capi.BFS_OPT_LOOP, rec["loop"])
+            capi.bfs_graph_set_option(graph, capi.BFS_OPT_PERSIST_CTAS, rec.get("persist_ctas", 0))
         capi.bfs_graph_set_shape(graph, kind, rec["shape"])
         return dict(rec, cached=True)
     best, ms = capi.bfs_tune(graph, kind, roots, levels, parents)
@@ -68,6 +69,7 @@ def apply_or_tune(graph: int, kind: int, graph_class: str, n_vertices: int, root
     rec = {"shape": shape, "ms": ms, "shape_info": capi.bfs_shape_info(kind, shape), "when": time.time()}
     if kind == capi.BFS_KERNEL_SINGLE:
         rec["loop"] = capi.BFS_LOOP_GRAPH if best < count else capi.BFS_LOOP_PERSISTENT
+        rec["persist_ctas"] = capi.bfs_graph_get_option(graph, capi.BFS_OPT_PERSIST_CTAS)
     db = _load()
     db[k] = rec
     _store(db)

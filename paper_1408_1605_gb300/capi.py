@@ -32,6 +32,7 @@ BFS_OPT_BETA = 4
 BFS_OPT_WAIT_LIMIT = 5
 BFS_OPT_PROBE = 6
 BFS_OPT_RELABELED = 7
+BFS_OPT_PERSIST_CTAS = 8
 BFS_LOOP_PERSISTENT = 0
 BFS_LOOP_GRAPH = 1
 BFS_LOOP_HOST = 2
@@ -312,11 +313,12 @@ def bfs_graph_get_shape(graph: int, kind: int) -> int:
 
 def bfs_tune(graph: int, kind: int, roots, levels, parents, stream=None):
     """Returns (best candidate, [ms per candidate]); single-source candidates are
-    (graph loop, shape 0..count-1) then (persistent loop, shape 0..count-1)."""
+    (graph loop, shape 0..count-1), (persistent loop, shape 0..count-1), then (persistent
+    loop with 2 CTAs per SM, shape 0..count-1)."""
     import numpy as np
 
     r = np.ascontiguousarray(roots, dtype=np.int32)
-    n = bfs_shape_count(kind) * (2 if kind == BFS_KERNEL_SINGLE else 1)
+    n = bfs_shape_count(kind) * (3 if kind == BFS_KERNEL_SINGLE else 1)
     ms = (ctypes.c_double * max(n, 1))()
     best = ctypes.c_int(-1)
     check(lib().bfs_tune(graph, int(kind), r.ctypes.data, int(r.size), ptr(levels), ptr(parents),

@@ -258,7 +258,10 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.spin_limit = G->wait_limit;
     pa.old_id = G->g.old_id;
     int& pg = G->pgrid[G->bottom_up ? 1 : 0];
-    if (!pg) pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
+    if (!pg) {
+      pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
+      if (G->persist_ctas > 0) pg = std::min(pg, G->persist_ctas * G->g.num_sms);
+    }
     if ((e = launch_persistent<OffT>(G->shape, pa, pg, st)) != cudaSuccess)
       return cuda_fail(e, "persistent search kernel");
   } else if (G->host_loop) {
@@ -579,6 +582,14 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
       if (value < 0 || value > (1ll << 40)) return fail(BFS_ERR_INVALID_ARG, "wait limit outside [0, 2^40]");
       G->wait_limit = value;
       return BFS_OK;
+    case BFS_OPT_PERSIST_CTAS:
+      if (value < 0 || value > 64) return fail(BFS_ERR_INVALID_ARG, "CTAs per SM outside [0, 64]");
+      if (G->persist_ctas != (int)value) {
+        if (G->last_done) cudaEventSynchronize(G->last_done);
+        G->persist_ctas = (int)value;
+        G->pgrid[0] = G->pgrid[1] = 0;
+      }
+      return BFS_OK;
     case BFS_OPT_PROBE:
       if (value < 0 || value > 1) return fail(BFS_ERR_INVALID_ARG, "probe mode outside [0, 1]");
       if (G->probe_mode != (int)value) {
@@ -601,6 +612,7 @@ GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* val
     case BFS_OPT_BETA: *value = G->beta; return BFS_OK;
     case BFS_OPT_WAIT_LIMIT: *value = G->wait_limit; return BFS_OK;
     case BFS_OPT_PROBE: *value = G->probe_mode; return BFS_OK;
+    case BFS_OPT_PERSIST_CTAS: *value = G->persist_ctas; return BFS_OK;
     case BFS_OPT_RELABELED: *value = G->g.new_id != nullptr; return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");

@@ -37,6 +37,7 @@ struct bfs_graph_s {
   int alpha = 8, beta = 24;
   int probe_mode = 1;       // bitmap pre-check through L2 (1) or default caching (0)
   long long wait_limit = 1ll << 27;  // grid-barrier polls before a wait gives up
+  int persist_ctas = 0;     // CTAs per SM of a persistent search (0: as many as fit)
   int pgrid[2] = {0, 0};    // CTAs of the persistent kernel (top-down only, with bottom-up)
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;

@@ -132,6 +132,7 @@ def test_autotune_cache_roundtrip(capi, monkeypatch, tmp_path):
     monkeypatch.setattr(capi, "bfs_tune", fake_tune)
     monkeypatch.setattr(capi, "bfs_graph_set_shape", lambda g, k, s: calls["set"].append((k, s)))
     monkeypatch.setattr(capi, "bfs_graph_set_option", lambda g, o, v: calls["set"].append(("opt", o, v)))
+    monkeypatch.setattr(capi, "bfs_graph_get_option", lambda g, o: 0)
     r1 = autotune.apply_or_tune(0, capi.BFS_KERNEL_SINGLE, "rmat", 1 << 20, [1], None, None)
     assert r1["shape"] == 1 and not r1["cached"] and calls["tune"] == 1
     r2 = autotune.apply_or_tune(0, capi.BFS_KERNEL_SINGLE, "rmat", (1 << 20) + 5, [1], None, None)

@@ -127,7 +127,7 @@ def test_option_errors(torch_cuda, graphs_mod):
     h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
     try:
         assert capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP) == capi.BFS_LOOP_GRAPH
-        for opt, val in ((capi.BFS_OPT_LOOP, 7), (capi.BFS_OPT_ALPHA, 0), (99, 1)):
+        for opt, val in ((capi.BFS_OPT_LOOP, 7), (capi.BFS_OPT_ALPHA, 0), (capi.BFS_OPT_PERSIST_CTAS, 65), (99, 1)):
             with pytest.raises(capi.BfsError):
                 capi.bfs_graph_set_option(h, opt, val)
     finally:
@@ -175,3 +175,21 @@ def test_barrier_wait_expiry_reports_timeout(torch_cuda, oracle_mod, graphs_mod)
         _check(capi, oracle_mod, torch_cuda, h, g, r)
     finally:
         capi.bfs_graph_destroy(h)
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_few_ctas_per_sm(torch_cuda, oracle_mod, graphs_mod, ctas):
+    """A persistent search with BFS_OPT_PERSIST_CTAS set (fewer, larger level boundaries)
+    returns the same BFS, top-down and direction-optimizing."""
+    from paper_1408_1605_gb300 import capi
+
+    for g in (graphs_mod.rmat(15, 16, seed=29), graphs_mod.grid3d(21, 19, 17)):
+        for policy in ("persistent-td", "persistent-do"):
+            h = _upload(capi, g, policy)
+            try:
+                capi.bfs_graph_set_option(h, capi.BFS_OPT_PERSIST_CTAS, ctas)
+                assert capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS) == ctas
+                for root in (0, g.n // 3, g.n - 1):
+                    _check(capi, oracle_mod, torch_cuda, h, g, root)
+            finally:
+                capi.bfs_graph_destroy(h)
