@@ -110,6 +110,10 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *     related work, Sec. 6) when frontier edges x ALPHA exceed the unexplored edges, and
  *     return to top-down once frontier vertices x BETA < n. Results are the same BFS
  *     (levels identical; parents valid). Default 0: every level top-down (Algorithm 3).
+ *     The option also applies to bfs_run_batch: a wave then runs large levels bottom-up
+ *     (every vertex pulls the root bits it misses from its neighbours' frontier masks),
+ *     switching by the same rule on the wave's union frontier; per_root_stats report the
+ *     wave's bottom-up levels. Serving waves stay top-down.
  *   BFS_OPT_ALPHA (default 8; swept on GB300: 8 beat 2, 4, 6, 14 on R-MAT and uniform graphs),
  *   BFS_OPT_BETA (default 24): the switching thresholds.
  *   BFS_OPT_WAIT_LIMIT: polls a CTA makes at a grid barrier of a persistent search before it

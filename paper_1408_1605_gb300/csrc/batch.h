@@ -30,6 +30,9 @@ struct BatchCtl {
   unsigned int emit_done;         // CTAs finished in the emit kernel (last-CTA detection)
   unsigned long long alive[2];    // OR of the masks claimed by the running expansion (next parity)
   unsigned long long ovf_count;   // parent events that did not fit the per-vertex slots
+  int bu;                         // the running level goes bottom-up (set by the previous level)
+  int bu_levels;                  // bottom-up levels so far
+  long long seen;                 // degree sum of the frontiers expanded so far
 };
 
 // Parent event of a claim: vertex u's edge claimed the bits `mask` of the claimed vertex
@@ -68,6 +71,9 @@ struct BatchArgs {
   int use_cond;
   const int32_t* new_id;          // caller -> internal vertex id (NULL: identity)
   const int32_t* old_id;          // internal -> caller vertex id (NULL: identity)
+  int64_t nnz;
+  int allow_bu;                   // bottom-up levels allowed (Beamer's switching, per wave)
+  int alpha, beta;                // switching thresholds (as for single-source searches)
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -121,6 +127,7 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.use_cond = 0;
   a.new_id = g.new_id;
   a.old_id = g.old_id;
+  a.nnz = g.nnz;
   return a;
 }
 

@@ -141,7 +141,11 @@ bfs_status ensure_batch_state(bfs_graph_s* G) {
 
 template <typename OffT>
 BatchArgs<OffT> batch_args(const bfs_graph_s* G) {
-  return make_batch_args<OffT>(G->g, G->batch->b);
+  BatchArgs<OffT> a = make_batch_args<OffT>(G->g, G->batch->b);
+  a.allow_bu = G->bottom_up;  // BFS_OPT_BOTTOM_UP also lets waves run bottom-up levels
+  a.alpha = G->alpha;
+  a.beta = G->beta;
+  return a;
 }
 
 template BatchArgs<int32_t> batch_args<int32_t>(const bfs_graph_s*);
@@ -293,7 +297,7 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
       cudaEventElapsedTime(&loop_ms, S->ev_mid, S->ev1);
       for (int b = 0; b < n_roots; ++b) {
         stats[b].depth = (int32_t)S->stats_host[3 * b + 2];
-        stats[b].bottom_up_levels = 0;
+        stats[b].bottom_up_levels = S->ctl_host->bu_levels;  // levels the wave ran bottom-up
         stats[b].vertices_reached = S->stats_host[3 * b + 1];
         stats[b].edges_traversed = S->stats_host[3 * b + 0] / 2;
         stats[b].device_ms = ms;

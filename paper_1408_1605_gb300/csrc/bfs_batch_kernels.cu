@@ -91,6 +91,9 @@ __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_see
       c->prev_count = 0;
       c->error = 0;
       c->alive[0] = c->alive[1] = 0;
+      c->bu = 0;
+      c->bu_levels = 0;
+      c->seen = 0;
     }
     const int t = c->level - 1;
     const int cur = t & 1, q3 = t % 3;
@@ -102,6 +105,7 @@ __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_see
       const int32_t vc = seeds[i].v;                  // caller id (indexes the outputs)
       const int32_t v = a.new_id ? a.new_id[vc] : vc;  // internal id
       const unsigned long long m = seeds[i].mask;
+      c->alive[cur] |= m;  // roots with a frontier (bottom-up levels look for these bits)
       a.visited[v] |= m;
       const unsigned long long old = a.fmask[q3][v];
       a.fmask[q3][v] = old | m;
@@ -186,6 +190,124 @@ __device__ __forceinline__ void batch_flush(const BatchArgs<OffT>& a, int nxt, i
   }
 }
 
+// Appends a warp's buffered claims (vertex, degree) to the wave's next frontier with one
+// 64-bit atomic (the batched counterpart of the single-source warp append).
+template <typename OffT, int P>
+__device__ __forceinline__ void batch_warp_flush(const BatchArgs<OffT>& a, int nxt, int q3n, const int2* buf,
+                                                 int nc) {
+  const int lane = threadIdx.x & 31;
+  const int lo = min(nc, lane * P), hi = min(nc, lo + P);
+  OffT mine = 0;
+  for (int i = lo; i < hi; ++i) mine += (OffT)buf[i].y;
+  const OffT inc = warp_inclusive_scan(mine);
+  const OffT total = __shfl_sync(0xffffffffu, inc, 31);
+  unsigned long long resv = 0;
+  if (lane == 0) resv = atomicAdd(&a.ctl->counter[nxt], a.pk.make(nc, (long long)total));
+  resv = __shfl_sync(0xffffffffu, resv, 0);
+  const long long slot0 = a.pk.count(resv);
+  OffT run = (OffT)a.pk.edges(resv) + inc - mine;
+  for (int t = 0; t < P; ++t) {  // uniform trip count: the chunk writes are warp-collective
+    const int i = lo + t;
+    const bool valid = i < hi;
+    OffT d = 0;
+    const int32_t slot = (int32_t)(slot0 + i);
+    if (valid) {
+      const int32_t v = buf[i].x;
+      d = (OffT)buf[i].y;
+      a.qv[q3n][slot] = v;
+      a.cum[nxt][slot] = run;
+      a.base[nxt][slot] = a.off[v] - run;
+    }
+    write_chunks_warp(a.chunk[nxt], valid, run, d, slot);
+    run += d;
+  }
+  __syncwarp();
+}
+
+// One bottom-up level of a wave (the multi-source form of Beamer's step, the paper's
+// related work, Sec. 6): every vertex v still missing some active root's bit scans its row
+// and takes, from each neighbour u, the bits of F_t[u] it still needs (each bit's parent is
+// the first u that has it), stopping once it has them all. No atomics: each vertex is
+// owned by one lane (warp w takes vertices 32 w ... 32 w + 31). Claims become parent events
+// and next-frontier entries exactly as in the top-down step, so the emit kernel writes the
+// outputs in both cases.
+template <typename OffT, int WCAP>
+__device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long long* __restrict__ F,
+                               unsigned long long* Fn, unsigned long long active, int nxt, int q3n, int2* wbuf,
+                               int32_t* const* s_par, unsigned long long* s_alive) {
+  static_assert(WCAP >= 64, "per-warp claim buffer too small");
+  constexpr int P = (WCAP + 31) / 32;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  int nc = 0;  // warp-uniform
+  unsigned long long mine = 0ull;
+  for (int64_t w = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); w * 32 < a.n; w += nwarps) {
+    const int64_t x = w * 32 + lane;
+    const int32_t v = (int32_t)x;
+    unsigned long long acc = 0ull;
+    int32_t deg = 0;
+    if (x < a.n) {
+      const unsigned long long need = active & ~a.visited[v];
+      if (need) {
+        const OffT b = a.off[v], e = a.off[v + 1];
+        deg = (int32_t)(e - b);
+        int nev = 0;
+        for (OffT i = b; i < e && acc != need; ++i) {
+          const uint32_t u = (uint32_t)__ldg(a.cols + i);
+          if (u >= (uint64_t)a.n) {
+            atomicOr(&a.ctl->error, kErrColumnRange);
+            continue;
+          }
+          const unsigned long long f = F[u] & need & ~acc;
+          if (f) {
+            acc |= f;
+            const int32_t uc = a.old_id ? __ldg(a.old_id + u) : (int32_t)u;
+            if (nev < kEventSlots) {
+              ClaimEvent ce;
+              ce.u = uc;
+              ce.pad = 0;
+              ce.mask = f;
+              a.ev[(size_t)v * kEventSlots + nev] = ce;
+            } else {
+              const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;
+              const unsigned long long o = atomicAdd(&a.ctl->ovf_count, 1ull);
+              if ((long long)o < a.ovf_cap) {
+                a.ovf[o] = OvfEvent{vc, uc, f};
+              } else {
+                for (unsigned long long bits = f; bits; bits &= bits - 1)  // no room: write now
+                  s_par[__ffsll((long long)bits) - 1][vc] = uc;
+              }
+            }
+            ++nev;
+          }
+        }
+        if (acc) {  // this lane owns v: plain stores
+          a.visited[v] |= acc;
+          Fn[v] = acc;
+          a.evc[v] = min(nev, kEventSlots);
+          mine |= acc;
+        }
+      }
+    }
+    const bool claimed = acc != 0ull;
+    const unsigned ball = __ballot_sync(full, claimed);
+    if (ball) {
+      if (nc + __popc(ball) > WCAP) {
+        __syncwarp();
+        batch_warp_flush<OffT, P>(a, nxt, q3n, wbuf, nc);
+        nc = 0;
+      }
+      if (claimed) wbuf[nc + __popc(ball & lanemask_lt())] = make_int2(v, deg);
+      nc += __popc(ball);
+    }
+  }
+  __syncwarp();
+  if (nc > 0) batch_warp_flush<OffT, P>(a, nxt, q3n, wbuf, nc);
+  if (mine) atomicOr(s_alive, mine);
+}
+
 template <typename OffT, int BLOCK, int E, int CLAIM>
 __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
   using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
@@ -236,8 +358,15 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
   const OffT* basep = a.base[cur];
   const int32_t* chunk_in = a.chunk[cur];
   const int64_t ntiles = ((int64_t)r + T - 1) / T;
+  const int bu = a.allow_bu ? *(volatile int*)&ctl->bu : 0;  // chosen when the previous level closed
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  if (bu) {
+    __syncthreads();  // slot pointers staged
+    constexpr int WCAP = CLAIM / (BLOCK / 32);
+    batch_bu_level<OffT, WCAP>(a, F, Fn, *(volatile unsigned long long*)&ctl->alive[cur], nxt, q3n,
+                               s_claim + warp * WCAP, s_par, &s_alive);
+  }
+  for (int64_t tile = bu ? ntiles : (int64_t)blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const OffT e0 = (OffT)(tile * T);
     const int cnt = (int)min((OffT)T, r - e0);
     __syncthreads();
@@ -378,7 +507,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
     }
   }
   __syncthreads();
-  const int nc = s_nclaim;
+  const int nc = bu ? 0 : s_nclaim;
   if (nc > 0) batch_flush<OffT, BLOCK, CLAIM>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -389,6 +518,17 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
       __threadfence();
       const unsigned long long pn = atomicAdd(&ctl->counter[nxt], 0ull);
       const long long nn = a.pk.count(pn);
+      if (a.allow_bu) {
+        // direction of the next level (Beamer's heuristic on the wave's union frontier):
+        // bottom-up while the next frontier's edges are a large share of the unexplored
+        // ones and it grows, top-down again once it is small and shrinking
+        const long long seen = ctl->seen + (long long)r;
+        const long long rn = a.pk.edges(pn);
+        const long long unexplored = a.nnz - seen;
+        ctl->seen = seen;
+        ctl->bu_levels += bu;
+        ctl->bu = bu ? !(nn * (long long)a.beta < a.n && nn < nf) : (rn * (long long)a.alpha > unexplored && nn > nf);
+      }
       ctl->prev_count = nf;
       ctl->counter[cur] = 0;
       ctl->done[cur] = 0;

@@ -572,11 +572,13 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
       return BFS_OK;
     case BFS_OPT_BOTTOM_UP:
       G->bottom_up = value != 0;
+      set_batch_shape(G, G->batch_shape);  // the captured wave loop holds the policy
       return BFS_OK;
     case BFS_OPT_ALPHA:
     case BFS_OPT_BETA:
       if (value < 1 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "alpha/beta outside [1, 2^20]");
       (option == BFS_OPT_ALPHA ? G->alpha : G->beta) = (int)value;
+      set_batch_shape(G, G->batch_shape);
       return BFS_OK;
     case BFS_OPT_WAIT_LIMIT:
       if (value < 0 || value > (1ll << 40)) return fail(BFS_ERR_INVALID_ARG, "wait limit outside [0, 2^40]");

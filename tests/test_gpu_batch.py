@@ -148,3 +148,38 @@ def test_batch_errors(torch_cuda, graphs_mod):
             assert e.value.status == 1
     finally:
         capi.bfs_graph_destroy(h)
+
+
+# (bottom-up, alpha, beta): Beamer's defaults, bottom-up from the first growing level, and
+# bottom-up while growing / top-down once shrinking
+BU_POLICIES = {"do": (1, 8, 24), "bu-eager": (1, 1 << 20, 1 << 20), "bu-flip": (1, 1 << 20, 1)}
+
+
+@pytest.mark.parametrize("policy", sorted(BU_POLICIES))
+@pytest.mark.parametrize("relabel", [False, True])
+def test_waves_with_bottom_up_levels(torch_cuda, oracle_mod, graphs_mod, policy, relabel):
+    """Waves that run some levels bottom-up (each vertex pulls the bits it misses from its
+    neighbours' frontier masks) give every root the single-source levels and valid parents."""
+    from paper_1408_1605_gb300 import capi
+
+    bu, alpha, beta = BU_POLICIES[policy]
+    gs = [graphs_mod.rmat(15, 16, seed=19), graphs_mod.grid3d(15, 13, 11), graphs_mod.uniform(12000, 48000, seed=3),
+          graphs_mod.from_edges(3000, *path_edges(3000))]
+    fx = load_golden("two_components.txt")
+    gs.append(graphs_mod.from_edges(fx["n"], fx["src"], fx["dst"]))
+    flags = capi.BFS_OFFSETS_INT64 | (capi.BFS_RELABEL_DEGREE if relabel else 0)
+    for g in gs:
+        rng = np.random.default_rng(g.n + 11)
+        h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, flags)
+        try:
+            capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, bu)
+            capi.bfs_graph_set_option(h, capi.BFS_OPT_ALPHA, alpha)
+            capi.bfs_graph_set_option(h, capi.BFS_OPT_BETA, beta)
+            roots = rng.integers(0, g.n, size=min(64, g.n))
+            roots[1] = roots[0]  # a repeated root
+            st = check_wave(capi, oracle_mod, torch_cuda, h, g, roots)
+            if g.name.startswith("rmat") and policy != "do":
+                assert st[0].bottom_up_levels > 0
+            check_wave(capi, oracle_mod, torch_cuda, h, g, roots[:5], host_out=True)
+        finally:
+            capi.bfs_graph_destroy(h)
