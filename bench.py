@@ -506,12 +506,29 @@ def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
         waves += 1
     single_agg = sum(s["edges_traversed"] for s in single_stats) / (sum(s["device_ms"] for s in single_stats) * 1e-3)
     agg = edges / (ms * 1e-3)
+    # the same waves with bottom-up levels allowed (BFS_OPT_BOTTOM_UP applies to waves too)
+    saved_bu = capi.bfs_graph_get_option(h, capi.BFS_OPT_BOTTOM_UP)
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
+    capi.bfs_run_batch(h, roots[:k], lv, pr, want_stats=True)  # warm-up (new wave loop)
+    edges_do, ms_do, bu_levels = 0, 0.0, 0
+    for i in range(0, len(roots), wave):
+        part = roots[i:i + wave]
+        st = capi.bfs_run_batch(h, part, lv[: len(part)], pr[: len(part)], want_stats=True)
+        edges_do += sum(s.edges_traversed for s in st)
+        ms_do += st[0].device_ms
+        bu_levels += st[0].bottom_up_levels
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, saved_bu)
+    agg_do = edges_do / (ms_do * 1e-3)
     del lv, pr
     torch.cuda.empty_cache()
     assert len(single_stats) == len(roots)
     return {"waves": waves, "roots_per_wave": wave, "roots": len(roots), "aggregate_gteps": round(agg / 1e9, 3),
             "single_source_aggregate_gteps": round(single_agg / 1e9, 3), "ratio": round(agg / single_agg, 3),
-            "ms_per_wave": round(ms / waves, 3)}
+            "ms_per_wave": round(ms / waves, 3),
+            "direction_optimizing": {"aggregate_gteps": round(agg_do / 1e9, 3),
+                                     "ratio_vs_single_top_down": round(agg_do / single_agg, 3),
+                                     "ms_per_wave": round(ms_do / waves, 3),
+                                     "bottom_up_levels_per_wave": round(bu_levels / waves, 2)}}
 
 
 def run_serve(args) -> int:
