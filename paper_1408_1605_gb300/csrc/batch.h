@@ -31,8 +31,10 @@ struct BatchCtl {
   unsigned long long alive[2];    // OR of the masks claimed by the running expansion (next parity)
   unsigned long long ovf_count;   // parent events that did not fit the per-vertex slots
   int bu;                         // the running level goes bottom-up (set by the previous level)
+  int bu_strict;                  // the choice if some root's next frontier is small
   int bu_levels;                  // bottom-up levels so far
   long long seen;                 // degree sum of the frontiers expanded so far
+  unsigned long long bitcnt[kMaxWave];  // per-root size of the new frontier (bottom-up choice)
 };
 
 // Parent event of a claim: vertex u's edge claimed the bits `mask` of the claimed vertex

@@ -94,6 +94,7 @@ __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_see
       c->bu = 0;
       c->bu_levels = 0;
       c->seen = 0;
+      for (int b = 0; b < kMaxWave; ++b) c->bitcnt[b] = 0ull;
     }
     const int t = c->level - 1;
     const int cur = t & 1, q3 = t % 3;
@@ -223,6 +224,8 @@ __device__ __forceinline__ void batch_warp_flush(const BatchArgs<OffT>& a, int n
   }
   __syncwarp();
 }
+
+constexpr unsigned long long kSmallFrontierDiv = 16384;
 
 // One bottom-up level of a wave (the multi-source form of Beamer's step, the paper's
 // related work, Sec. 6): every vertex v still missing some active root's bit scans its row
@@ -528,6 +531,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
         ctl->seen = seen;
         ctl->bu_levels += bu;
         ctl->bu = bu ? !(nn * (long long)a.beta < a.n && nn < nf) : (rn * (long long)a.alpha > unexplored && nn > nf);
+        ctl->bu_strict = ctl->bu && rn > unexplored;  // the rule when some root's frontier is small
       }
       ctl->prev_count = nf;
       ctl->counter[cur] = 0;
@@ -553,6 +557,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
   __shared__ int32_t* s_lvl[kMaxWave];
   __shared__ int32_t* s_par[kMaxWave];
   __shared__ int32_t s_start[kMaxWave];
+  __shared__ unsigned long long s_cnt[kMaxWave];
   BatchCtl* ctl = a.ctl;
   const int Lnext = *(volatile int*)&ctl->level;  // already advanced by the expansion
   const int L = Lnext - 1;
@@ -563,10 +568,14 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
     s_par[threadIdx.x] = a.slots->par[threadIdx.x];
     s_start[threadIdx.x] = a.slots->start[threadIdx.x];
+    s_cnt[threadIdx.x] = 0ull;
   }
   __syncthreads();
   const unsigned long long* Fn = a.fmask[q3n];
   const int lane = threadIdx.x & 31;
+  // per-root sizes of the new frontier (only needed to choose bottom-up levels): lane l
+  // counts roots l and l + 32
+  unsigned long long cnt_lo = 0ull, cnt_hi = 0ull;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool ordered = nn * 8 > a.n;  // a full pass pays only when a large share of vertices was claimed
@@ -611,6 +620,10 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     while (any) {
       const int b = __ffsll((long long)any) - 1;
       any &= any - 1;
+      if (a.allow_bu) {
+        const unsigned c = __popc(__ballot_sync(0xffffffffu, (f >> b) & 1ull));
+        if (lane == (b & 31)) (b < 32 ? cnt_lo : cnt_hi) += c;
+      }
       if ((f >> b) & 1ull) {
         s_lvl[b][vc] = L - s_start[b];
 #pragma unroll
@@ -628,12 +641,35 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
       s_par[b][e.v] = e.u;
     }
   }
+  if (a.allow_bu) {
+    if (cnt_lo) atomicAdd(&s_cnt[lane], cnt_lo);
+    if (cnt_hi) atomicAdd(&s_cnt[lane + 32], cnt_hi);
+  }
+  __syncthreads();
+  if (a.allow_bu && threadIdx.x < kMaxWave && s_cnt[threadIdx.x])
+    atomicAdd(&ctl->bitcnt[threadIdx.x], s_cnt[threadIdx.x]);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(&ctl->emit_done, 1u) == gridDim.x - 1) {
+      __threadfence();
       ctl->ovf_count = 0;
       ctl->emit_done = 0;
+      if (a.allow_bu) {
+        // A bottom-up level makes every vertex look for the bits of every active root, so a
+        // root with a small frontier (one in a small component, say) makes nearly every row
+        // be scanned to its end, which costs about the unexplored edges: with such a root
+        // (under n / kSmallFrontierDiv vertices), go bottom-up only if the frontier's edges
+        // exceed the unexplored ones. (Swept on R-MAT s22 / s24 and uniform waves: 1/16384
+        // kept the uniform and most of the R-MAT gain and removed a 3.5x loss on waves with
+        // roots in small components; 1/64 and 1/1024 gave up more.)
+        const unsigned long long m = *(volatile unsigned long long*)&ctl->alive[nxt];
+        bool small = false;
+        for (unsigned long long bits = m; bits; bits &= bits - 1)
+          small |= ctl->bitcnt[__ffsll((long long)bits) - 1] * kSmallFrontierDiv < (unsigned long long)a.n;
+        if (small) ctl->bu = ctl->bu_strict;
+        for (int b = 0; b < kMaxWave; ++b) ctl->bitcnt[b] = 0ull;
+      }
     }
   }
 }
