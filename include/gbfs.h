@@ -307,8 +307,9 @@ GBFS_API bfs_status bfs_serve_destroy(bfs_server_t srv);
 
 /* ---------------------------------------------------------------------------------------
  * Kernel shapes and tuning. Each expansion kernel is compiled for a few shapes (threads per
- * CTA, edges per thread, claim-buffer entries); the paper picks its edges-per-thread value
- * by a sweep (Sec. 3.4.1, Fig. 3), and bfs_tune does the same sweep per graph.
+ * CTA, edges per thread, claim-buffer entries, CTA or warp tiles, register budget); the
+ * paper picks its edges-per-thread value by a sweep (Sec. 3.4.1, Fig. 3), and bfs_tune does
+ * the same sweep per graph, together with the level-loop mode.
  * --------------------------------------------------------------------------------------- */
 #define BFS_KERNEL_SINGLE 0 /* single-source expansion (bfs_run, bfs_expand) */
 #define BFS_KERNEL_BATCH 1  /* multi-source expansion (bfs_run_batch, serving waves) */
