@@ -1,0 +1,61 @@
+"""Host-side pieces of bench.py (CPU only): the harmonic mean over roots, the algorithmic-byte
+model of the roofline, the relabelling choice, and the rule that the ncu traffic figure is
+reported only for the kernel source and vertex order it was captured on."""
+import re
+import types
+
+import pytest
+
+import bench
+
+
+def test_harmonic_mean():
+    assert bench.harmonic_mean([1.0, 2.0, 4.0]) == pytest.approx(3 / 1.75)
+    assert bench.harmonic_mean([5.0]) == 5.0
+    assert bench.harmonic_mean([]) == 0.0
+    assert bench.harmonic_mean([1.0, 0.0]) == 0.0  # a failed root is not averaged away
+
+
+def test_algorithmic_bytes():
+    # 2 m_c column ids of 4 B; per reached vertex: offsets pair, queue id + scan value
+    # written and read, level and parent
+    assert bench.alg_bytes_expand(100, 10, 4) == 8 * 100 + 32 * 10
+    assert bench.alg_bytes_expand(100, 10, 8) == 8 * 100 + 48 * 10
+
+
+def test_use_relabel():
+    assert bench.use_relabel("rmat", "auto") and not bench.use_relabel("rmat", "off")
+    assert not bench.use_relabel("grid3d", "auto") and bench.use_relabel("grid3d", "on")
+    assert not bench.use_relabel("uniform", "auto")
+
+
+def test_config_names_the_reference_input_order():
+    wl = types.SimpleNamespace(name="rmat-s16-ef16", description="d", kind="rmat")
+    g = types.SimpleNamespace(n=10, nnz=20)
+    ours = types.SimpleNamespace(steps=4, impl="ours", relabel="auto", gpus=1)
+    ref = types.SimpleNamespace(steps=4, impl="reference", relabel="auto", gpus=1)
+    assert bench.config_for(wl, g, ours)["vertex_order"].startswith("relabelled")
+    assert bench.config_for(wl, g, ref)["vertex_order"].startswith("as generated")
+
+
+def _traffic_file(tmp_path, h, order):
+    (tmp_path / "k_expand_traffic.md").write_text(
+        f"# x\n\nkernel_source_hash: {h}\nvertex_order: {order}\n\ntraffic_per_launch[rmat-s26-ef16]: 2.5e+09\n")
+
+
+def test_traffic_only_for_matching_source_and_order(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    h = bench.kernel_source_hash()
+    _traffic_file(tmp_path, h, "relabelled")
+    assert bench.profiled_traffic("rmat-s26-ef16", True) == 2.5e9
+    assert bench.profiled_traffic("rmat-s26-ef16", False) is None  # other vertex order
+    assert bench.profiled_traffic("rmat-s22-ef16", True) is None   # workload not profiled
+    _traffic_file(tmp_path, "0" * 16, "relabelled")
+    assert bench.profiled_traffic("rmat-s26-ef16", True) is None   # kernel changed since
+
+
+def test_committed_traffic_summary_parses():
+    text = open(bench.PROFILES + "/k_expand_traffic.md").read()
+    assert re.search(r"kernel_source_hash:\s*[0-9a-f]{16}\b", text)
+    assert re.search(r"traffic_per_launch\[rmat-s26-ef16\]:\s*[0-9.]+e\+?\d+", text)
+    assert "--clock-control none" in text
