@@ -51,11 +51,19 @@ def harmonic_mean(xs):
     return len(xs) / sum(1.0 / x for x in xs) if xs and all(x > 0 for x in xs) else 0.0
 
 
+def strip_comments(src: str) -> str:
+    """C++ source without comments and blank lines (so that comment edits keep the hash)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash() -> str:
+    """Identifies the single-source expansion code a traffic capture was taken on."""
     h = hashlib.sha256()
     for f in ("bfs_kernels.cu", "common.cuh", "kernels.h"):
-        with open(os.path.join(ROOT, "paper_1408_1605_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1408_1605_gb300", "csrc", f)) as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

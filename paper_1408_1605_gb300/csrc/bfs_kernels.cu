@@ -1,26 +1,29 @@
 // Single-source BFS kernels for sm_103a: output init, the standalone degree scan, and
-// the fused frontier-expansion kernel (Sec. 3.4, Algorithm 3, with the optimizations of
-// Sec. 3.4.1).
+// the fused frontier-expansion kernels (Sec. 3.4, Algorithm 3, with the optimizations of
+// Sec. 3.4.1), per level or all levels in one persistent launch with bottom-up levels.
 //
 // Level structure (Algorithm 2 with R = C = 1). The frontier of a level is held as
-// (v[k], cum[k], base[k]) plus a chunk index: chunk[c] = max{k : cum[k] <= c * kChunk},
-// the binary-search answer (Algorithm 3 line 2) for every kChunk-th edge, written when
-// the frontier is built. One expansion launch per level processes the level's edge space
-// [0, r) in tiles of T = BLOCK * E edges:
-//   1. tile bounds from chunk[] (the per-tile binary search, precomputed);
-//   2. stage the tile's frontier entries (cum relative to the tile, base, vertex) in
-//      shared memory;
-//   3. each warp takes 32 * E consecutive edges, lane l edges l, l + 32, ... (coalesced
-//      column reads); one shared-memory binary search for the first, then the linear walk
-//      of Sec. 3.4.1 (advance k while e >= cum[k + 1]) for the rest;
-//   4. all E column loads are issued before any is used (the interleaving of Sec. 3.4.1);
-//   5. bitmap pre-check, then atomicOr claim (Algorithm 3 lines 5-8); the winner writes
+// (v[k], cum[k], base[k]) plus a chunk index of tile descriptors: descriptor c holds
+// k = max{k : cum[k] <= c * kChunk}, the binary-search answer (Algorithm 3 line 2) for
+// every kChunk-th edge, with that entry's parent id and the column entry of edge
+// c * kChunk; it is written when the frontier is built. One expansion processes the
+// level's edge space [0, r) in tiles, of BLOCK * E edges per CTA (CTA tiles) or of 32 * E
+// edges per warp (warp tiles):
+//   1. tile bounds from the chunk index (the per-tile binary search, precomputed);
+//   2. the edge -> entry map: a warp tile inside one row takes it from its descriptor; a
+//      warp tile over at most 32 entries holds them one per lane and searches them with
+//      shuffles; a CTA tile stages its entries in shared memory, searches once, then walks
+//      (Sec. 3.4.1: advance k while e >= cum[k + 1]);
+//   3. lane l takes edges l, l + 32, ... of its warp's 32 * E (coalesced column reads), and
+//      all E column loads are issued before any is used (the interleaving of Sec. 3.4.1);
+//   4. bitmap pre-check, then atomicOr claim (Algorithm 3 lines 5-8); the winner writes
 //      level and parent (lines 15, 17) and reads the claimed vertex's degree;
-//   6. claimed vertices are appended to a shared-memory buffer with one shared atomic per
-//      warp (ballot / popc); the buffer is flushed with ONE global 64-bit atomicAdd that
-//      reserves both the queue slots and the edge range (the exclusive scan of the next
-//      frontier's degrees, Sec. 3.4, fused into the append of lines 9-14).
-// The last CTA to finish closes the level (no spin-waits anywhere).
+//   5. claimed vertices are appended to a warp (or CTA) buffer with one shared atomic or
+//      ballot per warp; the buffer is flushed with ONE global 64-bit atomicAdd that reserves
+//      both the queue slots and the edge range (the exclusive scan of the next frontier's
+//      degrees, Sec. 3.4, fused into the append of lines 9-14).
+// The last CTA to finish closes the level (no spin-waits in the per-level kernels; the
+// persistent kernel's grid barrier waits are bounded).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -54,6 +54,13 @@ def test_traffic_only_for_matching_source_and_order(tmp_path, monkeypatch):
     assert bench.profiled_traffic("rmat-s26-ef16", True) is None   # kernel changed since
 
 
+def test_source_hash_ignores_comments():
+    a = "int f() {  // one\n  return 1; /* two\n lines */\n}\n"
+    b = "int f() {\n\n  return 1;\n}\n// trailing\n"
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments("x = 1;") != bench.strip_comments("x = 2;")
+
+
 def test_committed_traffic_summary_parses():
     text = open(bench.PROFILES + "/k_expand_traffic.md").read()
     assert re.search(r"kernel_source_hash:\s*[0-9a-f]{16}\b", text)
