@@ -283,7 +283,15 @@ def main() -> int:
     args.grid_dims = wl.dims if wl.kind == "grid3d" else None
     rank, world, local_rank = dist_env()
     t = time.perf_counter()
-    g = wl.make()
+    if world > 1 or os.environ.get("GBFS_GRAPH_CACHE"):
+        # one generation per node, not per rank: ranks share the saved graph
+        import tempfile
+
+        cache = os.environ.get("GBFS_GRAPH_CACHE") or os.path.join(
+            "/dev/shm" if os.path.isdir("/dev/shm") else tempfile.gettempdir(), "gbfs_graphs")
+        g = wl.make_shared(cache)
+    else:
+        g = wl.make()
     log(f"[bench] {wl.name}: n={g.n} nnz={g.nnz} generated in {time.perf_counter() - t:.1f}s")
     pool = wl.pick_roots(g, max(64, (args.warmup + args.steps) * world))
     if pool.size == 0:

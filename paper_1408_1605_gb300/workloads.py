@@ -5,7 +5,12 @@ graph seed ^ 0x5EED. The R-MAT graphs stand in for the paper's Graph500 R-MAT in
 (Sec. 4, Table 1: scale per GPU, edge factor 16, 64 random roots per measurement)."""
 from __future__ import annotations
 
+import fcntl
+import hashlib
+import os
 from dataclasses import dataclass
+
+import numpy as np
 
 from . import graphs
 
@@ -41,6 +46,34 @@ class Workload:
 
     def pick_roots(self, g: graphs.CSRGraph, k: int):
         return graphs.pick_roots(g, k, self.root_seed)
+
+    def make_shared(self, cache_dir: str) -> graphs.CSRGraph:
+        """The graph of make(), generated once per machine: the first process to take the
+        lock generates it and saves offsets and columns under cache_dir; every process
+        (that one included) then maps the saved arrays read-only. For runs with one process
+        per GPU on one node, where every rank needs the same graph. The file names carry a
+        hash of the generator source, so a changed generator does not reuse old files."""
+        os.makedirs(cache_dir, exist_ok=True)
+        src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "graphgen.cpp")
+        with open(src, "rb") as f:
+            tag = hashlib.sha256(f.read()).hexdigest()[:12]
+        base = os.path.join(cache_dir, f"{self.name}-{self.graph_seed}-{tag}")
+        off_path, cols_path = base + ".off.npy", base + ".cols.npy"
+        with open(base + ".lock", "w") as lock:
+            fcntl.flock(lock, fcntl.LOCK_EX)  # one generator; the others wait, then map the files
+            try:
+                if not (os.path.exists(off_path) and os.path.exists(cols_path)):
+                    g = self.make()
+                    for path, arr in ((off_path, g.offsets), (cols_path, g.cols)):
+                        tmp = f"{path}.tmp{os.getpid()}.npy"
+                        np.save(tmp, arr)
+                        os.replace(tmp, path)
+                    del g
+            finally:
+                fcntl.flock(lock, fcntl.LOCK_UN)
+        off = np.load(off_path, mmap_mode="r")
+        cols = np.load(cols_path, mmap_mode="r")
+        return graphs.CSRGraph(len(off) - 1, off, cols, self.name)
 
 
 WORKLOADS = {w.name: w for w in [

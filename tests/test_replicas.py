@@ -66,3 +66,35 @@ def test_reference_arm_runs_on_rank_zero_only():
     args = types.SimpleNamespace(steps=4, warmup=1, gpus=2, impl="reference", relabel="auto")
     # rank 1 returns before touching the graph or the oracle
     assert bench.run_reference(args, wl=None, g=None, roots=np.arange(4), rank=1) == 0
+
+
+def _make_shared_worker(rank, cache_dir, out_dir):
+    from paper_1408_1605_gb300.workloads import WORKLOADS
+
+    g = WORKLOADS["rmat-s16-ef16"].make_shared(cache_dir)
+    np.save(os.path.join(out_dir, f"off{rank}.npy"), np.asarray(g.offsets))
+    np.save(os.path.join(out_dir, f"cols{rank}.npy"), np.asarray(g.cols))
+
+
+def test_ranks_share_one_generated_graph(tmp_path, graphs_mod):
+    """Ranks of a multi-GPU bench run map one saved copy of the graph (generated once, under
+    a file lock) instead of generating it each: same arrays as a fresh generation."""
+    import multiprocessing as mp
+
+    from paper_1408_1605_gb300.workloads import WORKLOADS
+
+    cache, out = tmp_path / "cache", tmp_path / "out"
+    out.mkdir()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_make_shared_worker, args=(r, str(cache), str(out))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    ref = WORKLOADS["rmat-s16-ef16"].make()
+    for r in range(2):
+        assert np.array_equal(np.load(out / f"off{r}.npy"), ref.offsets)
+        assert np.array_equal(np.load(out / f"cols{r}.npy"), ref.cols)
+    saved = sorted(p.name for p in cache.iterdir() if p.suffix == ".npy")
+    assert len(saved) == 2  # one offsets file, one columns file: a single generation
