@@ -119,13 +119,11 @@ int gg_rmat_edges(int scale, int64_t n_edges, double a, double b, double c, uint
       for (int l = 0; l < scale; ++l) {
         if ((l & 1) == 0) r = draw(s0, base + (uint64_t)(l >> 1));
         const uint64_t x = (l & 1) ? (r & 0xFFFFFFFFull) : (r >> 32);
-        uint32_t ub, vb;
-        if (x < tA) { ub = 0; vb = 0; }
-        else if (x < tAB) { ub = 0; vb = 1; }
-        else if (x < tABC) { ub = 1; vb = 0; }
-        else { ub = 1; vb = 1; }
-        u = (u << 1) | ub;
-        v = (v << 1) | vb;
+        // quadrant without branches (they mispredict at these probabilities):
+        // [0, tA) -> (0,0), [tA, tAB) -> (0,1), [tAB, tABC) -> (1,0), [tABC, 2^32) -> (1,1)
+        const uint32_t ga = x >= tA, gab = x >= tAB, gabc = x >= tABC;
+        u = (u << 1) | gab;
+        v = (v << 1) | (ga ^ gab ^ gabc);
       }
       src[i] = (int32_t)u;
       dst[i] = (int32_t)v;
@@ -208,64 +206,108 @@ int64_t gg_build_csr(int64_t n, int64_t n_edges, const int32_t* src, const int32
   if (n < 0 || n > INT32_MAX || n_edges < 0 || !offsets_out) return -1;
   if (n_edges > 0 && (!src || !dst || !cols_out)) return -1;
   nthreads = thread_count(nthreads);
+  // Both directions of every non-loop pair are first grouped by source bucket (a range of
+  // consecutive vertex ids) with per-thread counts, so that no two threads ever write the
+  // same place; then each bucket, on its own, is laid out as rows, and every row is sorted
+  // and its duplicates removed. (A per-vertex atomic cursor was 4x slower: the R-MAT hubs
+  // made every thread contend for the same counters.)
+  int bbits = 0;
+  while ((int64_t(1) << bbits) < n) ++bbits;
+  const int kBucketBits = 12;
+  const int shift = std::max(0, bbits - kBucketBits);
+  const int64_t nb = n > 0 ? ((n - 1) >> shift) + 1 : 1;  // buckets
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(nthreads, std::max<int64_t>(n_edges, 1)));
   std::atomic<int> bad{0};
-  std::vector<std::atomic<int64_t>> cursor;
-  std::vector<int32_t> tmp;
-  std::vector<int64_t> off;
+  std::vector<int64_t> cnt, bstart;
+  std::vector<int32_t> pu, pv, tmp;
   try {
-    cursor = std::vector<std::atomic<int64_t>>((size_t)n + 1);
-    off.assign((size_t)n + 1, 0);
+    cnt.assign((size_t)T * (size_t)nb, 0);
+    bstart.assign((size_t)nb + 1, 0);
   } catch (...) {
     return -2;
   }
-  parallel_for(n + 1, nthreads, [&](int64_t lo, int64_t hi) {
-    for (int64_t i = lo; i < hi; ++i) cursor[(size_t)i].store(0, std::memory_order_relaxed);
-  });
-  // 1. degree counts (before dedup)
-  parallel_for(n_edges, nthreads, [&](int64_t lo, int64_t hi) {
-    for (int64_t i = lo; i < hi; ++i) {
-      const int32_t u = src[i], v = dst[i];
-      if (u < 0 || v < 0 || u >= n || v >= n) { bad.store(1); continue; }
-      if (u == v) continue;
-      cursor[(size_t)u].fetch_add(1, std::memory_order_relaxed);
-      cursor[(size_t)v].fetch_add(1, std::memory_order_relaxed);
+  auto range = [&](int t, int64_t& lo, int64_t& hi) {
+    lo = n_edges * t / T;
+    hi = n_edges * (t + 1) / T;
+  };
+  // 1. per-thread counts per bucket
+  parallel_for(T, T, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t) {
+      int64_t lo, hi;
+      range((int)t, lo, hi);
+      int64_t* c = cnt.data() + (size_t)t * (size_t)nb;
+      for (int64_t i = lo; i < hi; ++i) {
+        const int32_t u = src[i], v = dst[i];
+        if (u < 0 || v < 0 || u >= n || v >= n) { bad.store(1); continue; }
+        if (u == v) continue;
+        ++c[u >> shift];
+        ++c[v >> shift];
+      }
     }
   });
   if (bad.load()) return -3;
-  // 2. exclusive prefix sum -> row starts
+  // 2. positions: bucket-major, thread-minor
   int64_t acc = 0;
-  for (int64_t u = 0; u < n; ++u) {
-    off[(size_t)u] = acc;
-    acc += cursor[(size_t)u].load(std::memory_order_relaxed);
+  for (int64_t b = 0; b < nb; ++b) {
+    bstart[(size_t)b] = acc;
+    for (int t = 0; t < T; ++t) {
+      int64_t& c = cnt[(size_t)t * (size_t)nb + (size_t)b];
+      const int64_t k = c;
+      c = acc;
+      acc += k;
+    }
   }
-  off[(size_t)n] = acc;
+  bstart[(size_t)nb] = acc;
   try {
+    pu.resize((size_t)acc);
+    pv.resize((size_t)acc);
     tmp.resize((size_t)acc);
   } catch (...) {
     return -2;
   }
-  parallel_for(n, nthreads, [&](int64_t lo, int64_t hi) {
-    for (int64_t u = lo; u < hi; ++u) cursor[(size_t)u].store(off[(size_t)u], std::memory_order_relaxed);
-  });
-  // 3. scatter both directions
-  parallel_for(n_edges, nthreads, [&](int64_t lo, int64_t hi) {
-    for (int64_t i = lo; i < hi; ++i) {
-      const int32_t u = src[i], v = dst[i];
-      if (u == v) continue;
-      tmp[(size_t)cursor[(size_t)u].fetch_add(1, std::memory_order_relaxed)] = v;
-      tmp[(size_t)cursor[(size_t)v].fetch_add(1, std::memory_order_relaxed)] = u;
+  // 3. scatter the pairs into their buckets (each thread into its own slots)
+  parallel_for(T, T, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t) {
+      int64_t lo, hi;
+      range((int)t, lo, hi);
+      int64_t* c = cnt.data() + (size_t)t * (size_t)nb;
+      for (int64_t i = lo; i < hi; ++i) {
+        const int32_t u = src[i], v = dst[i];
+        if (u == v) continue;
+        int64_t p = c[u >> shift]++;
+        pu[(size_t)p] = u;
+        pv[(size_t)p] = v;
+        p = c[v >> shift]++;
+        pu[(size_t)p] = v;
+        pv[(size_t)p] = u;
+      }
     }
   });
-  // 4. sort + dedup each row in place; record the new degree
-  std::vector<int64_t> newdeg((size_t)n + 1, 0);
-  parallel_chunks(n, 4096, nthreads, [&](int64_t lo, int64_t hi) {
-    for (int64_t u = lo; u < hi; ++u) {
-      int32_t* b = tmp.data() + off[(size_t)u];
-      int32_t* e = tmp.data() + off[(size_t)u + 1];
-      std::sort(b, e);
-      newdeg[(size_t)u] = std::unique(b, e) - b;
+  // 4. per bucket: rows (counting sort by source), then sort + dedup each row
+  std::vector<int64_t> off((size_t)n + 1, 0), newdeg((size_t)n + 1, 0);
+  parallel_chunks(nb, 1, nthreads, [&](int64_t b0, int64_t b1) {
+    std::vector<int64_t> cur;
+    for (int64_t b = b0; b < b1; ++b) {
+      const int64_t vlo = b << shift, vhi = std::min<int64_t>(n, (b + 1) << shift);
+      const int64_t plo = bstart[(size_t)b], phi = bstart[(size_t)b + 1];
+      cur.assign((size_t)(vhi - vlo) + 1, 0);
+      for (int64_t p = plo; p < phi; ++p) ++cur[(size_t)(pu[(size_t)p] - vlo) + 1];
+      for (int64_t k = 0; k < vhi - vlo; ++k) cur[(size_t)k + 1] += cur[(size_t)k];
+      for (int64_t u = vlo; u < vhi; ++u) off[(size_t)u] = plo + cur[(size_t)(u - vlo)];
+      for (int64_t p = plo; p < phi; ++p) tmp[(size_t)(plo + cur[(size_t)(pu[(size_t)p] - vlo)]++)] = pv[(size_t)p];
+      for (int64_t u = vlo; u < vhi; ++u) {
+        int32_t* rb = tmp.data() + off[(size_t)u];
+        int32_t* re = tmp.data() + (u + 1 < vhi ? off[(size_t)u + 1] : phi);
+        std::sort(rb, re);
+        newdeg[(size_t)u] = std::unique(rb, re) - rb;
+      }
     }
   });
+  off[(size_t)n] = acc;
+  pu.clear();
+  pu.shrink_to_fit();
+  pv.clear();
+  pv.shrink_to_fit();
   // 5. compacted offsets and copy
   acc = 0;
   for (int64_t u = 0; u < n; ++u) {
