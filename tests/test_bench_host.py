@@ -66,3 +66,22 @@ def test_committed_traffic_summary_parses():
     assert re.search(r"kernel_source_hash:\s*[0-9a-f]{16}\b", text)
     assert re.search(r"traffic_per_launch\[rmat-s26-ef16\]:\s*[0-9.]+e\+?\d+", text)
     assert "--clock-control none" in text
+
+
+def test_reference_arm_runs_on_cpu(tmp_path):
+    """The reference arm (the CPU oracle, timed) needs no GPU: one JSON line with the
+    contract's keys for a small workload."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.abspath(bench.__file__))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "rmat-s16-ef16", "--steps", "3", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=str(tmp_path))
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GTEPS" and line["value"] > 0
+    assert line["steps"] == 3 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "rmat-s16-ef16"
