@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -168,6 +169,26 @@ def alg_bytes_expand(m_c: int, n_c: int, off_bytes: int) -> int:
     return 8 * m_c + per_vertex * n_c
 
 
+def graph_cache_dir(wl):
+    """Where ranks share a generated graph: $GBFS_GRAPH_CACHE, else /dev/shm or the temp
+    directory, whichever has room for twice the graph (None if neither has)."""
+    if os.environ.get("GBFS_GRAPH_CACHE"):
+        return os.environ["GBFS_GRAPH_CACHE"]
+    import tempfile
+
+    n = 1 << wl.scale if wl.kind in ("rmat", "uniform") else math.prod(wl.dims)
+    entries = 2 * wl.edge_factor * n if wl.kind in ("rmat", "uniform") else 6 * n
+    need = 2 * (4 * entries + 8 * (n + 1))
+    for d in ("/dev/shm", tempfile.gettempdir()):
+        try:
+            st = os.statvfs(d)
+        except OSError:
+            continue
+        if st.f_bavail * st.f_frsize > need:
+            return os.path.join(d, "gbfs_graphs")
+    return None
+
+
 def replica_roots(pool, warmup: int, world: int, rank: int):
     """Each rank is an independent replica (a single search does not shard without a
     per-level exchange): the pool's first warmup x world roots warm the ranks up and the
@@ -283,14 +304,14 @@ def main() -> int:
     args.grid_dims = wl.dims if wl.kind == "grid3d" else None
     rank, world, local_rank = dist_env()
     t = time.perf_counter()
-    if world > 1 or os.environ.get("GBFS_GRAPH_CACHE"):
-        # one generation per node, not per rank: ranks share the saved graph
-        import tempfile
-
-        cache = os.environ.get("GBFS_GRAPH_CACHE") or os.path.join(
-            "/dev/shm" if os.path.isdir("/dev/shm") else tempfile.gettempdir(), "gbfs_graphs")
-        g = wl.make_shared(cache)
-    else:
+    cache = graph_cache_dir(wl) if (world > 1 or os.environ.get("GBFS_GRAPH_CACHE")) else None
+    g = None
+    if cache:  # one generation per node, not per rank: ranks share the saved graph
+        try:
+            g = wl.make_shared(cache)
+        except OSError as e:
+            log(f"[bench] shared graph cache unusable ({e}); generating in this process")
+    if g is None:
         g = wl.make()
     log(f"[bench] {wl.name}: n={g.n} nnz={g.nnz} generated in {time.perf_counter() - t:.1f}s")
     pool = wl.pick_roots(g, max(64, (args.warmup + args.steps) * world))

@@ -98,3 +98,21 @@ def test_ranks_share_one_generated_graph(tmp_path, graphs_mod):
         assert np.array_equal(np.load(out / f"cols{r}.npy"), ref.cols)
     saved = sorted(p.name for p in cache.iterdir() if p.suffix == ".npy")
     assert len(saved) == 2  # one offsets file, one columns file: a single generation
+
+
+def test_graph_cache_dir(monkeypatch):
+    """The shared graph goes where there is room for it; with no room anywhere each rank
+    generates its own copy."""
+    from paper_1408_1605_gb300.workloads import WORKLOADS
+
+    wl = WORKLOADS["rmat-s16-ef16"]
+    monkeypatch.setenv("GBFS_GRAPH_CACHE", "/some/dir")
+    assert bench.graph_cache_dir(wl) == "/some/dir"
+    monkeypatch.delenv("GBFS_GRAPH_CACHE")
+    full = types.SimpleNamespace(f_bavail=0, f_frsize=4096)
+    roomy = types.SimpleNamespace(f_bavail=1 << 30, f_frsize=4096)
+    monkeypatch.setattr(bench.os, "statvfs", lambda d: full)
+    assert bench.graph_cache_dir(wl) is None
+    monkeypatch.setattr(bench.os, "statvfs", lambda d: full if d == "/dev/shm" else roomy)
+    got = bench.graph_cache_dir(wl)
+    assert got is not None and not got.startswith("/dev/shm")
