@@ -28,6 +28,21 @@ def test_builder_matches_reference(graphs_mod, seed):
     assert np.array_equal(g.offsets, off) and np.array_equal(g.cols, cols)
 
 
+@pytest.mark.parametrize("n,threads", [(4097, 1), (4097, 7), (50001, 3), (1 << 16, 8)])
+def test_builder_many_buckets(graphs_mod, n, threads):
+    """Above 4096 vertices the builder groups rows into buckets of several vertices, the
+    last one ragged; with hub endpoints, loops and repeats the result still equals the
+    contract for any thread count."""
+    rng = np.random.default_rng(n + threads)
+    src, dst = random_edges(n, 6 * n, rng)
+    hubs = rng.integers(0, n, 5).astype(np.int32)
+    src[: 2 * n] = hubs[rng.integers(0, 5, 2 * n)]  # skewed sources
+    src[-50:], dst[-50:] = n - 1, n - 1              # loops at the last vertex
+    g = graphs_mod.from_edges(n, src, dst, threads=threads)
+    off, cols = _csr_reference(n, src, dst)
+    assert np.array_equal(g.offsets, off) and np.array_equal(g.cols, cols)
+
+
 def test_builder_rejects_out_of_range(graphs_mod):
     with pytest.raises(ValueError):
         graphs_mod.from_edges(4, np.array([0, 5], np.int32), np.array([1, 1], np.int32))
