@@ -150,14 +150,40 @@ def check(status: int) -> None:
 
 
 def ptr(a) -> int:
-    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    """Raw address of a torch tensor or numpy array (None -> NULL; an int passes through as
+    an address). The library reads and writes flat arrays, so a strided view is refused."""
     if a is None:
         return 0
     if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("gbfs: tensor arguments must be contiguous")
         return a.data_ptr()
     if hasattr(a, "ctypes"):
+        if not a.flags.c_contiguous:
+            raise ValueError("gbfs: array arguments must be C-contiguous")
         return a.ctypes.data
     return int(a)
+
+
+def _numel(a) -> int | None:
+    if hasattr(a, "numel"):
+        return int(a.numel())
+    if hasattr(a, "size") and hasattr(a, "dtype"):
+        return int(a.size)
+    return None  # a raw address: nothing to check
+
+
+def _check_int32_out(name: str, a, need: int | None = None) -> None:
+    """Outputs are int32 arrays of at least `need` entries; checked on the host so that a
+    wrong buffer is an exception here rather than an out-of-range write on the device."""
+    if a is None or isinstance(a, int):
+        return
+    dt = str(getattr(a, "dtype", ""))
+    if dt not in ("int32", "torch.int32"):
+        raise ValueError(f"gbfs: {name} must be int32, got {dt or type(a).__name__}")
+    k = _numel(a)
+    if need is not None and k is not None and k < need:
+        raise ValueError(f"gbfs: {name} holds {k} entries, the call writes {need}")
 
 
 def stream_handle(stream=None) -> int:
@@ -191,6 +217,12 @@ def bfs_graph_info(graph: int) -> tuple[int, int]:
 
 
 def bfs_run(graph: int, root: int, levels, parents, stream=None, want_stats: bool = False):
+    _check_int32_out("levels", levels)
+    _check_int32_out("parents", parents)
+    if _numel(levels) is not None or _numel(parents) is not None:
+        n = bfs_graph_info(graph)[0]
+        _check_int32_out("levels", levels, n)
+        _check_int32_out("parents", parents, n)
     st = bfs_stats()
     check(lib().bfs_run(graph, int(root), ptr(levels), ptr(parents), stream_handle(stream),
                         ctypes.byref(st) if want_stats else None))
@@ -202,6 +234,12 @@ def bfs_run_batch(graph: int, roots, levels, parents, stream=None, want_stats: b
     import numpy as np
 
     r = np.ascontiguousarray(roots, dtype=np.int32)
+    _check_int32_out("levels", levels)
+    _check_int32_out("parents", parents)
+    if 1 <= r.size <= 64 and (_numel(levels) is not None or _numel(parents) is not None):
+        need = r.size * bfs_graph_info(graph)[0]
+        _check_int32_out("levels", levels, need)
+        _check_int32_out("parents", parents, need)
     st = (bfs_stats * max(1, r.size))()
     check(lib().bfs_run_batch(graph, r.ctypes.data, int(r.size), ptr(levels), ptr(parents), stream_handle(stream),
                               st if want_stats else None))
@@ -236,6 +274,8 @@ def bfs_serve_add_graph(server: int, graph: int) -> int:
 
 
 def bfs_serve_submit(server: int, graph_id: int, root: int, levels, parents) -> int:
+    _check_int32_out("levels", levels)
+    _check_int32_out("parents", parents)
     t = ctypes.c_uint64()
     check(lib().bfs_serve_submit(server, int(graph_id), int(root), ptr(levels), ptr(parents), ctypes.byref(t)))
     return t.value

@@ -140,3 +140,19 @@ def test_autotune_cache_roundtrip(capi, monkeypatch, tmp_path):
     r3 = autotune.apply_or_tune(0, capi.BFS_KERNEL_BATCH, "rmat", 1 << 20, [1], None, None)
     assert not r3["cached"] and calls["tune"] == 2
     assert autotune.key(0, "grid", 1 << 24, "X") == "X|single|grid|s24"
+
+
+def test_binding_checks_output_buffers(capi, monkeypatch):
+    """Outputs must be contiguous int32 arrays large enough for the call: a wrong buffer
+    raises on the host, before any library call could write past it."""
+    with pytest.raises(ValueError, match="contiguous"):
+        capi.ptr(np.zeros((4, 4), np.int32)[:, 1])
+    with pytest.raises(ValueError, match="int32"):
+        capi.bfs_run(0, 0, np.zeros(10, np.int64), np.zeros(10, np.int32))
+    monkeypatch.setattr(capi, "bfs_graph_info", lambda graph: (10, 20))
+    with pytest.raises(ValueError, match="holds 9 entries"):
+        capi.bfs_run(0, 0, np.zeros(10, np.int32), np.zeros(9, np.int32))
+    with pytest.raises(ValueError, match="holds 19 entries"):
+        capi.bfs_run_batch(0, [1, 2], np.zeros((2, 10), np.int32), np.zeros(19, np.int32))
+    with pytest.raises(ValueError, match="int32"):
+        capi.bfs_serve_submit(0, 0, 0, np.zeros(10, np.float32), np.zeros(10, np.int32))
