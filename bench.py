@@ -171,7 +171,10 @@ def alg_bytes_expand(m_c: int, n_c: int, off_bytes: int) -> int:
 
 def graph_cache_dir(wl):
     """Where ranks share a generated graph: $GBFS_GRAPH_CACHE, else /dev/shm or the temp
-    directory, whichever has room for twice the graph (None if neither has)."""
+    directory, whichever has room for twice the graph (None if neither has). A graph read
+    from a file is not cached: every rank reads the file."""
+    if wl.kind == "edgelist":
+        return None
     if os.environ.get("GBFS_GRAPH_CACHE"):
         return os.environ["GBFS_GRAPH_CACHE"]
     import tempfile
@@ -239,7 +242,7 @@ def run_reference(args, wl, g, roots, rank):
         "impl": "reference", "metric": METRIC, "value": round(hm, 4), "unit": UNIT, "n_gpus": args.gpus,
         "steps": used, "steps_requested": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * sum(times) / max(used, 1), 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "i32/i64", "data": data_kind(wl),
         "config": config_for(wl, g, args),
         "cpu_baseline": {"value": round(hm, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{used} of {args.steps} requested roots (wall-clock budget {budget:.0f} s); "
@@ -252,7 +255,8 @@ def run_reference(args, wl, g, roots, rank):
 
 def use_relabel(kind: str, mode: str) -> bool:
     """Degree relabelling (BFS_RELABEL_DEGREE) pays on skewed degree distributions (R-MAT);
-    on uniform random graphs and grids it was measured slightly slower, so auto leaves them."""
+    on uniform random graphs and grids it was measured slightly slower, so auto leaves them,
+    and graphs read from files (not measured) keep their order unless asked."""
     return mode == "on" or (mode == "auto" and kind == "rmat")
 
 
@@ -261,12 +265,27 @@ def create_graph(capi, g, relabel: bool) -> int:
                                  capi.BFS_OFFSETS_INT64 | (capi.BFS_RELABEL_DEGREE if relabel else 0))
 
 
+L2_BYTES = 129e6
+
+
+def l2_note(g) -> str:
+    """How the timed searches stand to the L2 cache: the rules ask for inputs larger than
+    L2 or a flush between timed iterations; no flush is done, so say which case holds."""
+    if 4 * g.nnz > L2_BYTES:
+        return "inputs larger than L2 (the column array alone exceeds the 129 MB L2)"
+    return "inputs smaller than L2 and not flushed between roots (warm-cache figure)"
+
+
+def data_kind(wl) -> str:
+    return f"edge list file ({os.path.basename(wl.path)})" if wl.kind == "edgelist" else "synthetic"
+
+
 def config_for(wl, g, args) -> dict:
     return {"workload": wl.name, "description": wl.description, "n_vertices": g.n, "csr_entries": g.nnz,
             "offsets": "int64" if g.nnz > 2**31 - 1 else "int32", "roots": args.steps,
             "vertex_order": "as generated (the oracle's input)" if args.impl == "reference"
             else "relabelled by degree at graph creation" if use_relabel(wl.kind, args.relabel) else "as generated",
-            "l2_flush": "inputs larger than L2 (column array and per-root outputs exceed the 129 MB L2)",
+            "l2_flush": l2_note(g),
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -276,6 +295,8 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat-s26-ef16")
+    ap.add_argument("--edge-list", default="",
+                    help="run on a graph read from this text edge list file instead of --workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
@@ -300,7 +321,12 @@ def main() -> int:
 
     from paper_1408_1605_gb300.workloads import WORKLOADS
 
-    wl = WORKLOADS[args.workload]
+    if args.edge_list:
+        from paper_1408_1605_gb300.workloads import edge_list_workload
+
+        wl = edge_list_workload(args.edge_list)
+    else:
+        wl = WORKLOADS[args.workload]
     args.grid_dims = wl.dims if wl.kind == "grid3d" else None
     rank, world, local_rank = dist_env()
     t = time.perf_counter()
@@ -313,7 +339,7 @@ def main() -> int:
             log(f"[bench] shared graph cache unusable ({e}); generating in this process")
     if g is None:
         g = wl.make()
-    log(f"[bench] {wl.name}: n={g.n} nnz={g.nnz} generated in {time.perf_counter() - t:.1f}s")
+    log(f"[bench] {wl.name}: n={g.n} nnz={g.nnz} prepared in {time.perf_counter() - t:.1f}s")
     pool = wl.pick_roots(g, max(64, (args.warmup + args.steps) * world))
     if pool.size == 0:
         raise SystemExit("graph has no vertex with degree > 0")
@@ -430,7 +456,7 @@ def main() -> int:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": len(stats),
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "i32/i64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "i32/i64", "data": data_kind(wl),
             "config": dict(config_for(wl, g, args), shapes=shapes),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,

@@ -89,9 +89,118 @@ void parallel_chunks(int64_t n, int64_t chunk, int nthreads, F&& fn) {
   for (auto& th : pool) th.join();
 }
 
+// Text edge lists, the form in which public graph collections such as SNAP (the source of
+// the paper's real-world inputs, Sec. 5, Table 3) distribute their graphs: one pair "u v"
+// per line, ids non-negative decimal integers separated by blanks, tabs or a comma. Blank
+// lines and lines that start with '#' or '%' are skipped, anything after the second id
+// (a weight, a timestamp) is ignored, and a '\r' before the '\n' is accepted.
+struct ParsePiece {
+  int64_t pairs = 0;
+  int64_t max_id = -1;
+  int64_t err_pos = -1;  // byte offset of the first bad line's start
+  int err = 0;           // -3: id above INT32_MAX - 1; -5: malformed line
+};
+
+inline bool is_blank(char c) { return c == ' ' || c == '\t' || c == '\r' || c == '\v' || c == '\f'; }
+inline bool is_sep(char c) { return c == ' ' || c == '\t' || c == ','; }
+inline bool is_digit(char c) { return c >= '0' && c <= '9'; }
+
+inline int64_t next_line(const char* text, int64_t len, int64_t p) {
+  const void* nl = p < len ? std::memchr(text + p, '\n', (size_t)(len - p)) : nullptr;
+  return nl ? (const char*)nl - text + 1 : len;
+}
+
+// Parses every line that starts in [lo, hi); a line may run past hi. With src non-NULL
+// the pairs are written from index 0 of src / dst. Stops at the first bad line.
+ParsePiece parse_lines(const char* text, int64_t len, int64_t lo, int64_t hi, int32_t* src, int32_t* dst) {
+  ParsePiece r;
+  const uint64_t kMaxId = (uint64_t)INT32_MAX - 1;  // n = max id + 1 must fit in int32
+  int64_t p = lo;
+  while (p < hi) {
+    const int64_t start = p;
+    while (p < len && is_blank(text[p])) ++p;
+    if (p >= len || text[p] == '\n' || text[p] == '#' || text[p] == '%') {
+      p = next_line(text, len, p);
+      continue;
+    }
+    uint64_t id[2] = {0, 0};
+    for (int f = 0; f < 2; ++f) {
+      if (f == 1) {
+        if (p >= len || !is_sep(text[p])) { r.err = -5; r.err_pos = start; return r; }
+        while (p < len && is_sep(text[p])) ++p;
+      }
+      if (p >= len || !is_digit(text[p])) { r.err = -5; r.err_pos = start; return r; }
+      uint64_t x = 0;
+      for (; p < len && is_digit(text[p]); ++p) {
+        x = x * 10 + (uint64_t)(text[p] - '0');
+        if (x > kMaxId) { r.err = -3; r.err_pos = start; return r; }
+      }
+      id[f] = x;
+    }
+    if (p < len && text[p] != '\n' && !is_sep(text[p]) && !is_blank(text[p])) {
+      r.err = -5;
+      r.err_pos = start;
+      return r;
+    }
+    if (src) {
+      src[r.pairs] = (int32_t)id[0];
+      dst[r.pairs] = (int32_t)id[1];
+    }
+    ++r.pairs;
+    r.max_id = std::max<int64_t>(r.max_id, (int64_t)std::max(id[0], id[1]));
+    p = next_line(text, len, p);
+  }
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
+
+// Parses a text edge list (format above) held in text[0, len). Pieces of the text, split
+// at line starts, are parsed by separate threads; the pairs keep the file's order. With
+// src == NULL only counts. Otherwise writes the pairs to src / dst (capacity cap each).
+// *max_id receives the largest id (-1 if there is no pair). Returns the number of pairs;
+// -1 on bad arguments or too small a capacity; -3 if an id exceeds 2^31 - 2; -5 on a
+// malformed line. On -3 / -5, *err_pos receives the byte offset where the first bad line
+// starts.
+int64_t gg_parse_edge_list(const char* text, int64_t len, int32_t* src, int32_t* dst, int64_t cap,
+                           int64_t* max_id, int64_t* err_pos, int nthreads) {
+  if (len < 0 || (len > 0 && !text) || (src && (!dst || cap < 0))) return -1;
+  nthreads = thread_count(nthreads);
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(nthreads, len / (1 << 16) + 1));
+  std::vector<int64_t> cut((size_t)T + 1, len);
+  cut[0] = 0;
+  for (int t = 1; t < T; ++t) {
+    const int64_t s = len * t / T;
+    cut[(size_t)t] = (text[s - 1] == '\n') ? s : next_line(text, len, s);
+  }
+  for (int t = T - 1; t >= 1; --t) cut[(size_t)t] = std::min(cut[(size_t)t], cut[(size_t)t + 1]);
+  std::vector<ParsePiece> part((size_t)T);
+  parallel_for(T, T, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t)
+      part[(size_t)t] = parse_lines(text, len, cut[(size_t)t], cut[(size_t)t + 1], nullptr, nullptr);
+  });
+  int64_t total = 0, mx = -1;
+  for (const ParsePiece& q : part) {
+    if (q.err) {
+      if (err_pos) *err_pos = q.err_pos;
+      return q.err;
+    }
+    total += q.pairs;
+    mx = std::max(mx, q.max_id);
+  }
+  if (max_id) *max_id = mx;
+  if (!src) return total;
+  if (total > cap) return -1;
+  std::vector<int64_t> at((size_t)T, 0);
+  for (int t = 1; t < T; ++t) at[(size_t)t] = at[(size_t)t - 1] + part[(size_t)t - 1].pairs;
+  parallel_for(T, T, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t)
+      parse_lines(text, len, cut[(size_t)t], cut[(size_t)t + 1], src + at[(size_t)t], dst + at[(size_t)t]);
+  });
+  return total;
+}
 
 // R-MAT edge list: n_edges = edge_factor * 2^scale directed pairs (the undirected edges
 // before symmetrization). Quadrant per bit level with probabilities (a, b, c, 1-a-b-c):

@@ -11,6 +11,10 @@ itself is not available, so byte parity with it is not claimed):
     duplicates removed, symmetrized.
   * ``uniform(n, m)``: G(n, m) pairs with both endpoints uniform, same cleaning.
   * ``grid3d(X, Y, Z)``: non-periodic 6-neighbour grid, id = x + X * (y + Y * z).
+
+Graphs from files: ``load_edge_list(path)`` reads a text edge list (one "u v" pair per line,
+the form in which SNAP distributes the real-world graphs of the paper's Table 3, Sec. 5),
+optionally gzip-compressed, and builds the same cleaned symmetric CSR.
 """
 from __future__ import annotations
 
@@ -48,6 +52,9 @@ def _load():
         lib.gg_grid3d_edges.argtypes = [ctypes.c_int64] * 3 + [_P32, _P32, ctypes.c_int]
         lib.gg_build_csr.restype = ctypes.c_int64
         lib.gg_build_csr.argtypes = [ctypes.c_int64, ctypes.c_int64, _P32, _P32, _P64, _P32, ctypes.c_int]
+        lib.gg_parse_edge_list.restype = ctypes.c_int64
+        lib.gg_parse_edge_list.argtypes = [ctypes.c_void_p, ctypes.c_int64, _P32, _P32, ctypes.c_int64, _P64, _P64,
+                                           ctypes.c_int]
         lib.gg_pick_roots.restype = ctypes.c_int64
         lib.gg_pick_roots.argtypes = [ctypes.c_int64, _P64, ctypes.c_int64, ctypes.c_uint64, _P32]
         _lib = lib
@@ -56,12 +63,14 @@ def _load():
 
 @dataclass
 class CSRGraph:
-    """Symmetric CSR: ``offsets`` int64[n + 1], ``cols`` int32[nnz], rows sorted."""
+    """Symmetric CSR: ``offsets`` int64[n + 1], ``cols`` int32[nnz], rows sorted. ``ids``:
+    for a graph loaded with its ids compacted, the file id of each vertex (else None)."""
 
     n: int
     offsets: np.ndarray
     cols: np.ndarray
     name: str = ""
+    ids: np.ndarray | None = None
 
     @property
     def nnz(self) -> int:
@@ -150,6 +159,76 @@ def uniform(n: int, m: int, seed: int, threads: int = 0) -> CSRGraph:
 def grid3d(X: int, Y: int, Z: int, threads: int = 0) -> CSRGraph:
     src, dst = grid3d_edges(X, Y, Z, threads)
     return from_edges(X * Y * Z, src, dst, threads=threads, name=f"grid3d-{X}x{Y}x{Z}")
+
+
+def parse_edge_list(text, threads: int = 0):
+    """(src, dst, max_id) of a text edge list held in memory (bytes, bytearray, mmap or a
+    uint8 array): one "u v" pair per line, ids non-negative decimal integers separated by
+    blanks, tabs or a comma; blank lines and lines starting with '#' or '%' are skipped and
+    fields after the second id are ignored. Raises ValueError naming the first bad line."""
+    buf = np.frombuffer(text, dtype=np.uint8) if not isinstance(text, np.ndarray) else text
+    n_bytes = int(buf.size)
+    addr = buf.ctypes.data if n_bytes else None
+    max_id, err = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    lib = _load()
+
+    def fail(code: int):
+        if code in (-3, -5):
+            line = int(np.count_nonzero(buf[: err.value] == 10)) + 1
+            what = "vertex id above 2^31 - 2" if code == -3 else "not a pair of non-negative integer ids"
+            raise ValueError(f"edge list line {line}: {what}")
+        raise ValueError("gg_parse_edge_list: bad arguments")
+
+    m = lib.gg_parse_edge_list(addr, n_bytes, None, None, 0, ctypes.byref(max_id), ctypes.byref(err), int(threads))
+    if m < 0:
+        fail(m)
+    src = np.empty(max(m, 1), dtype=np.int32)
+    dst = np.empty(max(m, 1), dtype=np.int32)
+    got = lib.gg_parse_edge_list(addr, n_bytes, _p(src, _P32), _p(dst, _P32), int(m), ctypes.byref(max_id),
+                                 ctypes.byref(err), int(threads))
+    if got != m:
+        fail(got)
+    return src[:m], dst[:m], int(max_id.value)
+
+
+def load_edge_list(path: str, compact: bool = False, threads: int = 0, name: str = "") -> CSRGraph:
+    """The cleaned symmetric CSR of a text edge list file (``parse_edge_list``'s format;
+    ``.gz`` files are decompressed). Every pair becomes an undirected edge, as the paper
+    treats its inputs (Sec. 4); self-loops and duplicates are removed. Vertex ids are the
+    file's (n = largest id + 1; ids that never appear have degree 0) unless ``compact``,
+    which renumbers the ids that appear to 0..n-1 in ascending order and keeps the file ids
+    in ``ids``."""
+    import gzip
+    import mmap
+
+    name = name or os.path.basename(path)
+    if path.endswith(".gz"):
+        with gzip.open(path, "rb") as f:
+            src, dst, max_id = parse_edge_list(f.read(), threads)
+    else:
+        with open(path, "rb") as f:
+            if os.fstat(f.fileno()).st_size == 0:
+                src, dst, max_id = parse_edge_list(b"", threads)
+            else:
+                bad = None
+                with mmap.mmap(f.fileno(), 0, access=mmap.ACCESS_READ) as mm:
+                    buf = np.frombuffer(mm, dtype=np.uint8)
+                    try:
+                        src, dst, max_id = parse_edge_list(buf, threads)
+                    except ValueError as e:  # re-raised once the map is closed: the
+                        bad = str(e)         # traceback would keep the view alive
+                    del buf
+                if bad:
+                    raise ValueError(f"{path}: {bad}")
+    if src.size == 0:
+        raise ValueError(f"{path}: no edges")
+    if not compact:
+        return from_edges(max_id + 1, src, dst, threads=threads, name=name)
+    ids = np.unique(np.concatenate([src, dst]))
+    g = from_edges(ids.size, np.searchsorted(ids, src).astype(np.int32), np.searchsorted(ids, dst).astype(np.int32),
+                   threads=threads, name=name)
+    g.ids = ids
+    return g
 
 
 def pick_roots(g: CSRGraph, k: int, seed: int) -> np.ndarray:

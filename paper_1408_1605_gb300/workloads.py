@@ -2,7 +2,9 @@
 
 Seeds: graph seed = GRAPH_SEED_BASE + index of the workload group below; root seed =
 graph seed ^ 0x5EED. The R-MAT graphs stand in for the paper's Graph500 R-MAT inputs
-(Sec. 4, Table 1: scale per GPU, edge factor 16, 64 random roots per measurement)."""
+(Sec. 4, Table 1: scale per GPU, edge factor 16, 64 random roots per measurement).
+``edge_list_workload(path)`` wraps a graph file (e.g. one of the SNAP graphs of Table 3,
+which this package does not ship) in the same interface."""
 from __future__ import annotations
 
 import fcntl
@@ -18,13 +20,14 @@ from . import graphs
 @dataclass(frozen=True)
 class Workload:
     name: str
-    kind: str            # rmat | uniform | grid3d
+    kind: str            # rmat | uniform | grid3d | edgelist
     scale: int = 0       # rmat / uniform: n = 2^scale
     edge_factor: int = 16
     dims: tuple = ()
     group: int = 0       # seed group
     roots: int = 64
     description: str = ""
+    path: str = ""       # edgelist: the text edge list file
 
     @property
     def graph_seed(self) -> int:
@@ -42,6 +45,8 @@ class Workload:
             return graphs.uniform(n, self.edge_factor * n, seed=self.graph_seed, threads=threads)
         if self.kind == "grid3d":
             return graphs.grid3d(*self.dims, threads=threads)
+        if self.kind == "edgelist":
+            return graphs.load_edge_list(self.path, compact=True, threads=threads, name=self.name)
         raise ValueError(self.kind)
 
     def pick_roots(self, g: graphs.CSRGraph, k: int):
@@ -92,3 +97,16 @@ WORKLOADS = {w.name: w for w in [
     Workload("uniform-n8M-deg8", "uniform", 23, edge_factor=4, group=4, roots=64,
              description="uniform G(n, m), n = 2^23, mean degree 8"),
 ]}
+
+
+def edge_list_workload(path: str, roots: int = 64) -> Workload:
+    """A graph read from a text edge list file (ids compacted to 0..n-1, every pair an
+    undirected edge, loops and duplicates removed); roots are drawn like the synthetic
+    workloads' from a fixed seed."""
+    base = os.path.basename(path)
+    for ext in (".gz", ".txt", ".tsv", ".csv", ".el", ".edges"):
+        if base.endswith(ext):
+            base = base[: -len(ext)]
+    return Workload(f"edgelist-{base}", "edgelist", group=200, roots=roots, path=os.path.abspath(path),
+                    description=f"edge list file {os.path.basename(path)} (ids compacted, pairs made undirected, "
+                                "loops and duplicates removed)")

@@ -85,3 +85,33 @@ def test_reference_arm_runs_on_cpu(tmp_path):
     assert line["impl"] == "reference" and line["unit"] == "GTEPS" and line["value"] > 0
     assert line["steps"] == 3 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "rmat-s16-ef16"
+
+
+def test_reference_arm_on_an_edge_list_file(tmp_path, graphs_mod):
+    """bench.py --edge-list runs on a graph read from a text edge list (the form of the
+    paper's real-world inputs); the line names the file and says the data is not synthetic."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    import numpy as np
+
+    src, dst = graphs_mod.rmat_edges(12, 16, seed=21)
+    path = tmp_path / "toy-graph.txt"
+    np.savetxt(path, np.stack([src, dst], 1), fmt="%d", delimiter="\t", header="toy", comments="# ")
+    root = os.path.dirname(os.path.abspath(bench.__file__))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--edge-list",
+                          str(path), "--steps", "3", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=str(tmp_path))
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["config"]["workload"] == "edgelist-toy-graph" and line["data"] == "edge list file (toy-graph.txt)"
+    assert line["value"] > 0 and line["steps"] == 3
+    assert line["config"]["l2_flush"].startswith("inputs smaller than L2")
+
+
+def test_l2_note():
+    big, small = types.SimpleNamespace(nnz=2_000_000_000, n=1), types.SimpleNamespace(nnz=1000, n=10)
+    assert bench.l2_note(big).startswith("inputs larger than L2")
+    assert bench.l2_note(small).startswith("inputs smaller than L2")
