@@ -20,6 +20,8 @@ def test_exports_every_declared_symbol(capi):
     L = ctypes.CDLL(capi.library_path())
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
+    unbound = [n for n in names if not callable(getattr(capi, n, None))]
+    assert not unbound, unbound  # the binding has a function of the same name for each
 
 
 def test_version(capi):
