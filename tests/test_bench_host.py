@@ -115,3 +115,28 @@ def test_l2_note():
     big, small = types.SimpleNamespace(nnz=2_000_000_000, n=1), types.SimpleNamespace(nnz=1000, n=10)
     assert bench.l2_note(big).startswith("inputs larger than L2")
     assert bench.l2_note(small).startswith("inputs smaller than L2")
+
+
+def test_clock_summary_reads_the_timed_window():
+    """Median SM clock and the throttle reasons seen inside the timed window (samples just
+    outside it are ignored while the window has any)."""
+    cs = bench.ClockSampler(None)
+    row = lambda sm, hw="Not Active", cap="Not Active": ["t", str(sm), "2070", "900", "0x0", hw,  # noqa: E731
+                                                         "Not Active", "Not Active", cap]
+    cs.samples = [(0.5, row(900, hw="Active")), (1.0, row(2070)), (1.1, row(2040, cap="Active")),
+                  (1.2, row(2070)), (5.0, row(800))]
+    s = bench.ClockSampler.summary(cs, 1.0, 1.2)
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples_in_window"] == 3
+    cs.samples = [(9.0, row(1500)), (9.1, ["t", "[N/A]"])]  # none inside: all usable samples
+    s = cs.summary(1.0, 1.2)
+    assert s["sm_mhz"] == 1500.0 and s["samples_in_window"] == 0
+
+
+def test_load_peaks(tmp_path, monkeypatch):
+    import json
+
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_peaks()["source"] == "fallback"
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6668.2, "bf16_tflops": 1700}))
+    assert bench.load_peaks() == {"hbm_gbs": 6668.2, "source": "measured"}
