@@ -246,7 +246,7 @@ def run_reference(args, wl, g, roots, rank):
         "config": config_for(wl, g, args),
         "cpu_baseline": {"value": round(hm, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{used} of {args.steps} requested roots (wall-clock budget {budget:.0f} s); "
-                                   f"warm-up = one strided pass over the CSR ({warm_s:.1f} s)"},
+                                   f"warm-up = one strided pass over the CSR ({warm_s:.1f} s)", **host_cpu()},
         "e2e": {"value": round(hm, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -754,6 +754,22 @@ def run_multigraph(args) -> int:
     return 0 if ok else 1
 
 
+def host_cpu() -> dict:
+    """The host the oracle is timed on: CPU model (x86 'model name', else the Arm part
+    number) and the number of cores present (the oracle uses one)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        m = re.search(r"^model name\s*:\s*(.+)$", info, re.M) or re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+        model = m.group(1).strip() if m else None
+    except OSError:
+        pass
+    import platform
+
+    return {"cpu_model": model or platform.machine(), "host_cores": os.cpu_count()}
+
+
 def cpu_leg(args, g, h, roots, lv, pr):
     """Oracle timed single-threaded on a bounded sample of the timed roots; the GPU result
     for the same roots is checked against it (levels exact, parents valid)."""
@@ -798,7 +814,7 @@ def cpu_leg(args, g, h, roots, lv, pr):
         parity["closed_form_ok"] = closed_ok
         parity["ok"] = parity["ok"] and closed_ok
     cpu = {"value": round(harmonic_mean(teps), 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{used} of the {len(roots)} timed roots, full searches on the same graph"}
+           "sample": f"{used} of the {len(roots)} timed roots, full searches on the same graph", **host_cpu()}
     return parity, cpu
 
 

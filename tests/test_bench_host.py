@@ -85,6 +85,7 @@ def test_reference_arm_runs_on_cpu(tmp_path):
     assert line["impl"] == "reference" and line["unit"] == "GTEPS" and line["value"] > 0
     assert line["steps"] == 3 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "rmat-s16-ef16"
+    assert line["cpu_baseline"]["cpu_model"] and line["cpu_baseline"]["host_cores"] >= 1
 
 
 def test_reference_arm_on_an_edge_list_file(tmp_path, graphs_mod):
