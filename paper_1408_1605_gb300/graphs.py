@@ -13,8 +13,9 @@ itself is not available, so byte parity with it is not claimed):
   * ``grid3d(X, Y, Z)``: non-periodic 6-neighbour grid, id = x + X * (y + Y * z).
 
 Graphs from files: ``load_edge_list(path)`` reads a text edge list (one "u v" pair per line,
-the form in which SNAP distributes the real-world graphs of the paper's Table 3, Sec. 5),
-optionally gzip-compressed, and builds the same cleaned symmetric CSR.
+the form in which SNAP distributes the real-world graphs of the paper's Table 3, Sec. 5) or a
+MatrixMarket coordinate file, optionally gzip-compressed, and builds the same cleaned
+symmetric CSR.
 """
 from __future__ import annotations
 
@@ -161,11 +162,12 @@ def grid3d(X: int, Y: int, Z: int, threads: int = 0) -> CSRGraph:
     return from_edges(X * Y * Z, src, dst, threads=threads, name=f"grid3d-{X}x{Y}x{Z}")
 
 
-def parse_edge_list(text, threads: int = 0):
+def parse_edge_list(text, threads: int = 0, first_line: int = 1):
     """(src, dst, max_id) of a text edge list held in memory (bytes, bytearray, mmap or a
     uint8 array): one "u v" pair per line, ids non-negative decimal integers separated by
     blanks, tabs or a comma; blank lines and lines starting with '#' or '%' are skipped and
-    fields after the second id are ignored. Raises ValueError naming the first bad line."""
+    fields after the second id are ignored. Raises ValueError naming the first bad line
+    (numbered from ``first_line``)."""
     buf = np.frombuffer(text, dtype=np.uint8) if not isinstance(text, np.ndarray) else text
     n_bytes = int(buf.size)
     addr = buf.ctypes.data if n_bytes else None
@@ -174,7 +176,7 @@ def parse_edge_list(text, threads: int = 0):
 
     def fail(code: int):
         if code in (-3, -5):
-            line = int(np.count_nonzero(buf[: err.value] == 10)) + 1
+            line = int(np.count_nonzero(buf[: err.value] == 10)) + first_line
             what = "vertex id above 2^31 - 2" if code == -3 else "not a pair of non-negative integer ids"
             raise ValueError(f"edge list line {line}: {what}")
         raise ValueError("gg_parse_edge_list: bad arguments")
@@ -191,30 +193,83 @@ def parse_edge_list(text, threads: int = 0):
     return src[:m], dst[:m], int(max_id.value)
 
 
+def _line_end(buf, pos: int) -> int:
+    """Index of the first newline at or after pos (len(buf) if none)."""
+    while pos < buf.size:
+        hit = np.flatnonzero(buf[pos: pos + 4096] == 10)
+        if hit.size:
+            return pos + int(hit[0])
+        pos += 4096
+    return int(buf.size)
+
+
+def _parse_matrix_market(buf, threads: int):
+    """(src, dst, n) of a MatrixMarket coordinate file: a '%%MatrixMarket matrix coordinate
+    ...' header, '%' comment lines, a 'rows cols entries' size line, then one 1-based
+    'i j [value...]' entry per line. Rows and columns share one vertex numbering, so
+    n = max(rows, cols); values are ignored."""
+    end = _line_end(buf, 0)
+    head = bytes(buf[:end]).decode("ascii", "replace").split()
+    if len(head) < 3 or head[1].lower() != "matrix" or head[2].lower() != "coordinate":
+        raise ValueError("MatrixMarket: only 'matrix coordinate' files hold a graph")
+    pos, line_no = end + 1, 2
+    while pos < buf.size:
+        end = _line_end(buf, pos)
+        line = bytes(buf[pos:end]).strip()
+        if line and not line.startswith(b"%"):
+            break
+        pos, line_no = end + 1, line_no + 1
+    else:
+        raise ValueError("MatrixMarket: no size line")
+    try:
+        rows, cols, entries = (int(x) for x in line.split()[:3])
+    except ValueError:
+        raise ValueError(f"MatrixMarket line {line_no}: expected 'rows cols entries'") from None
+    src, dst, max_id = parse_edge_list(buf[end + 1:], threads, first_line=line_no + 1)
+    if src.size != entries:
+        raise ValueError(f"MatrixMarket: {src.size} entries, the size line says {entries}")
+    if src.size and (min(int(src.min()), int(dst.min())) < 1 or max_id > max(rows, cols)):
+        raise ValueError("MatrixMarket: an entry lies outside the 1-based matrix")
+    return src - 1, dst - 1, max(rows, cols)
+
+
+def _parse_graph_text(buf, threads: int):
+    """(src, dst, n) of a text edge list or a MatrixMarket coordinate file in buf."""
+    if bytes(buf[:14]) == b"%%MatrixMarket":
+        return _parse_matrix_market(buf, threads)
+    src, dst, max_id = parse_edge_list(buf, threads)
+    return src, dst, max_id + 1
+
+
 def load_edge_list(path: str, compact: bool = False, threads: int = 0, name: str = "") -> CSRGraph:
-    """The cleaned symmetric CSR of a text edge list file (``parse_edge_list``'s format;
-    ``.gz`` files are decompressed). Every pair becomes an undirected edge, as the paper
-    treats its inputs (Sec. 4); self-loops and duplicates are removed. Vertex ids are the
-    file's (n = largest id + 1; ids that never appear have degree 0) unless ``compact``,
-    which renumbers the ids that appear to 0..n-1 in ascending order and keeps the file ids
-    in ``ids``."""
+    """The cleaned symmetric CSR of a graph file: a text edge list (``parse_edge_list``'s
+    format, the SNAP form) or a MatrixMarket coordinate file (1-based ids, recognised by its
+    header); ``.gz`` files are decompressed. Every pair becomes an undirected edge, as the
+    paper treats its inputs (Sec. 4); self-loops and duplicates are removed. Vertex ids are
+    the file's (edge list: n = largest id + 1; MatrixMarket: ids - 1, n = the matrix order;
+    ids that never appear have degree 0) unless ``compact``, which renumbers the ids that
+    appear to 0..n-1 in ascending order and keeps the original (0-based) ids in ``ids``."""
     import gzip
     import mmap
 
     name = name or os.path.basename(path)
     if path.endswith(".gz"):
         with gzip.open(path, "rb") as f:
-            src, dst, max_id = parse_edge_list(f.read(), threads)
+            data = np.frombuffer(f.read(), dtype=np.uint8)
+        try:
+            src, dst, n = _parse_graph_text(data, threads)
+        except ValueError as e:
+            raise ValueError(f"{path}: {e}") from None
     else:
         with open(path, "rb") as f:
             if os.fstat(f.fileno()).st_size == 0:
-                src, dst, max_id = parse_edge_list(b"", threads)
+                src, dst, n = _parse_graph_text(np.zeros(0, np.uint8), threads)
             else:
                 bad = None
                 with mmap.mmap(f.fileno(), 0, access=mmap.ACCESS_READ) as mm:
                     buf = np.frombuffer(mm, dtype=np.uint8)
                     try:
-                        src, dst, max_id = parse_edge_list(buf, threads)
+                        src, dst, n = _parse_graph_text(buf, threads)
                     except ValueError as e:  # re-raised once the map is closed: the
                         bad = str(e)         # traceback would keep the view alive
                     del buf
@@ -223,7 +278,7 @@ def load_edge_list(path: str, compact: bool = False, threads: int = 0, name: str
     if src.size == 0:
         raise ValueError(f"{path}: no edges")
     if not compact:
-        return from_edges(max_id + 1, src, dst, threads=threads, name=name)
+        return from_edges(n, src, dst, threads=threads, name=name)
     ids = np.unique(np.concatenate([src, dst]))
     g = from_edges(ids.size, np.searchsorted(ids, src).astype(np.int32), np.searchsorted(ids, dst).astype(np.int32),
                    threads=threads, name=name)

@@ -104,7 +104,7 @@ def edge_list_workload(path: str, roots: int = 64) -> Workload:
     undirected edge, loops and duplicates removed); roots are drawn like the synthetic
     workloads' from a fixed seed."""
     base = os.path.basename(path)
-    for ext in (".gz", ".txt", ".tsv", ".csv", ".el", ".edges"):
+    for ext in (".gz", ".txt", ".tsv", ".csv", ".el", ".edges", ".mtx"):
         if base.endswith(ext):
             base = base[: -len(ext)]
     return Workload(f"edgelist-{base}", "edgelist", group=200, roots=roots, path=os.path.abspath(path),

@@ -110,3 +110,46 @@ def test_loaded_graph_equals_generated(graphs_mod, oracle_mod, tmp_path):
     assert np.array_equal(g.offsets, ref.offsets) and np.array_equal(g.cols, ref.cols)
     root = int(graphs_mod.pick_roots(g, 1, 5)[0])
     assert np.array_equal(oracle_mod.bfs(g.offsets, g.cols, root)[0], oracle_mod.bfs(ref.offsets, ref.cols, root)[0])
+
+
+MTX = """%%MatrixMarket matrix coordinate real symmetric
+% a 4-cycle 1-2-3-4-1 plus a pendant vertex 6 on 4; vertex 5 is isolated
+%
+6 6 6
+2 1 1.5
+3 2 -2e3
+4 3 7
+4 1 0.25
+6 4 1
+4 4 3.0
+"""
+
+
+def test_matrix_market(graphs_mod, oracle_mod, tmp_path):
+    plain, gz = tmp_path / "g.mtx", tmp_path / "g.mtx.gz"
+    plain.write_text(MTX)
+    with gzip.open(gz, "wt") as f:
+        f.write(MTX)
+    for path in (plain, gz):
+        g = graphs_mod.load_edge_list(str(path))
+        assert g.n == 6 and g.nnz == 10  # the diagonal entry (4, 4) is a loop: removed
+        assert g.degrees().tolist() == [2, 2, 2, 3, 0, 1]
+        lv, _ = oracle_mod.bfs(g.offsets, g.cols, 0)
+        assert lv.tolist() == [0, 1, 2, 1, -1, 2]
+        c = graphs_mod.load_edge_list(str(path), compact=True)
+        assert c.n == 5 and c.ids.tolist() == [0, 1, 2, 3, 5]
+
+
+@pytest.mark.parametrize("text,match", [
+    ("%%MatrixMarket matrix array real general\n2 2\n1\n2\n3\n4\n", "only 'matrix coordinate'"),
+    ("%%MatrixMarket matrix coordinate pattern general\n% c\n", "no size line"),
+    ("%%MatrixMarket matrix coordinate pattern general\n% c\n3 3\n1 2\n", "line 3: expected"),
+    ("%%MatrixMarket matrix coordinate pattern general\n3 3 2\n1 2\n", "1 entries, the size line says 2"),
+    ("%%MatrixMarket matrix coordinate pattern general\n3 3 2\n1 2\n0 3\n", "outside"),
+    ("%%MatrixMarket matrix coordinate pattern general\n3 3 2\n1 2\n2 4\n", "outside"),
+    ("%%MatrixMarket matrix coordinate pattern general\n%\n3 3 2\n1 2\n2 x\n", "line 5: not a pair")])
+def test_matrix_market_errors(graphs_mod, tmp_path, text, match):
+    path = tmp_path / "bad.mtx"
+    path.write_text(text)
+    with pytest.raises(ValueError, match=match):
+        graphs_mod.load_edge_list(str(path))
