@@ -45,7 +45,9 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        # GBFS_ORACLE_LIB: a separately compiled oracle library, used by the test that plants
+        # mistakes in copies of the oracle source to show that the pins catch them
+        lib = ctypes.CDLL(os.environ.get("GBFS_ORACLE_LIB") or build())
         lib.oracle_bfs.restype = ctypes.c_int64
         lib.oracle_bfs.argtypes = [ctypes.c_int64, _P64, _P32, ctypes.c_int32, _P32, _P32]
         lib.oracle_component_edges.restype = ctypes.c_int64
@@ -82,6 +84,8 @@ def bfs(offsets, cols, root: int):
     r = _load().oracle_bfs(n, _p(off, _P64), _p(col, _P32), int(root), _p(level, _P32), _p(pred, _P32))
     if r < 0:
         raise ValueError("oracle_bfs: bad arguments")
+    if r != int(np.count_nonzero(level >= 0)):  # the returned count is the reached set's size
+        raise RuntimeError("oracle_bfs: reached count disagrees with the levels")
     return level, pred
 
 

@@ -226,3 +226,16 @@ def test_expand_level_hand_example(oracle_mod, graphs_mod):
     nxt = oracle_mod.expand_level(g.offsets, g.cols, front, 2, bitmap, level, pred)
     assert sorted(nxt.tolist()) == [3, 6]
     assert level[3] == 2 and level[6] == 2 and pred[3] == 1 and pred[6] == 2
+
+
+def test_checker_edges_exact_bounds(oracle_mod, graphs_mod):
+    """The edge check's two conditions on their own: a level gap of exactly 2 across an
+    edge, and an edge from the root to a vertex marked unreached (gap 1, so only the
+    reached-or-neither condition can catch it); valid levels, including an unreached
+    component, pass."""
+    g = graphs_mod.from_edges(5, np.array([0, 1, 3], np.int32), np.array([1, 2, 4], np.int32))
+    ok = np.array([0, 1, 2, -1, -1], np.int32)
+    assert oracle_mod.check_edges(g.offsets, g.cols, ok) == (0, -1)
+    assert oracle_mod.check_edges(g.offsets, g.cols, np.array([0, 1, 3, -1, -1], np.int32))[0] == 6
+    assert oracle_mod.check_edges(g.offsets, g.cols, np.array([0, -1, -1, -1, -1], np.int32)) == (6, 0)
+    assert oracle_mod.check_edges(g.offsets, g.cols, np.array([0, 1, 2, 5, -1], np.int32))[0] == 6
