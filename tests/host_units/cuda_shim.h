@@ -1,6 +1,7 @@
 // Declarations that let the library's device helper headers compile as plain host C++ for
-// the CPU unit tests of their scalar functions. Only declared, never defined: a test that
-// called a warp-collective helper would fail to link rather than run a fake.
+// the CPU unit tests of their scalar functions. Only declared, never defined: a scalar test
+// that reached a warp-collective helper would fail to link. (The warp- and block-collective
+// helpers are tested on the SIMT emulator of simt_emu.h instead.)
 #pragma once
 struct gbfs_host_dim3 {
   unsigned x, y, z;

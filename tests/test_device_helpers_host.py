@@ -1,7 +1,10 @@
-"""The scalar device helpers of the CUDA library (the thread -> edge binary search of
-Algorithm 3 line 2, the chunk-index / tile-descriptor writers, the packed append counter)
-compiled as plain host C++ and checked against the C++ standard library on random and
-adversarial degree sequences (CPU only; see tests/host_units/device_helpers.cpp)."""
+"""Device helpers of the CUDA library compiled as plain host C++ (CPU only):
+  * the scalar ones (the thread -> edge binary search of Algorithm 3 line 2, the chunk-index
+    and tile-descriptor writers, the packed append counter) against the C++ standard
+    library on random and adversarial degree sequences (tests/host_units/device_helpers.cpp);
+  * the warp- and block-collective ones (warp and block scans, the warp-cooperative
+    descriptor writers for hub rows) on a small SIMT emulator, one OS thread per GPU thread,
+    against the standard library and the scalar writers (tests/host_units/warp_helpers.cpp)."""
 import os
 import shutil
 import subprocess
@@ -12,15 +15,16 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
 
 
-def test_device_helpers_on_host(tmp_path):
+@pytest.mark.parametrize("unit,prelude", [("device_helpers", "cuda_shim.h"), ("warp_helpers", "simt_emu.h")])
+def test_device_helpers_on_host(tmp_path, unit, prelude):
     cxx = shutil.which("g++")
     if not cxx or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
         pytest.skip("needs g++ and the CUDA headers")
-    exe = tmp_path / "device_helpers"
+    exe = tmp_path / unit
     units = os.path.join(ROOT, "tests", "host_units")
-    subprocess.run([cxx, "-std=c++17", "-O1", "-x", "c++", "-I", CUDA_INC,
+    subprocess.run([cxx, "-std=c++17", "-O1", "-pthread", "-x", "c++", "-I", CUDA_INC,
                     "-I", os.path.join(ROOT, "paper_1408_1605_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
-                    "-include", os.path.join(units, "cuda_shim.h"), os.path.join(units, "device_helpers.cpp"),
+                    "-include", os.path.join(units, prelude), os.path.join(units, unit + ".cpp"),
                     "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout[-2000:]
