@@ -358,6 +358,13 @@ def bfs_tune(graph: int, kind: int, roots, levels, parents, stream=None):
     import numpy as np
 
     r = np.ascontiguousarray(roots, dtype=np.int32)
+    _check_int32_out("levels", levels)
+    _check_int32_out("parents", parents)
+    single = kind == BFS_KERNEL_SINGLE
+    if (single or 1 <= r.size <= 64) and (_numel(levels) is not None or _numel(parents) is not None):
+        need = bfs_graph_info(graph)[0] * (1 if single else r.size)
+        _check_int32_out("levels", levels, need)
+        _check_int32_out("parents", parents, need)
     n = bfs_shape_count(kind) * (3 if kind == BFS_KERNEL_SINGLE else 1)
     ms = (ctypes.c_double * max(n, 1))()
     best = ctypes.c_int(-1)

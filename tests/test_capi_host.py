@@ -158,3 +158,7 @@ def test_binding_checks_output_buffers(capi, monkeypatch):
         capi.bfs_run_batch(0, [1, 2], np.zeros((2, 10), np.int32), np.zeros(19, np.int32))
     with pytest.raises(ValueError, match="int32"):
         capi.bfs_serve_submit(0, 0, 0, np.zeros(10, np.float32), np.zeros(10, np.int32))
+    with pytest.raises(ValueError, match="holds 9 entries"):
+        capi.bfs_tune(0, capi.BFS_KERNEL_SINGLE, [1], np.zeros(9, np.int32), np.zeros(10, np.int32))
+    with pytest.raises(ValueError, match="holds 20 entries, the call writes 30"):
+        capi.bfs_tune(0, capi.BFS_KERNEL_BATCH, [1, 2, 3], np.zeros((2, 10), np.int32), np.zeros(30, np.int32))
