@@ -296,7 +296,7 @@ def main() -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat-s26-ef16")
     ap.add_argument("--edge-list", default="",
-                    help="run on a graph read from this text edge list file instead of --workload")
+                    help="run on a graph read from this file (text edge list or MatrixMarket) instead of --workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
