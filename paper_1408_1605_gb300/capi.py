@@ -174,8 +174,9 @@ def _numel(a) -> int | None:
 
 
 def _check_int32_out(name: str, a, need: int | None = None) -> None:
-    """Outputs are int32 arrays of at least `need` entries; checked on the host so that a
-    wrong buffer is an exception here rather than an out-of-range write on the device."""
+    """Arrays the library writes (or reads in full) are int32 with at least `need` entries;
+    checked on the host so that a wrong buffer is an exception here rather than an
+    out-of-range access on the device."""
     if a is None or isinstance(a, int):
         return
     dt = str(getattr(a, "dtype", ""))
@@ -254,6 +255,12 @@ def bfs_expand(graph: int, frontier, n_frontier: int, level: int, bitmap, levels
 
 def bfs_run_noalloc(row_offsets, cols, n_vertices: int, n_entries: int, root: int, levels, parents,
                     stream=None) -> None:
+    # every array is read or written in full on the device: check types and sizes here
+    _check_int32_out("row_offsets", row_offsets, int(n_vertices) + 1)
+    if int(n_entries) > 0:
+        _check_int32_out("cols", cols, int(n_entries))
+    _check_int32_out("levels", levels, int(n_vertices))
+    _check_int32_out("parents", parents, int(n_vertices))
     check(lib().bfs_run_noalloc(ptr(row_offsets), ptr(cols), int(n_vertices), int(n_entries), int(root),
                                 ptr(levels), ptr(parents), stream_handle(stream)))
 

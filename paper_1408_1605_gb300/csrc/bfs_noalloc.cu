@@ -60,6 +60,24 @@ __global__ void k_check_offsets(const int32_t* __restrict__ off, int64_t n, int6
   if (tid == 0 && (off[0] != 0 || (int64_t)off[n] != nnz)) atomicOr(bad, 1u);
 }
 
+// Device (or managed) memory, as the kernels read and write these arrays directly.
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// After a failed launch, earlier work of this call may still be running on the shared
+// array: wait for it before the lock is released (its own status is not reported).
+bfs_status settle(cudaStream_t cs, bfs_status s) {
+  cudaStreamSynchronize(cs);
+  cudaGetLastError();
+  return s;
+}
+
 // Once per device, with that device current: look up the array's device address.
 bfs_status scratch_for_device(int dev, unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(BFS_ERR_CUDA, "device ordinal beyond the supported range");
@@ -91,6 +109,8 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
     return fail(BFS_ERR_INVALID_ARG, "bfs_run_noalloc: n_entries must be in [0, " +
                                          std::to_string(kNoAllocMaxEntries) + "] (size of the static scratch)");
   if (root < 0 || root >= n_vertices) return fail(BFS_ERR_INVALID_ARG, "root outside [0, n)");
+  if (!on_device(row_offsets) || (n_entries > 0 && !on_device(cols)) || !on_device(levels) || !on_device(parents))
+    return fail(BFS_ERR_INVALID_ARG, "bfs_run_noalloc: row_offsets, cols, levels and parents must be device memory");
 
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   int dev = 0;
@@ -103,7 +123,8 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
 
   GraphDev g;
   g.device = dev;
-  cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess || g.num_sms < 1)
+    return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidValue, "cudaDeviceGetAttribute(SM count)");
   g.n = n_vertices;
   g.nnz = n_entries;
   g.off64 = false;
@@ -135,11 +156,11 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
   unsigned bad = 0;
   if ((e = cudaMemcpyAsync(&bad, check, sizeof(unsigned), cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
       (e = cudaStreamSynchronize(cs)) != cudaSuccess)
-    return cuda_fail(e, "offsets check");
+    return settle(cs, cuda_fail(e, "offsets check"));
   if (bad) return fail(BFS_ERR_INVALID_GRAPH, "row_offsets is not a well-formed CSR offsets array");
 
   launch_init_single<int32_t>(g, root, levels, parents, ws, cs);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "init kernel");
+  if ((e = cudaGetLastError()) != cudaSuccess) return settle(cs, cuda_fail(e, "init kernel"));
   ExpandArgs<int32_t> a{};
   a.off = row_offsets;
   a.cols = cols;
@@ -156,10 +177,11 @@ extern "C" GBFS_API bfs_status bfs_run_noalloc(const int32_t* row_offsets, const
   const int grid = expand_grid<int32_t>(kDefaultShape, g.num_sms);
   Ctl c{};
   for (int64_t it = 0; it <= n_vertices; ++it) {
-    if ((e = launch_expand<int32_t>(kDefaultShape, a, grid, cs)) != cudaSuccess) return cuda_fail(e, "expand kernel");
+    if ((e = launch_expand<int32_t>(kDefaultShape, a, grid, cs)) != cudaSuccess)
+      return settle(cs, cuda_fail(e, "expand kernel"));
     if ((e = cudaMemcpyAsync(&c, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
         (e = cudaStreamSynchronize(cs)) != cudaSuccess)
-      return cuda_fail(e, "level flag");
+      return settle(cs, cuda_fail(e, "level flag"));
     if (c.error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
     if (!c.cont) break;
   }

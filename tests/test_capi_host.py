@@ -162,3 +162,25 @@ def test_binding_checks_output_buffers(capi, monkeypatch):
         capi.bfs_tune(0, capi.BFS_KERNEL_SINGLE, [1], np.zeros(9, np.int32), np.zeros(10, np.int32))
     with pytest.raises(ValueError, match="holds 20 entries, the call writes 30"):
         capi.bfs_tune(0, capi.BFS_KERNEL_BATCH, [1, 2, 3], np.zeros((2, 10), np.int32), np.zeros(30, np.int32))
+
+
+def test_noalloc_checks_its_arrays(capi):
+    """bfs_run_noalloc reads and writes its four arrays directly on the device: the binding
+    refuses wrong types and sizes, and the library refuses host memory with
+    BFS_ERR_INVALID_ARG before any GPU work."""
+    off = np.array([0, 1, 2], dtype=np.int32)
+    cols = np.array([1, 0], dtype=np.int32)
+    lv = np.zeros(2, dtype=np.int32)
+    with pytest.raises(ValueError, match="row_offsets holds 2 entries"):
+        capi.bfs_run_noalloc(off[:2].copy(), cols, 2, 2, 0, lv, lv)
+    with pytest.raises(ValueError, match="row_offsets must be int32"):
+        capi.bfs_run_noalloc(off.astype(np.int64), cols, 2, 2, 0, lv, lv)
+    with pytest.raises(ValueError, match="cols holds 1 entries"):
+        capi.bfs_run_noalloc(off, cols[:1].copy(), 2, 2, 0, lv, lv)
+    with pytest.raises(ValueError, match="levels holds 1 entries"):
+        capi.bfs_run_noalloc(off, cols, 2, 2, 0, lv[:1].copy(), lv)
+    with pytest.raises(ValueError, match="parents must be int32"):
+        capi.bfs_run_noalloc(off, cols, 2, 2, 0, lv, np.zeros(2, np.int64))
+    L = capi.lib()
+    s = L.bfs_run_noalloc(capi.ptr(off), capi.ptr(cols), 2, 2, 0, capi.ptr(lv), capi.ptr(lv), None)
+    assert s == 1 and "must be device memory" in capi.bfs_last_error()
