@@ -64,6 +64,8 @@ typedef struct bfs_graph_s *bfs_graph_t;
 #define BFS_OFFSETS_INT64 0x8u /* row_offsets is int64[n_vertices + 1] */
 #define BFS_VALIDATE 0x10u     /* also check every column id and the symmetry (O(n_entries)) */
 #define BFS_RELABEL_DEGREE 0x20u /* renumber vertices internally by degree (see bfs_graph_create) */
+#define BFS_KEEP_INT64 0x40u     /* keep 64-bit row offsets on the device even when n_entries fits
+                                    in int32 (see bfs_graph_create) */
 
 /* Per-search statistics. edges_traversed is m_c, the TEPS numerator of Sec. 4: the
  * number of undirected input edges inside the traversed component, i.e. half the degree
@@ -90,6 +92,11 @@ typedef struct bfs_stats {
  *     2 x n_entries x 4 bytes during the call). It is invisible to callers: roots, levels
  *     and parents stay in the caller's numbering, and results are the same BFS (levels
  *     identical; parents valid). bfs_expand is not available on such a graph.
+ *   BFS_KEEP_INT64: the device copy keeps 64-bit row offsets, frontier scan values and
+ *     tile-descriptor column entries even when n_entries <= 2^31 - 1 (where the library
+ *     otherwise narrows them to 32 bits, which moves fewer bytes). Results are the same; the
+ *     flag exists so that the wide path, which graphs above 2^31 - 1 entries need, can be
+ *     run and checked on small graphs.
  *   Failures: BFS_ERR_INVALID_ARG (NULL / sizes / flags), BFS_ERR_INVALID_GRAPH (checks
  *   above), BFS_ERR_OOM, BFS_ERR_CUDA. The call is synchronous on `stream`. */
 GBFS_API bfs_status bfs_graph_create(const void *row_offsets, const int32_t *cols, int64_t n_vertices,
@@ -104,7 +111,8 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *     conditional WHILE node, one expansion launch per level. BFS_LOOP_PERSISTENT: one
  *     cooperative launch runs every level, separated by a grid barrier whose waits are
  *     bounded (expiry: BFS_ERR_TIMEOUT). BFS_LOOP_HOST: one launch per level and a host
- *     check of the next frontier (for profilers that cannot see graph kernel nodes).
+ *     check of the next frontier (for profilers that cannot see graph kernel nodes); with it
+ *     bfs_run_batch also drives its waves' levels from the host.
  *   BFS_OPT_BOTTOM_UP: 1 lets a persistent search run large levels bottom-up (every
  *     unvisited vertex looks for a parent in the frontier; Beamer et al., the paper's
  *     related work, Sec. 6) when frontier edges x ALPHA exceed the unexplored edges, and

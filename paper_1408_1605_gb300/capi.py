@@ -25,6 +25,7 @@ BFS_OFFSETS_INT32 = 0x4
 BFS_OFFSETS_INT64 = 0x8
 BFS_VALIDATE = 0x10
 BFS_RELABEL_DEGREE = 0x20
+BFS_KEEP_INT64 = 0x40
 BFS_OPT_LOOP = 1
 BFS_OPT_BOTTOM_UP = 2
 BFS_OPT_ALPHA = 3

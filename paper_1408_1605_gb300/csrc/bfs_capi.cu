@@ -414,7 +414,8 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
   if (n_vertices < 1 || n_vertices > INT32_MAX) return fail(BFS_ERR_INVALID_ARG, "n_vertices outside [1, 2^31-1]");
   if (n_entries < 0) return fail(BFS_ERR_INVALID_ARG, "n_entries < 0");
   const uint32_t known =
-      BFS_HOST_PTRS | BFS_DEVICE_PTRS | BFS_OFFSETS_INT32 | BFS_OFFSETS_INT64 | BFS_VALIDATE | BFS_RELABEL_DEGREE;
+      BFS_HOST_PTRS | BFS_DEVICE_PTRS | BFS_OFFSETS_INT32 | BFS_OFFSETS_INT64 | BFS_VALIDATE | BFS_RELABEL_DEGREE |
+                         BFS_KEEP_INT64;
   if (flags & ~known) return fail(BFS_ERR_INVALID_ARG, "unknown flag bits");
   if ((flags & BFS_HOST_PTRS) && (flags & BFS_DEVICE_PTRS))
     return fail(BFS_ERR_INVALID_ARG, "BFS_HOST_PTRS and BFS_DEVICE_PTRS both set");
@@ -467,8 +468,7 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
   cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, g.device);
   g.n = n;
   g.nnz = nnz;
-  const char* f64 = std::getenv("GBFS_FORCE_OFF64");  // exercise the int64 path on small graphs
-  g.off64 = nnz > INT32_MAX || (f64 && std::atoi(f64) != 0);
+  g.off64 = nnz > INT32_MAX || (flags & BFS_KEEP_INT64) != 0;
   const int count_bits = bits_for((uint64_t)n);
   g.pk.shift = 64 - count_bits;
   g.pk.mask = (g.pk.shift >= 64) ? ~0ull : ((1ull << g.pk.shift) - 1);
@@ -506,8 +506,7 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
     delete G;
     return cuda_fail(e, "graph upload");
   }
-  const char* rl = std::getenv("GBFS_RELABEL");  // overrides the flag (experiments)
-  const bool relabel = rl ? std::atoi(rl) != 0 : (flags & BFS_RELABEL_DEGREE) != 0;
+  const bool relabel = (flags & BFS_RELABEL_DEGREE) != 0;
   if (relabel && (e = relabel_by_degree(g, st)) != cudaSuccess) {
     cudaFree(g.off);
     cudaFree(g.cols);
@@ -518,24 +517,12 @@ GBFS_API bfs_status bfs_graph_create(const void* row_offsets, const int32_t* col
   // Bitmap pre-check: relabelled graphs concentrate the probes on the hub words, which L1
   // serves best; otherwise the L2-only load sees claims made during the level sooner.
   G->probe_mode = g.new_id ? 0 : 1;
-  const char* hl = std::getenv("GBFS_HOST_LOOP");
-  G->host_loop = hl && std::atoi(hl) != 0;
-  const char* lm = std::getenv("GBFS_LOOP");
-  if (lm) {
-    const std::string m(lm);
-    G->loop_mode = m == "persistent" ? BFS_LOOP_PERSISTENT : m == "host" ? BFS_LOOP_HOST : BFS_LOOP_GRAPH;
-  }
-  if (G->host_loop) G->loop_mode = BFS_LOOP_HOST;
-  G->host_loop = G->loop_mode == BFS_LOOP_HOST;
-  const char* bu = std::getenv("GBFS_BOTTOM_UP");
-  G->bottom_up = bu && std::atoi(bu) != 0;
-  const char* pm = std::getenv("GBFS_PROBE");
-  if (pm) G->probe_mode = std::atoi(pm) != 0;
-  const char* sh = std::getenv("GBFS_SHAPE");
-  G->shape = sh ? std::max(0, std::min(kNumExpandShapes - 1, std::atoi(sh))) : kDefaultShape;
+  G->loop_mode = BFS_LOOP_GRAPH;
+  G->host_loop = false;
+  G->bottom_up = 0;
+  G->shape = kDefaultShape;
   G->grid = g.off64 ? expand_grid<int64_t>(G->shape, g.num_sms) : expand_grid<int32_t>(G->shape, g.num_sms);
-  const char* bsh = std::getenv("GBFS_BATCH_SHAPE");
-  G->batch_shape = bsh ? std::max(0, std::min(kNumBatchShapes - 1, std::atoi(bsh))) : kDefaultBatchShape;
+  G->batch_shape = kDefaultBatchShape;
   *out = G;
   return BFS_OK;
 }

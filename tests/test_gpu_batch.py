@@ -1,6 +1,5 @@
 """Parity of the multi-source (batched) search with the oracle: every root's slice of a
 64-root wave has exactly the single-source levels, valid parents, and the oracle's m_c."""
-import os
 
 import numpy as np
 import pytest
@@ -22,17 +21,11 @@ def torch_cuda():
 
 
 def _upload(capi, g, force64=False, host_loop=False):
-    env = {"GBFS_FORCE_OFF64": "1" if force64 else "0", "GBFS_HOST_LOOP": "1" if host_loop else "0"}
-    old = {k: os.environ.get(k) for k in env}
-    os.environ.update(env)
-    try:
-        return capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+    h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz,
+                              capi.BFS_OFFSETS_INT64 | (capi.BFS_KEEP_INT64 if force64 else 0))
+    if host_loop:
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, capi.BFS_LOOP_HOST)
+    return h
 
 
 def check_wave(capi, oracle, torch, h, g, roots, host_out=False):

@@ -2,7 +2,6 @@
 oracle, through the C ABI. Levels must match bit for bit; parents must pass the BFS-tree
 invariants (ties between parents are decided by atomics, Sec. 3.4); the edge count m_c
 (Sec. 4) must equal the oracle's."""
-import os
 
 import numpy as np
 import pytest
@@ -25,19 +24,13 @@ def torch_cuda():
 
 
 def _upload(capi, g, force64=False, shape=None, host_loop=False):
-    env = {"GBFS_FORCE_OFF64": "1" if force64 else "0", "GBFS_HOST_LOOP": "1" if host_loop else "0"}
+    h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz,
+                              capi.BFS_OFFSETS_INT64 | (capi.BFS_KEEP_INT64 if force64 else 0))
     if shape is not None:
-        env["GBFS_SHAPE"] = str(shape)
-    old = {k: os.environ.get(k) for k in env}
-    os.environ.update(env)
-    try:
-        return capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+        capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_SINGLE, shape)
+    if host_loop:
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, capi.BFS_LOOP_HOST)
+    return h
 
 
 def check_root(capi, oracle, torch, h, g, root, host_out=False):

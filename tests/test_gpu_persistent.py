@@ -28,17 +28,8 @@ def torch_cuda():
 
 
 def _upload(capi, g, policy, force64=False):
-    import os
-
-    old = os.environ.get("GBFS_FORCE_OFF64")
-    os.environ["GBFS_FORCE_OFF64"] = "1" if force64 else "0"
-    try:
-        h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64)
-    finally:
-        if old is None:
-            os.environ.pop("GBFS_FORCE_OFF64", None)
-        else:
-            os.environ["GBFS_FORCE_OFF64"] = old
+    h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz,
+                              capi.BFS_OFFSETS_INT64 | (capi.BFS_KEEP_INT64 if force64 else 0))
     loop, bu, alpha, beta = POLICIES[policy]
     capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, loop)
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, bu)

@@ -3,7 +3,6 @@ the renumbering is invisible to callers. Every search mode returns the oracle's 
 the caller's vertex ids, valid parents and the oracle's m_c: the CUDA-graph, host and
 persistent loops, bottom-up levels, int32 and int64 offsets, host outputs, batched waves
 and the serving loop."""
-import os
 
 import numpy as np
 import pytest
@@ -32,17 +31,11 @@ def capi_mod(torch_cuda):
 
 
 def _create(capi, g, force64=False, host_loop=False):
-    env = {"GBFS_FORCE_OFF64": "1" if force64 else "0", "GBFS_HOST_LOOP": "1" if host_loop else "0"}
-    old = {k: os.environ.get(k) for k in env}
-    os.environ.update(env)
-    try:
-        return capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64 | capi.BFS_RELABEL_DEGREE)
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+    h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64 | capi.BFS_RELABEL_DEGREE
+                              | (capi.BFS_KEEP_INT64 if force64 else 0))
+    if host_loop:
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, capi.BFS_LOOP_HOST)
+    return h
 
 
 def _families(graphs_mod):
