@@ -68,21 +68,24 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, relabel: bool):
-    """Per-launch DRAM bytes of the expansion kernel from the committed ncu summary, if it
-    was taken on the current kernel source and the same vertex order (else None)."""
-    path = os.path.join(PROFILES, "k_expand_traffic.md")
-    if not os.path.exists(path):
+TRAFFIC_JSON = "traffic.json"
+
+
+def profiled_traffic(workload: str, relabel: bool, kernel: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu figures
+    (profiles/traffic.json), if they were taken on the current kernel source and the same
+    vertex order (else None: the kernel changed since the counters were read)."""
+    path = os.path.join(PROFILES, TRAFFIC_JSON)
+    try:
+        with open(path) as f:
+            db = json.load(f)
+    except (OSError, ValueError):
         return None
-    text = open(path).read()
-    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
-    if not m_hash or m_hash.group(1) != kernel_source_hash():
+    if db.get("kernel_source_hash") != kernel_source_hash():
         return None
-    m_order = re.search(r"vertex_order:\s*(\S+)", text)
-    if (m_order.group(1) if m_order else "as-generated") != ("relabelled" if relabel else "as-generated"):
-        return None
-    m = re.search(rf"traffic_per_launch\[{re.escape(workload)}\]:\s*([0-9.eE+]+)", text)
-    return float(m.group(1)) if m else None
+    order = "relabelled" if relabel else "as-generated"
+    rec = db.get("entries", {}).get(f"{workload}|{order}|{kernel}")
+    return float(rec["traffic_per_launch"]) if rec else None
 
 
 # ------------------------------------------------------------------------------------------
@@ -192,11 +195,12 @@ def graph_cache_dir(wl):
     return None
 
 
-def replica_roots(pool, warmup: int, world: int, rank: int):
+def replica_roots(pool, per_rank: int, world: int, rank: int):
     """Each rank is an independent replica (a single search does not shard without a
-    per-level exchange): the pool's first warmup x world roots warm the ranks up and the
-    rest are dealt round-robin, so the ranks' timed roots are disjoint and cover the pool."""
-    return pool[: warmup * world][rank::world], pool[warmup * world:][rank::world]
+    per-level exchange) and searches its own per_rank roots: rank r takes the r-th slice of
+    one seeded draw of per_rank x world distinct roots, so the ranks' roots are disjoint and
+    rank 0's are the configuration's roots (weak scaling: the work per rank is fixed)."""
+    return pool[rank * per_rank:(rank + 1) * per_rank]
 
 
 def aggregate_replicas(hm: float, e2e_hm: float, ms_step: float, world: int, device="cuda"):
@@ -216,7 +220,9 @@ def aggregate_replicas(hm: float, e2e_hm: float, ms_step: float, world: int, dev
 
 def run_reference(args, wl, g, roots, rank):
     """The reference arm: the CPU oracle as it stands, one thread, on the same graph and
-    roots; steps are bounded by a wall-clock budget so the run ends within minutes."""
+    roots. Each step is a bounded sample of the GPU arm's step (one search, from the next of
+    the same roots, instead of one from each), and the steps are bounded by a wall-clock
+    budget so that the run ends within minutes."""
     import oracle
 
     if rank != 0:
@@ -227,7 +233,8 @@ def run_reference(args, wl, g, roots, rank):
     teps, times, used = [], [], 0
     budget = float(os.environ.get("GBFS_REFERENCE_BUDGET_S", "150"))
     t_start = time.perf_counter()
-    for r in roots[: args.steps]:
+    for i in range(args.steps):
+        r = roots[i % len(roots)]
         t = time.perf_counter()
         lv, _ = oracle.bfs(g.offsets, g.cols, int(r))
         dt = time.perf_counter() - t
@@ -242,10 +249,11 @@ def run_reference(args, wl, g, roots, rank):
         "impl": "reference", "metric": METRIC, "value": round(hm, 4), "unit": UNIT, "n_gpus": args.gpus,
         "steps": used, "steps_requested": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * sum(times) / max(used, 1), 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "i32/i64", "data": data_kind(wl),
-        "config": config_for(wl, g, args),
+        "vs_baseline": None, "dtype": "i32", "data": data_kind(wl),
+        "config": dict(config_for(wl, g, args), step="one oracle search (a bounded sample of the GPU step)"),
         "cpu_baseline": {"value": round(hm, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{used} of {args.steps} requested roots (wall-clock budget {budget:.0f} s); "
+                         "sample": f"{used} of {args.steps} requested steps, one search each from the timed roots in order "
+                                   f"(wall-clock budget {budget:.0f} s); "
                                    f"warm-up = one strided pass over the CSR ({warm_s:.1f} s)", **host_cpu()},
         "e2e": {"value": round(hm, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -282,31 +290,75 @@ def data_kind(wl) -> str:
 
 def config_for(wl, g, args) -> dict:
     return {"workload": wl.name, "description": wl.description, "n_vertices": g.n, "csr_entries": g.nnz,
-            "offsets": "int64" if g.nnz > 2**31 - 1 else "int32", "roots": args.steps,
+            "offsets": "int64" if g.nnz > 2**31 - 1 else "int32", "roots": args.roots,
+            "step": f"one search from each of the {args.roots} roots",
             "vertex_order": "as generated (the oracle's input)" if args.impl == "reference"
             else "relabelled by degree at graph creation" if use_relabel(wl.kind, args.relabel) else "as generated",
             "l2_flush": l2_note(g),
             "parallelism": f"replicas x{args.gpus}"}
 
 
+def teps_of(s: dict) -> float:
+    return s["edges_traversed"] / (s["device_ms"] * 1e-3) / 1e9
+
+
+class DeviceSlots:
+    """Per-root output buffers [k][n] on the device, so that every result a leg produced
+    can be checked against the oracle after the timed region. With too little free device
+    memory a leg keeps no slots and its results are checked by searching again."""
+
+    def __init__(self, k: int, n: int, want: bool = True, reserve: int = 8 << 30):
+        import torch
+
+        self.lv = self.pr = None
+        if not want:
+            return
+        free, _ = torch.cuda.mem_get_info()
+        if 2 * 4 * k * n + reserve <= free:
+            self.lv = torch.empty((k, n), dtype=torch.int32, device="cuda")
+            self.pr = torch.empty((k, n), dtype=torch.int32, device="cuda")
+
+    @property
+    def kept(self) -> bool:
+        return self.lv is not None
+
+    def release(self):
+        self.lv = self.pr = None
+
+
+def single_pass(capi, h, roots, lv, pr, slots=None):
+    """One step: a search from each root (slot i receives root i's result when kept)."""
+    out = []
+    for i, r in enumerate(roots):
+        dl, dp = (slots.lv[i], slots.pr[i]) if slots is not None and slots.kept else (lv, pr)
+        out.append(capi.bfs_run(h, int(r), dl, dp, want_stats=True).as_dict())
+    return out
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=10,
+                    help="timed steps; a step is one search from each of the workload's roots (64)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat-s26-ef16")
     ap.add_argument("--edge-list", default="",
                     help="run on a graph read from this file (text edge list or MatrixMarket) instead of --workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=16)
-    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--roots", type=int, default=0, help="roots per step (default: the workload's, 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle checks of every result")
+    ap.add_argument("--parity-threads", type=int, default=0, help="threads of the oracle checks (default: cores)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batch-waves", type=int, default=0,
-                    help="64-root waves in the batched leg (default: 4 on R-MAT s22, i.e. 256 roots; else 1)")
+    ap.add_argument("--no-batched-config", action="store_true",
+                    help="skip the R-MAT scale-22 leg of 256 roots in 4 batched waves")
+    ap.add_argument("--batch-waves", type=int, default=1, help="64-root waves in the batched leg")
     ap.add_argument("--no-direction", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "serve", "multigraph"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--loop", default="", choices=["", "persistent", "graph", "host"],
+                    help="level loop of single-source searches (default: the tuner's choice)")
+    ap.add_argument("--shape", type=int, default=-1, help="single-source expansion shape (default: the tuner's)")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-levels-per-round", type=int, default=0)
@@ -318,6 +370,7 @@ def main() -> int:
     if args.mode == "multigraph":
         return run_multigraph(args)
     args.warmup = max(args.warmup, 0)
+    args.steps = max(args.steps, 1)
 
     from paper_1408_1605_gb300.workloads import WORKLOADS
 
@@ -327,6 +380,7 @@ def main() -> int:
         wl = edge_list_workload(args.edge_list)
     else:
         wl = WORKLOADS[args.workload]
+    args.roots = args.roots or wl.roots
     args.grid_dims = wl.dims if wl.kind == "grid3d" else None
     rank, world, local_rank = dist_env()
     t = time.perf_counter()
@@ -340,16 +394,16 @@ def main() -> int:
     if g is None:
         g = wl.make()
     log(f"[bench] {wl.name}: n={g.n} nnz={g.nnz} prepared in {time.perf_counter() - t:.1f}s")
-    pool = wl.pick_roots(g, max(64, (args.warmup + args.steps) * world))
-    if pool.size == 0:
-        raise SystemExit("graph has no vertex with degree > 0")
     import numpy as np
 
-    need = (args.warmup + args.steps) * world
-    pool = np.resize(pool, need) if pool.size < need else pool[:need]
+    pool = wl.pick_roots(g, args.roots * world)
+    if pool.size == 0:
+        raise SystemExit("graph has no vertex with degree > 0")
+    if pool.size < args.roots * world:  # fewer distinct roots than asked: repeat the draw
+        pool = np.resize(pool, args.roots * world)
+    roots = replica_roots(pool, args.roots, world, rank)
     if args.impl == "reference":
-        _, timed_roots = replica_roots(pool, args.warmup, world, rank)
-        return run_reference(args, wl, g, timed_roots, rank)
+        return run_reference(args, wl, g, roots, rank)
 
     import torch
 
@@ -360,7 +414,6 @@ def main() -> int:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    warm_roots, timed_roots = replica_roots(pool, args.warmup, world, rank)
 
     t = time.perf_counter()
     relabel = use_relabel(wl.kind, args.relabel)
@@ -370,18 +423,12 @@ def main() -> int:
     off_bytes = 8 if g.nnz > 2**31 - 1 else 4
     lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
     pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
-    shapes = {}
-    if not args.no_autotune:
-        from paper_1408_1605_gb300 import autotune
+    shapes = {"single": single_shape(capi, h, args, tune_class, g, roots, lv, pr)}
 
-        tune_roots = pool[: max(3, min(len(pool), 3))]
-        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, tune_class, g.n, tune_roots, lv, pr)
-        shapes["single"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"],
-                            "loop": ["persistent", "graph", "host"][rec.get("loop", 1)],
-                            "persist_ctas_per_sm": rec.get("persist_ctas", 0)}
-        log(f"[bench] single-source shape {shapes['single']} ms per shape {rec.get('ms')}")
-    for r in warm_roots:
-        capi.bfs_run(h, int(r), lv, pr, want_stats=True)
+    args.keep = rank == 0 and world == 1 and not args.no_parity  # results kept for the oracle checks
+    slots = DeviceSlots(len(roots), g.n, args.keep)
+    for _ in range(args.warmup):
+        single_pass(capi, h, roots, lv, pr)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(gpu_smi_id())
@@ -394,9 +441,8 @@ def main() -> int:
     stats = []
     w0 = time.time()
     ev0.record()
-    for r in timed_roots:
-        st = capi.bfs_run(h, int(r), lv, pr, want_stats=True)
-        stats.append(st.as_dict())
+    for _ in range(args.steps):
+        stats.extend(single_pass(capi, h, roots, lv, pr, slots))
     ev1.record()
     torch.cuda.synchronize()
     if world > 1:
@@ -407,191 +453,278 @@ def main() -> int:
     clocks = sampler.summary(w0, w1)
     elapsed_ms = ev0.elapsed_time(ev1)
 
-    teps = [s["edges_traversed"] / (s["device_ms"] * 1e-3) / 1e9 for s in stats]
-    hm = harmonic_mean(teps)
+    hm = harmonic_mean([teps_of(s) for s in stats])
+    loop = shapes["single"]["loop"]
+    kernel = "k_bfs_persistent" if loop == "persistent" else "k_expand"
     total_bytes = sum(alg_bytes_expand(s["edges_traversed"], s["vertices_reached"], off_bytes) for s in stats)
     expand_ms = sum(s["expand_ms"] for s in stats)
-    launches_expand = sum(s["depth"] for s in stats)
-    launches = sum(s["depth"] + 1 for s in stats)
+    levels_run = sum(s["depth"] for s in stats)
+    launches_kernel = len(stats) if loop == "persistent" else levels_run
+    gpu_launches = 2 * len(stats) if loop == "persistent" else levels_run + len(stats)
     achieved = total_bytes / (expand_ms * 1e-3) / 1e9
+    last = stats[-len(roots):]  # the last step: the results kept in the slots
 
     # end to end through the C ABI with host (pinned) outputs: device->host copy of the
     # levels and parents inside the timed region, the root passed in as the step's input
-    e2e_roots = timed_roots[: max(1, min(args.e2e_steps, len(timed_roots)))]
     hl = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
     hp = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
-    capi.bfs_run(h, int(e2e_roots[0]), hl, hp)
+    capi.bfs_run(h, int(roots[0]), hl, hp)
     e2e_teps = []
-    for r in e2e_roots:
+    for r in roots:
         t = time.perf_counter()
         st = capi.bfs_run(h, int(r), hl, hp, want_stats=True)
         dt = time.perf_counter() - t
         e2e_teps.append(st.edges_traversed / dt / 1e9)
     e2e_hm = harmonic_mean(e2e_teps)
+    del hl, hp
 
     direction = None
     if not args.no_direction:
-        direction = direction_leg(h, g, timed_roots, stats, wl, args, lv, pr)
+        direction = direction_leg(capi, h, g, roots, args, lv, pr)
 
     batched = None
     if not args.no_batched:
-        waves = args.batch_waves or (4 if wl.name == "rmat-s22-ef16" else 1)
-        if waves * 64 <= len(timed_roots):
-            broots, bstats = timed_roots[: waves * 64], stats[: waves * 64]
-        else:  # more roots than the timed ones: same seeded draw, single-source times taken here
-            broots = wl.pick_roots(g, waves * 64)
-            bstats = [capi.bfs_run(h, int(r), lv, pr, want_stats=True).as_dict() for r in broots]
-        batched = batched_leg(h, g, broots, bstats, None if args.no_autotune else tune_class, shapes)
+        k = min(64 * max(args.batch_waves, 1), len(roots))
+        batched = batched_leg(capi, h, g, roots[:k], last[:k], None if args.no_autotune else tune_class, shapes,
+                              args.keep)
 
     # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks
-    value, e2e_hm, ms_step = aggregate_replicas(hm, e2e_hm, elapsed_ms / max(len(stats), 1), world)
+    value, e2e_hm, ms_step = aggregate_replicas(hm, e2e_hm, elapsed_ms / args.steps, world)
 
-    parity, cpu_baseline = None, None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        parity, cpu_baseline = cpu_leg(args, g, h, timed_roots, lv, pr)
+    parity, cpu_baseline, batched_config = None, None, None
+    if rank == 0 and world == 1:
+        checks = None if args.no_parity else OracleChecks(g, args.parity_threads)
+        if not args.no_cpu_baseline:
+            cpu_baseline = cpu_baseline_leg(g, roots, checks)
+        if checks is not None:
+            parity = parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, args)
+            checks.close()
+    for leg in (direction, batched):  # release the kept outputs
+        for key in ("_slots", "_slots_do", "_options"):
+            if leg is not None:
+                leg.pop(key, None)
+    del slots
+    if rank == 0 and world == 1 and not args.no_batched_config and not args.no_batched \
+            and wl.name != "rmat-s22-ef16":
+        capi.bfs_graph_destroy(h)
+        h = None
+        torch.cuda.empty_cache()
+        batched_config = batched_config_leg(capi, args)
 
     if rank == 0:
         peaks = load_peaks()
-        traffic = profiled_traffic(wl.name, relabel)
+        traffic = profiled_traffic(wl.name, relabel, kernel)
         line = {
-            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": len(stats),
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "i32/i64", "data": data_kind(wl),
+            "vs_baseline": None, "dtype": "i32", "data": data_kind(wl),
             "config": dict(config_for(wl, g, args), shapes=shapes),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                         "kernel": "k_expand", "launches": launches_expand,
+                         "frac": round(achieved / peaks["hbm_gbs"], 4),
+                         "traffic": round(traffic) if traffic else None,
+                         "kernel": kernel, "launches": launches_kernel, "levels": levels_run,
                          "peak_source": peaks["source"],
-                         "alg_bytes_per_launch": round(total_bytes / max(launches_expand, 1))},
-            "e2e": {"value": round(e2e_hm, 3), "unit": UNIT, "h2d_bytes_per_step": 4,
-                    "d2h_bytes_per_step": 8 * g.n + 72, "steps": len(e2e_roots)},
-            "gpu_launches": launches,
+                         "alg_bytes_per_launch": round(total_bytes / max(launches_kernel, 1))},
+            "e2e": {"value": round(e2e_hm, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * len(roots),
+                    "d2h_bytes_per_step": (8 * g.n + 72) * len(roots), "searches": len(roots),
+                    "timing": "wall clock around each bfs_run call with pinned host outputs"},
+            "gpu_launches": gpu_launches,
             "clocks": clocks,
-            "detail": {"mean_device_ms": round(sum(s["device_ms"] for s in stats) / len(stats), 4),
+            "detail": {"searches_timed": len(stats),
+                       "mean_device_ms": round(sum(s["device_ms"] for s in stats) / len(stats), 4),
                        "mean_expand_ms": round(expand_ms / len(stats), 4),
-                       "mean_depth": round(launches_expand / len(stats), 2),
+                       "mean_depth": round(levels_run / len(stats), 2),
                        "mean_m_c": round(sum(s["edges_traversed"] for s in stats) / len(stats)),
-                       "min_gteps": round(min(teps), 3), "max_gteps": round(max(teps), 3)},
+                       "min_gteps": round(min(teps_of(s) for s in stats), 3),
+                       "max_gteps": round(max(teps_of(s) for s in stats), 3)},
         }
         if direction is not None:
             line["direction_optimizing"] = direction
         if batched is not None:
             line["batched"] = batched
+        if batched_config is not None:
+            line["batched_rmat_s22_4x64"] = batched_config
         if parity is not None:
             line["parity"] = parity
         if cpu_baseline is not None:
             line["cpu_baseline"] = cpu_baseline
         print(json.dumps(line), flush=True)
-    capi.bfs_graph_destroy(h)
+    if h is not None:
+        capi.bfs_graph_destroy(h)
     if world > 1:
         torch.distributed.destroy_process_group()
-    if parity is not None and not parity["ok"]:
-        return 1
-    return 0
+    ok = (parity is None or parity["ok"]) and (batched_config is None or batched_config.get("parity_ok", True))
+    return 0 if ok else 1
 
 
-def direction_leg(h, g, roots, single_stats, wl, args, lv, pr):
+def single_shape(capi, h, args, tune_class, g, roots, lv, pr) -> dict:
+    """The single-source loop mode and shape: the tuner's (cached per GPU, graph class and
+    scale), or the ones given on the command line."""
+    loops = {"persistent": capi.BFS_LOOP_PERSISTENT, "graph": capi.BFS_LOOP_GRAPH, "host": capi.BFS_LOOP_HOST}
+    names = {v: k for k, v in loops.items()}
+    if not args.no_autotune and not args.loop and args.shape < 0:
+        from paper_1408_1605_gb300 import autotune
+
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_SINGLE, tune_class, g.n, roots[:3], lv, pr)
+        out = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"],
+               "loop": names[rec.get("loop", 1)], "persist_ctas_per_sm": rec.get("persist_ctas", 0)}
+        log(f"[bench] single-source shape {out} ms per shape {rec.get('ms')}")
+        return out
+    if args.loop:
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, loops[args.loop])
+    if args.shape >= 0:
+        capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_SINGLE, args.shape)
+    shape = capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE)
+    return {"shape": shape, **capi.bfs_shape_info(capi.BFS_KERNEL_SINGLE, shape), "cached": False,
+            "loop": names[capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP)],
+            "persist_ctas_per_sm": capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS)}
+
+
+def direction_leg(capi, h, g, roots, args, lv, pr):
     """The same roots with bottom-up levels allowed (persistent loop, Beamer's switching):
-    harmonic-mean GTEPS, levels checked exact against the top-down results on sampled roots."""
-    import numpy as np
-
-    from paper_1408_1605_gb300 import capi
-
+    harmonic-mean GTEPS over the roots; each root's result is kept for the oracle checks."""
     saved = (capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP), capi.bfs_graph_get_option(h, capi.BFS_OPT_BOTTOM_UP),
              capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE),
              capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS))
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
-    shape_ms = None
     if not args.no_autotune:
-        best, shape_ms = capi.bfs_tune(h, capi.BFS_KERNEL_SINGLE, roots[:3], lv, pr)
+        capi.bfs_tune(h, capi.BFS_KERNEL_SINGLE, roots[:3], lv, pr)
     else:
         capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, capi.BFS_LOOP_PERSISTENT)
     shape = capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE)
-    for r in roots[:3]:
-        capi.bfs_run(h, int(r), lv, pr, want_stats=True)
-    st = [capi.bfs_run(h, int(r), lv, pr, want_stats=True).as_dict() for r in roots]
-    teps = [s["edges_traversed"] / (s["device_ms"] * 1e-3) / 1e9 for s in st]
-    # parity: levels identical to the top-down search on a few roots (which the oracle checks)
-    import torch
+    single_pass(capi, h, roots[:3], lv, pr)
+    slots = DeviceSlots(len(roots), g.n, args.keep)
+    st = single_pass(capi, h, roots, lv, pr, slots)
+    out = {"value": round(harmonic_mean([teps_of(s) for s in st]), 3), "unit": UNIT, "searches": len(st),
+           "shape": shape, "mean_device_ms": round(sum(s["device_ms"] for s in st) / len(st), 4),
+           "mean_bottom_up_levels": round(sum(s["bottom_up_levels"] for s in st) / len(st), 2),
+           "note": "same BFS (levels identical, parents valid); large levels run bottom-up "
+                   "(Beamer direction switching); the TEPS numerator is m_c as for the top-down search",
+           "_slots": slots,
+           "_options": (capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP), 1, shape,
+                        capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS))}
+    restore_options(capi, h, saved)
+    return out
 
-    import oracle
 
-    ok, parents_ok = True, True
-    tl = torch.empty_like(lv)
-    tp = torch.empty_like(pr)
-    for i, r in enumerate(roots[:4]):
-        capi.bfs_run(h, int(r), lv, pr)
-        capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 0)
-        capi.bfs_run(h, int(r), tl, tp)
-        capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
-        ok &= bool(torch.equal(lv, tl))
-        if i == 0:  # parents of the bottom-up search: valid BFS tree for the (oracle-checked) levels
-            ref = tl.cpu().numpy()
-            code, _ = oracle.check_tree(g.offsets, g.cols, int(r), ref, lv.cpu().numpy(), pr.cpu().numpy())
-            parents_ok = code == 0
+def restore_options(capi, h, saved):
     capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, saved[0])
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, saved[1])
     capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_SINGLE, saved[2])
     capi.bfs_graph_set_option(h, capi.BFS_OPT_PERSIST_CTAS, saved[3])
-    return {"value": round(harmonic_mean(teps), 3), "unit": UNIT, "steps": len(st), "shape": shape,
-            "mean_device_ms": round(sum(s["device_ms"] for s in st) / len(st), 4),
-            "mean_bottom_up_levels": round(sum(s["bottom_up_levels"] for s in st) / len(st), 2),
-            "levels_equal_top_down_on_roots": 4, "levels_equal": ok, "parents_valid": parents_ok,
-            "note": "same BFS (levels identical, parents valid); large levels run bottom-up (Beamer direction switching)"}
 
 
-def batched_leg(h, g, roots, single_stats, graph_class=None, shapes=None):
+def run_waves(capi, h, roots, lv, pr, wave=64):
+    """Device ms and edges of the roots run as consecutive waves of up to 64 roots; wave i
+    writes rows [64 i, 64 i + len) of lv / pr."""
+    edges, ms, bu, waves = 0, 0.0, 0, 0
+    for i in range(0, len(roots), wave):
+        part = roots[i:i + wave]
+        st = capi.bfs_run_batch(h, part, lv[i:i + len(part)], pr[i:i + len(part)], want_stats=True)
+        edges += sum(s.edges_traversed for s in st)
+        ms += st[0].device_ms
+        bu += st[0].bottom_up_levels
+        waves += 1
+    return edges, ms, bu, waves
+
+
+def batched_leg(capi, h, g, roots, single_stats, graph_class=None, shapes=None, keep=True):
     """The same roots as 64-root waves (bfs_run_batch): aggregate GTEPS of the waves against
     the aggregate of the single-source searches of exactly these roots (sum m_c / sum time
-    for both)."""
+    for both), top-down and with bottom-up levels allowed. The waves' outputs stay on the
+    device for the oracle checks (those of the bottom-up waves only if there is room for a
+    second set; else the bottom-up waves overwrite them and only theirs are checked)."""
     import torch
 
-    from paper_1408_1605_gb300 import capi
-
-    wave = 64
-    k = min(wave, len(roots))
-    lv = torch.empty((k, g.n), dtype=torch.int32, device="cuda")
-    pr = torch.empty((k, g.n), dtype=torch.int32, device="cuda")
+    k = min(64, len(roots))
+    lv = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
+    pr = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
     if graph_class is not None:
         from paper_1408_1605_gb300 import autotune
 
-        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, graph_class, g.n, roots[:k], lv, pr)
+        rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, graph_class, g.n, roots[:k], lv[:k], pr[:k])
         if shapes is not None:
             shapes["batch"] = {"shape": rec["shape"], **rec["shape_info"], "cached": rec["cached"]}
         log(f"[bench] batch shape {rec['shape']} ms per shape {rec.get('ms')}")
-    capi.bfs_run_batch(h, roots[:k], lv, pr, want_stats=True)  # warm-up (buffers, graph)
-    edges, ms, waves = 0, 0.0, 0
-    for i in range(0, len(roots), wave):
-        part = roots[i:i + wave]
-        st = capi.bfs_run_batch(h, part, lv[: len(part)], pr[: len(part)], want_stats=True)
-        edges += sum(s.edges_traversed for s in st)
-        ms += st[0].device_ms
-        waves += 1
+    capi.bfs_run_batch(h, roots[:k], lv[:k], pr[:k], want_stats=True)  # warm-up (buffers, graph)
+    edges, ms, _, waves = run_waves(capi, h, roots, lv, pr)
     single_agg = sum(s["edges_traversed"] for s in single_stats) / (sum(s["device_ms"] for s in single_stats) * 1e-3)
     agg = edges / (ms * 1e-3)
+    slots = DeviceSlots(0, 0, False)
+    slots.lv, slots.pr = lv, pr
     # the same waves with bottom-up levels allowed (BFS_OPT_BOTTOM_UP applies to waves too)
     saved_bu = capi.bfs_graph_get_option(h, capi.BFS_OPT_BOTTOM_UP)
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
-    capi.bfs_run_batch(h, roots[:k], lv, pr, want_stats=True)  # warm-up (new wave loop)
-    edges_do, ms_do, bu_levels = 0, 0.0, 0
-    for i in range(0, len(roots), wave):
-        part = roots[i:i + wave]
-        st = capi.bfs_run_batch(h, part, lv[: len(part)], pr[: len(part)], want_stats=True)
-        edges_do += sum(s.edges_traversed for s in st)
-        ms_do += st[0].device_ms
-        bu_levels += st[0].bottom_up_levels
+    slots_do = DeviceSlots(len(roots), g.n, keep)
+    if not slots_do.kept:
+        slots_do, slots = slots, None
+    capi.bfs_run_batch(h, roots[:k], slots_do.lv[:k], slots_do.pr[:k], want_stats=True)  # warm-up (new loop)
+    edges_do, ms_do, bu_levels, _ = run_waves(capi, h, roots, slots_do.lv, slots_do.pr)
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, saved_bu)
     agg_do = edges_do / (ms_do * 1e-3)
-    del lv, pr
-    torch.cuda.empty_cache()
     assert len(single_stats) == len(roots)
-    return {"waves": waves, "roots_per_wave": wave, "roots": len(roots), "aggregate_gteps": round(agg / 1e9, 3),
+    return {"waves": waves, "roots_per_wave": 64, "roots": len(roots), "aggregate_gteps": round(agg / 1e9, 3),
             "single_source_aggregate_gteps": round(single_agg / 1e9, 3), "ratio": round(agg / single_agg, 3),
             "ms_per_wave": round(ms / waves, 3),
             "direction_optimizing": {"aggregate_gteps": round(agg_do / 1e9, 3),
                                      "ratio_vs_single_top_down": round(agg_do / single_agg, 3),
                                      "ms_per_wave": round(ms_do / waves, 3),
-                                     "bottom_up_levels_per_wave": round(bu_levels / waves, 2)}}
+                                     "bottom_up_levels_per_wave": round(bu_levels / waves, 2)},
+            "_slots": slots, "_slots_do": slots_do}
+
+
+def batched_config_leg(capi, args) -> dict:
+    """The batched configuration of the benchmark: R-MAT scale 22 (edge factor 16), 256
+    seeded roots run as 4 waves of 64, against single-source searches of the same 256 roots
+    on the same GPU; every root's result of both forms is checked against the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_1408_1605_gb300.workloads import WORKLOADS
+
+    wl = WORKLOADS["rmat-s22-ef16"]
+    t = time.perf_counter()
+    g = wl.make()
+    roots = wl.pick_roots(g, 256)
+    relabel = use_relabel(wl.kind, args.relabel)
+    h = create_graph(capi, g, relabel)
+    log(f"[bench] batched configuration {wl.name}: n={g.n} nnz={g.nnz}, 256 roots ({time.perf_counter() - t:.1f}s)")
+    try:
+        lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        sub = argparse.Namespace(**vars(args))
+        tune_class = wl.kind + ("-relabel" if relabel else "")
+        single = single_shape(capi, h, sub, tune_class, g, roots, lv, pr)
+        single_pass(capi, h, roots[:8], lv, pr)
+        slots = DeviceSlots(len(roots), g.n, not args.no_parity)
+        stats = single_pass(capi, h, roots, lv, pr, slots)
+        shapes = {"single": single}
+        res = batched_leg(capi, h, g, roots, stats, None if args.no_autotune else tune_class, shapes,
+                          not args.no_parity)
+        res["shapes"] = shapes
+        res["single_source_hm_gteps"] = round(harmonic_mean([teps_of(s) for s in stats]), 3)
+        if not args.no_parity:
+            checks = OracleChecks(g, args.parity_threads)
+            checks.compute(roots)
+            for i, r in enumerate(roots):
+                checks.submit("single", i, r, *fetch(capi, h, r, slots, i, lv, pr))
+            for leg, key in (("batched", "_slots"), ("batched_bottom_up", "_slots_do")):
+                sl = res.get(key)
+                if sl is None:
+                    continue
+                for i, r in enumerate(roots):
+                    checks.submit(leg, i, r, sl.lv[i].cpu().numpy(), sl.pr[i].cpu().numpy())
+            rep = checks.report()
+            checks.close()
+            res["parity"] = rep
+            res["parity_ok"] = all(v["ok"] for v in rep.values())
+        res.pop("_slots", None)
+        res.pop("_slots_do", None)
+        del slots
+        return res
+    finally:
+        capi.bfs_graph_destroy(h)
+        torch.cuda.empty_cache()
 
 
 def run_serve(args) -> int:
@@ -770,52 +903,171 @@ def host_cpu() -> dict:
     return {"cpu_model": model or platform.machine(), "host_cores": os.cpu_count()}
 
 
-def cpu_leg(args, g, h, roots, lv, pr):
-    """Oracle timed single-threaded on a bounded sample of the timed roots; the GPU result
-    for the same roots is checked against it (levels exact, parents valid)."""
-    import numpy as np
+class OracleChecks:
+    """Every GPU result checked against the oracle, outside the timed regions. The oracle's
+    levels of each root are computed once, in threads: the oracle is a C library whose calls
+    release the GIL, so the checks use the host's cores (these are correctness runs; the CPU
+    baseline's timing comes from separate single-threaded runs). A result passes when its
+    levels equal the oracle's and its parents form a valid BFS tree for them
+    (oracle.check_tree: root, parent edges in the graph, parent one level up). Results wait
+    for a free thread in a bounded queue, so at most a few full-size arrays are held."""
 
+    def __init__(self, g, threads: int = 0):
+        import concurrent.futures as cf
+
+        self.g = g
+        self.threads = threads or min(os.cpu_count() or 1, 32)
+        self.pool = cf.ThreadPoolExecutor(self.threads)
+        self.refs = {}
+        self.futs = []
+        self.sem = threading.BoundedSemaphore(self.threads + 2)
+
+    @staticmethod
+    def compact(lv):
+        import numpy as np
+
+        top = int(lv.max()) if lv.size else 0
+        return lv.astype(np.int8) if top < 127 else lv.astype(np.int16) if top < 32767 else lv
+
+    def set_ref(self, root, lv):
+        self.refs[int(root)] = self.compact(lv)
+
+    def compute(self, roots):
+        import oracle
+
+        todo = [r for r in dict.fromkeys(int(x) for x in roots) if r not in self.refs]
+
+        def one(r):
+            lv, _ = oracle.bfs(self.g.offsets, self.g.cols, r)
+            return r, self.compact(lv)
+
+        for r, c in self.pool.map(one, todo):
+            self.refs[r] = c
+
+    def submit(self, leg: str, i: int, root, levels, parents):
+        import numpy as np
+
+        import oracle
+
+        self.sem.acquire()
+        root = int(root)
+
+        def job():
+            try:
+                ref = self.refs[root].astype(np.int32)
+                exact = bool(np.array_equal(levels, ref))
+                code, bad = oracle.check_tree(self.g.offsets, self.g.cols, root, ref, levels, parents)
+                return leg, i, root, exact, code, bad
+            finally:
+                self.sem.release()
+
+        self.futs.append(self.pool.submit(job))
+
+    def report(self) -> dict:
+        import oracle
+
+        out = {}
+        for f in self.futs:
+            leg, i, root, exact, code, bad = f.result()
+            rec = out.setdefault(leg, {"roots_checked": 0, "levels_exact": True, "parents_valid": True,
+                                       "failures": []})
+            rec["roots_checked"] += 1
+            rec["levels_exact"] &= exact
+            rec["parents_valid"] &= code == 0
+            if (not exact or code) and len(rec["failures"]) < 4:
+                rec["failures"].append({"slot": i, "root": root, "code": oracle.TREE_CODES[code], "vertex": bad})
+        self.futs = []
+        for rec in out.values():
+            rec["ok"] = rec["levels_exact"] and rec["parents_valid"]
+            if not rec["failures"]:
+                del rec["failures"]
+        return out
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+
+def fetch(capi, h, root, slots, i, lv, pr):
+    """Host copies of root i's result: from its slot, or from a new search."""
+    if slots is not None and slots.kept:
+        return slots.lv[i].cpu().numpy(), slots.pr[i].cpu().numpy()
+    capi.bfs_run(h, int(root), lv, pr)
+    return lv.cpu().numpy(), pr.cpu().numpy()
+
+
+def cpu_baseline_leg(g, roots, checks, budget_s: float = 15.0) -> dict:
+    """The oracle timed single-threaded (monotonic clock around each call) on a bounded
+    sample of the timed roots: roots in order until the budget is spent, at least one. Its
+    levels serve the checks of those roots."""
     import oracle
-    from paper_1408_1605_gb300 import capi
 
-    teps, checked, exact_all, valid_all, used = [], 0, True, True, 0
+    teps = []
     t_all = time.perf_counter()
     for r in roots:
         t = time.perf_counter()
-        ref, _ = oracle.bfs(g.offsets, g.cols, int(r))
+        lv, _ = oracle.bfs(g.offsets, g.cols, int(r))
         dt = time.perf_counter() - t
-        m_c = oracle.component_edges(g.offsets, ref)
-        teps.append(m_c / dt / 1e9)
-        used += 1
-        capi.bfs_run(h, int(r), lv, pr, want_stats=True)
-        got_l, got_p = lv.cpu().numpy(), pr.cpu().numpy()
-        exact_all &= bool(np.array_equal(got_l, ref))
-        code, _ = oracle.check_tree(g.offsets, g.cols, int(r), ref, got_l, got_p)
-        valid_all &= code == 0
-        checked += 1
-        if time.perf_counter() - t_all > args.cpu_budget_s:
+        teps.append(oracle.component_edges(g.offsets, lv) / dt / 1e9)
+        if checks is not None:
+            checks.set_ref(r, lv)
+        if time.perf_counter() - t_all > budget_s:
             break
-    parity = {"roots_checked": checked, "levels_exact": exact_all, "parents_valid": valid_all,
-              "ok": exact_all and valid_all}
+    return {"value": round(harmonic_mean(teps), 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(teps)} of the {len(roots)} timed roots, one full search each on the same graph, "
+                      "one thread", **host_cpu()}
+
+
+def parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, args) -> dict:
+    """Every timed root's result against the oracle: the top-down searches of the last timed
+    step, the direction-optimizing searches and the batched waves' slots (all kept on the
+    device), plus, on 3D grids, levels equal to the Manhattan distance on sampled roots."""
+    import numpy as np
+
+    t = time.perf_counter()
+    checks.compute(roots)
+    log(f"[bench] oracle levels of {len(roots)} roots in {time.perf_counter() - t:.1f}s "
+        f"({checks.threads} threads)")
+    for i, r in enumerate(roots):
+        checks.submit("single_source", i, r, *fetch(capi, h, r, slots, i, lv, pr))
+    if direction is not None:
+        sl = direction.get("_slots")
+        if sl is None or not sl.kept:
+            saved = (capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP),
+                     capi.bfs_graph_get_option(h, capi.BFS_OPT_BOTTOM_UP),
+                     capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE),
+                     capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS))
+            restore_options(capi, h, direction["_options"])
+        for i, r in enumerate(roots):
+            checks.submit("direction_optimizing", i, r, *fetch(capi, h, r, sl, i, lv, pr))
+        if sl is None or not sl.kept:
+            restore_options(capi, h, saved)
+    if batched is not None:
+        for leg, key in (("batched", "_slots"), ("batched_bottom_up", "_slots_do")):
+            sl = batched.get(key)
+            if sl is None:
+                continue
+            for i in range(sl.lv.shape[0]):
+                checks.submit(leg, i, roots[i], sl.lv[i].cpu().numpy(), sl.pr[i].cpu().numpy())
+    rep = checks.report()
+    log(f"[bench] parity checks done in {time.perf_counter() - t:.1f}s")
+    parity = {"legs": rep, "roots_checked": len(roots), "ok": all(v["ok"] for v in rep.values())}
     dims = getattr(args, "grid_dims", None)
     if dims:
-        # full-size closed form on more roots: level = Manhattan distance on the grid
+        # full-size closed form: level = Manhattan distance on the grid
         X, Y, Z = dims
         ids = np.arange(g.n, dtype=np.int64)
         x, y, z = ids % X, (ids // X) % Y, ids // (X * Y)
         closed_ok, n_closed = True, 0
-        for r in roots[:8]:
-            capi.bfs_run(h, int(r), lv, pr)
+        for i, r in enumerate(roots[:8]):
+            got, _ = fetch(capi, h, r, slots, i, lv, pr)
             rx, ry, rz = int(r) % X, (int(r) // X) % Y, int(r) // (X * Y)
             want = np.abs(x - rx) + np.abs(y - ry) + np.abs(z - rz)
-            closed_ok &= bool(np.array_equal(lv.cpu().numpy(), want))
+            closed_ok &= bool(np.array_equal(got, want))
             n_closed += 1
         parity["closed_form_roots"] = n_closed
         parity["closed_form_ok"] = closed_ok
         parity["ok"] = parity["ok"] and closed_ok
-    cpu = {"value": round(harmonic_mean(teps), 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{used} of the {len(roots)} timed roots, full searches on the same graph", **host_cpu()}
-    return parity, cpu
+    return parity
 
 
 if __name__ == "__main__":

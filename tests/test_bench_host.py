@@ -32,26 +32,31 @@ def test_use_relabel():
 def test_config_names_the_reference_input_order():
     wl = types.SimpleNamespace(name="rmat-s16-ef16", description="d", kind="rmat")
     g = types.SimpleNamespace(n=10, nnz=20)
-    ours = types.SimpleNamespace(steps=4, impl="ours", relabel="auto", gpus=1)
-    ref = types.SimpleNamespace(steps=4, impl="reference", relabel="auto", gpus=1)
+    ours = types.SimpleNamespace(steps=4, roots=64, impl="ours", relabel="auto", gpus=1)
+    ref = types.SimpleNamespace(steps=4, roots=64, impl="reference", relabel="auto", gpus=1)
     assert bench.config_for(wl, g, ours)["vertex_order"].startswith("relabelled")
     assert bench.config_for(wl, g, ref)["vertex_order"].startswith("as generated")
 
 
-def _traffic_file(tmp_path, h, order):
-    (tmp_path / "k_expand_traffic.md").write_text(
-        f"# x\n\nkernel_source_hash: {h}\nvertex_order: {order}\n\ntraffic_per_launch[rmat-s26-ef16]: 2.5e+09\n")
+def _traffic_file(tmp_path, h, order, kernel="k_bfs_persistent"):
+    import json
+
+    (tmp_path / "traffic.json").write_text(json.dumps(
+        {"kernel_source_hash": h, "entries": {f"rmat-s26-ef16|{order}|{kernel}": {"traffic_per_launch": 2.5e9}}}))
 
 
 def test_traffic_only_for_matching_source_and_order(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
     h = bench.kernel_source_hash()
     _traffic_file(tmp_path, h, "relabelled")
-    assert bench.profiled_traffic("rmat-s26-ef16", True) == 2.5e9
-    assert bench.profiled_traffic("rmat-s26-ef16", False) is None  # other vertex order
-    assert bench.profiled_traffic("rmat-s22-ef16", True) is None   # workload not profiled
+    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent") == 2.5e9
+    assert bench.profiled_traffic("rmat-s26-ef16", False, "k_bfs_persistent") is None  # other vertex order
+    assert bench.profiled_traffic("rmat-s22-ef16", True, "k_bfs_persistent") is None   # workload not profiled
+    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_expand") is None   # other kernel
     _traffic_file(tmp_path, "0" * 16, "relabelled")
-    assert bench.profiled_traffic("rmat-s26-ef16", True) is None   # kernel changed since
+    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent") is None   # kernel changed since
+    (tmp_path / "traffic.json").write_text("not json")
+    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent") is None
 
 
 def test_source_hash_ignores_comments():
@@ -61,11 +66,20 @@ def test_source_hash_ignores_comments():
     assert bench.strip_comments("x = 1;") != bench.strip_comments("x = 2;")
 
 
-def test_committed_traffic_summary_parses():
-    text = open(bench.PROFILES + "/k_expand_traffic.md").read()
-    assert re.search(r"kernel_source_hash:\s*[0-9a-f]{16}\b", text)
-    assert re.search(r"traffic_per_launch\[rmat-s26-ef16\]:\s*[0-9.]+e\+?\d+", text)
-    assert "--clock-control none" in text
+def test_committed_traffic_figures_parse():
+    import json
+    import os
+
+    path = os.path.join(bench.PROFILES, bench.TRAFFIC_JSON)
+    if not os.path.exists(path):
+        pytest.skip("no traffic figures committed")
+    db = json.load(open(path))
+    assert re.fullmatch(r"[0-9a-f]{16}", db["kernel_source_hash"])
+    for key, rec in db["entries"].items():
+        workload, order, kernel = key.split("|")
+        assert order in ("relabelled", "as-generated") and kernel.startswith("k_")
+        assert rec["traffic_per_launch"] > 0
+        assert "--clock-control none" in rec["command"]
 
 
 def test_reference_arm_runs_on_cpu(tmp_path):
@@ -141,3 +155,34 @@ def test_load_peaks(tmp_path, monkeypatch):
     assert bench.load_peaks()["source"] == "fallback"
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6668.2, "bf16_tflops": 1700}))
     assert bench.load_peaks() == {"hbm_gbs": 6668.2, "source": "measured"}
+
+
+def test_oracle_checks_catch_planted_mistakes(graphs_mod, oracle_mod):
+    """The bench's parity machinery (oracle levels in threads, bounded check queue): the
+    oracle's own results pass; a changed level, a parent that is not a neighbour and a
+    parent one level too high are each reported for the leg and root they were planted in."""
+    import numpy as np
+
+    g = graphs_mod.rmat(12, 16, seed=graphs_mod.GRAPH_SEED_BASE)
+    roots = graphs_mod.pick_roots(g, 6, 3)
+    checks = bench.OracleChecks(g, threads=3)
+    checks.set_ref(int(roots[0]), oracle_mod.bfs(g.offsets, g.cols, int(roots[0]))[0])
+    checks.compute(roots)
+    for i, r in enumerate(roots):
+        lv, pr = oracle_mod.bfs(g.offsets, g.cols, int(r))
+        checks.submit("good", i, r, lv, pr)
+        bad_l, bad_p = lv.copy(), pr.copy()
+        v = int(np.flatnonzero(lv == 2)[0])
+        if i % 3 == 0:
+            bad_l[v] = 3
+        elif i % 3 == 1:
+            bad_p[v] = v  # a vertex is not its own neighbour (the builder removes loops)
+        else:
+            bad_p[v] = int(r)  # the root is at level 0, not 1
+        checks.submit("planted", i, r, bad_l, bad_p)
+    rep = checks.report()
+    checks.close()
+    assert rep["good"] == {"roots_checked": 6, "levels_exact": True, "parents_valid": True, "ok": True}
+    bad = rep["planted"]
+    assert bad["roots_checked"] == 6 and not bad["ok"] and not bad["levels_exact"] and not bad["parents_valid"]
+    assert len(bad["failures"]) == 4 and bad["failures"][0]["root"] == int(roots[0])

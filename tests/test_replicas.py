@@ -13,16 +13,15 @@ import bench
 
 
 def test_replica_roots_disjoint_and_covering():
-    pool = np.arange(1000, 1100, dtype=np.int32)
+    pool = np.arange(1000, 1000 + 64 * 4, dtype=np.int32)
     for world in (1, 2, 3, 4):
-        warm = [bench.replica_roots(pool, 3, world, r)[0] for r in range(world)]
-        timed = [bench.replica_roots(pool, 3, world, r)[1] for r in range(world)]
-        assert sorted(np.concatenate(warm).tolist()) == pool[: 3 * world].tolist()
-        assert sorted(np.concatenate(timed).tolist()) == pool[3 * world:].tolist()
+        parts = [bench.replica_roots(pool, 64, world, r) for r in range(world)]
+        assert sorted(np.concatenate(parts).tolist()) == pool[: 64 * world].tolist()
+        assert parts[0].tolist() == pool[:64].tolist()  # rank 0 searches the configuration's roots
         for r in range(world):
-            assert len(warm[r]) == 3
+            assert len(parts[r]) == 64
             for q in range(r + 1, world):
-                assert not set(timed[r].tolist()) & set(timed[q].tolist())
+                assert not set(parts[r].tolist()) & set(parts[q].tolist())
 
 
 def test_aggregate_single_rank_is_identity():
