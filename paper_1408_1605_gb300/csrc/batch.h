@@ -37,19 +37,26 @@ struct BatchCtl {
   unsigned long long bitcnt[kMaxWave];  // per-root size of the new frontier (bottom-up choice)
 };
 
-// Parent event of a claim: vertex u's edge claimed the bits `mask` of the claimed vertex
-// (u in caller ids, ready to be written out; the event array itself is indexed internally).
+// Parent event of a claim: at wave level `level`, vertex u's edge claimed the bits `mask`
+// of the claimed vertex (u in caller ids, ready to be written out; the event array itself is
+// indexed internally).
 struct ClaimEvent {
   int32_t u;
-  int32_t pad;
+  int32_t level;
   unsigned long long mask;
 };
 struct OvfEvent {  // an event that did not fit the vertex's slots; v and u in caller ids
   int32_t v;
   int32_t u;
   unsigned long long mask;
+  int32_t level;
+  int32_t pad;
 };
-constexpr int kEventSlots = 4;  // per-vertex event slots per level
+// Per-vertex event slots. Serving waves write their outputs after every level and reuse the
+// slots level by level; bfs_run_batch keeps every event of the wave and writes the outputs
+// once, after the last level, so a vertex needs room for the events of all its levels.
+constexpr int kEventSlots = 4;
+constexpr int kEventSlotsWave = 8;
 
 template <typename OffT>
 struct BatchArgs {
@@ -64,8 +71,8 @@ struct BatchArgs {
   int32_t* chunk[2];
   BatchCtl* ctl;
   const WaveSlots* slots;
-  int32_t* evc;                   // events recorded per vertex this level
-  ClaimEvent* ev;                 // [n][kEventSlots]
+  int32_t* evc;                   // events recorded per vertex this level (this wave, with defer)
+  ClaimEvent* ev;                 // [n][ev_slots]
   OvfEvent* ovf;                  // events beyond the slots
   long long ovf_cap;
   Packed pk;
@@ -76,6 +83,9 @@ struct BatchArgs {
   int64_t nnz;
   int allow_bu;                   // bottom-up levels allowed (Beamer's switching, per wave)
   int alpha, beta;                // switching thresholds (as for single-source searches)
+  int ev_slots;                   // event slots per vertex (kEventSlots or kEventSlotsWave)
+  int defer;                      // 1: events kept for the whole wave, outputs written once at its end
+  int n_slots;                    // slots (roots) of the wave whose outputs the final pass writes
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -96,6 +106,7 @@ struct BatchBufs {
   ClaimEvent* ev = nullptr;
   OvfEvent* ovf = nullptr;
   long long ovf_cap = 0;
+  int ev_slots = kEventSlots;
 };
 
 struct RootSeed {
@@ -130,6 +141,9 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.new_id = g.new_id;
   a.old_id = g.old_id;
   a.nnz = g.nnz;
+  a.ev_slots = b.ev_slots;
+  a.defer = 0;
+  a.n_slots = kMaxWave;
   return a;
 }
 
@@ -139,9 +153,9 @@ template <typename OffT>
 void launch_level_stats(const OffT* off, const int32_t* new_id, int64_t n, const int32_t* levels, long long* out,
                         int num_sms, cudaStream_t st);
 
-cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b);
+cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots = kEventSlots);
 void free_batch_bufs(BatchBufs& b);
-size_t batch_bufs_bytes(const GraphDev& g);
+size_t batch_bufs_bytes(const GraphDev& g, int ev_slots = kEventSlots);
 
 template <typename OffT>
 void launch_batch_clear(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
@@ -159,6 +173,13 @@ void launch_fill(int32_t* p, int64_t count, int32_t value, int num_sms, cudaStre
 // Writes the levels and parents of the roots' vertices claimed by the last expansion.
 template <typename OffT>
 void launch_batch_emit(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
+// Waves with deferred outputs (a.defer): after each level, only the per-root sizes of the
+// new frontier (for the bottom-up choice; launched only when bottom-up levels are allowed);
+// after the last level, every output entry of the wave's slots, written once.
+template <typename OffT>
+void launch_batch_count(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
+template <typename OffT>
+void launch_batch_final(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_stats(const OffT* off, const int32_t* new_id, int64_t n, const WaveSlots* slots, int n_slots,
                         long long* stats, int num_sms, cudaStream_t st);

@@ -79,14 +79,14 @@ void free_batch_bufs(BatchBufs& b) {
   b = BatchBufs{};
 }
 
-size_t batch_bufs_bytes(const GraphDev& g) {
+size_t batch_bufs_bytes(const GraphDev& g, int ev_slots) {
   const size_t osz = g.off64 ? 8 : 4;
   const size_t ovf_cap = (size_t)g.n / 4 + 65536;
-  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * kEventSlots) +
+  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots) +
          ovf_cap * sizeof(OvfEvent) + 2 * 4 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
 }
 
-cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b) {
+cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots) {
   const size_t osz = g.off64 ? 8 : 4;
   b.chunk_cap = g.nnz / kChunk + 2;
   cudaError_t e = dalloc(&b.visited, (size_t)g.n);
@@ -105,7 +105,8 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b) {
   if (e == cudaSuccess) e = dalloc(&b.roots_dev, 4 * kMaxWave);
   b.ovf_cap = g.n / 4 + 65536;
   if (e == cudaSuccess) e = dalloc(&b.evc, (size_t)g.n);
-  if (e == cudaSuccess) e = dalloc(&b.ev, (size_t)g.n * kEventSlots);
+  b.ev_slots = ev_slots;
+  if (e == cudaSuccess) e = dalloc(&b.ev, (size_t)g.n * ev_slots);
   if (e == cudaSuccess) e = dalloc(&b.ovf, (size_t)b.ovf_cap);
   if (e == cudaSuccess) e = cudaMemset(b.evc, 0, sizeof(int32_t) * (size_t)g.n);
   if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
@@ -122,7 +123,7 @@ bfs_status ensure_batch_state(bfs_graph_s* G) {
   auto* S = new (std::nothrow) BatchState();
   if (!S) return fail(BFS_ERR_OOM, "host allocation");
   const GraphDev& g = G->g;
-  cudaError_t e = alloc_batch_bufs(g, S->b);
+  cudaError_t e = alloc_batch_bufs(g, S->b, kEventSlotsWave);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev_mid);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
@@ -145,6 +146,7 @@ BatchArgs<OffT> batch_args(const bfs_graph_s* G) {
   a.allow_bu = G->bottom_up;  // BFS_OPT_BOTTOM_UP also lets waves run bottom-up levels
   a.alpha = G->alpha;
   a.beta = G->beta;
+  a.defer = 1;  // every event kept until the wave ends; the outputs are written once, after it
   return a;
 }
 
@@ -180,7 +182,7 @@ static bfs_status build_batch_graph(bfs_graph_s* G) {
   }
   {
     cudaError_t le = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, cs);
-    launch_batch_emit<OffT>(a, G->g.num_sms, cs);
+    if (a.allow_bu) launch_batch_count<OffT>(a, G->g.num_sms, cs);
     e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
     if (le != cudaSuccess) e = le;
@@ -248,8 +250,8 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
                            st)) != cudaSuccess)
     return cuda_fail(e, "batch inputs");
   BatchArgs<OffT> a = batch_args<OffT>(G);
-  launch_fill(dl, (int64_t)per * n_roots, -1, g.num_sms, st);
-  launch_fill(dp, (int64_t)per * n_roots, -1, g.num_sms, st);
+  a.n_slots = n_roots;
+  // no fill of the outputs: the final pass writes every entry the roots' seeds do not
   launch_batch_clear<OffT>(a, g.num_sms, st);
   launch_batch_seed<OffT>(a, reinterpret_cast<const RootSeed*>(S->b.roots_dev), (int)seeds.size(), 0, true, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch init");
@@ -258,7 +260,7 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
     for (int64_t it = 0; it <= g.n; ++it) {
       if ((e = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, st)) != cudaSuccess)
         return cuda_fail(e, "batch expand");
-      launch_batch_emit<OffT>(a, g.num_sms, st);
+      if (a.allow_bu) launch_batch_count<OffT>(a, g.num_sms, st);
       if ((e = cudaMemcpyAsync(S->ctl_host, S->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "batch level sync");
@@ -271,6 +273,8 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
     }
     if ((e = cudaGraphLaunch(S->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   }
+  launch_batch_final<OffT>(a, g.num_sms, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch outputs");
   if ((e = cudaEventRecord(S->ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if (stats)
     launch_batch_stats<OffT>(reinterpret_cast<const OffT*>(g.off), g.new_id, g.n, S->b.slots, n_roots, S->b.stats, g.num_sms,

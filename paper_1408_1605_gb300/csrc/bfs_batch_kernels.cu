@@ -237,7 +237,8 @@ constexpr unsigned long long kSmallFrontierDiv = 16384;
 template <typename OffT, int WCAP>
 __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long long* __restrict__ F,
                                unsigned long long* Fn, unsigned long long active, int nxt, int q3n, int2* wbuf,
-                               int32_t* const* s_par, unsigned long long* s_alive) {
+                               int32_t* const* s_par, int32_t* const* s_lvl, const int32_t* s_start, int L,
+                               unsigned long long* s_alive) {
   static_assert(WCAP >= 64, "per-warp claim buffer too small");
   constexpr int P = (WCAP + 31) / 32;
   const unsigned full = 0xffffffffu;
@@ -256,7 +257,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
       if (need) {
         const OffT b = a.off[v], e = a.off[v + 1];
         deg = (int32_t)(e - b);
-        int nev = 0;
+        int nev = a.defer ? a.evc[v] : 0;  // this lane owns v: no other writer this level
         for (OffT i = b; i < e && acc != need; ++i) {
           const uint32_t u = (uint32_t)__ldg(a.cols + i);
           if (u >= (uint64_t)a.n) {
@@ -267,20 +268,23 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
           if (f) {
             acc |= f;
             const int32_t uc = a.old_id ? __ldg(a.old_id + u) : (int32_t)u;
-            if (nev < kEventSlots) {
+            if (nev < a.ev_slots) {
               ClaimEvent ce;
               ce.u = uc;
-              ce.pad = 0;
+              ce.level = L;
               ce.mask = f;
-              a.ev[(size_t)v * kEventSlots + nev] = ce;
+              a.ev[(size_t)v * a.ev_slots + nev] = ce;
             } else {
               const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;
               const unsigned long long o = atomicAdd(&a.ctl->ovf_count, 1ull);
               if ((long long)o < a.ovf_cap) {
-                a.ovf[o] = OvfEvent{vc, uc, f};
+                a.ovf[o] = OvfEvent{vc, uc, f, L, 0};
               } else {
-                for (unsigned long long bits = f; bits; bits &= bits - 1)  // no room: write now
-                  s_par[__ffsll((long long)bits) - 1][vc] = uc;
+                for (unsigned long long bits = f; bits; bits &= bits - 1) {  // no room: write now
+                  const int bb = __ffsll((long long)bits) - 1;
+                  s_par[bb][vc] = uc;
+                  s_lvl[bb][vc] = L - s_start[bb];
+                }
               }
             }
             ++nev;
@@ -289,7 +293,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
         if (acc) {  // this lane owns v: plain stores
           a.visited[v] |= acc;
           Fn[v] = acc;
-          a.evc[v] = min(nev, kEventSlots);
+          a.evc[v] = nev;
           mine |= acc;
         }
       }
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
     __syncthreads();  // slot pointers staged
     constexpr int WCAP = CLAIM / (BLOCK / 32);
     batch_bu_level<OffT, WCAP>(a, F, Fn, *(volatile unsigned long long*)&ctl->alive[cur], nxt, q3n,
-                               s_claim + warp * WCAP, s_par, &s_alive);
+                               s_claim + warp * WCAP, s_par, s_lvl, s_start, L, &s_alive);
   }
   for (int64_t tile = bu ? ntiles : (int64_t)blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const OffT e0 = (OffT)(tile * T);
@@ -469,21 +473,22 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
       if (claimed[j]) {
         mine |= claimed[j];
         // Parent event: the outputs are written in vertex order after the level (emit).
-        if (slot[j] < kEventSlots) {
+        if (slot[j] < a.ev_slots) {
           ClaimEvent ce;
           ce.u = uu[j];
-          ce.pad = 0;
+          ce.level = L;
           ce.mask = claimed[j];
-          a.ev[(size_t)v * kEventSlots + slot[j]] = ce;
+          a.ev[(size_t)v * a.ev_slots + slot[j]] = ce;
         } else {
           const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
           const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
           if ((long long)o < a.ovf_cap) {
-            a.ovf[o] = OvfEvent{vc, uu[j], claimed[j]};
+            a.ovf[o] = OvfEvent{vc, uu[j], claimed[j], L, 0};
           } else {
             for (unsigned long long bits = claimed[j]; bits; bits &= bits - 1) {  // no room: write now
               const int b = __ffsll((long long)bits) - 1;
               s_par[b][vc] = uu[j];
+              s_lvl[b][vc] = L - s_start[b];
             }
           }
         }
@@ -552,7 +557,9 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
 // vertices come from the next frontier list instead (scattered, cheaper than a full pass).
 // Events that did not fit the per-vertex slots are applied last; the last CTA resets the
 // overflow count.
-template <typename OffT>
+// COUNT_ONLY (waves with deferred outputs and bottom-up levels allowed): only the per-root
+// frontier sizes and the direction choice; no output writes, and the events stay.
+template <typename OffT, bool COUNT_ONLY>
 __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
   __shared__ int32_t* s_lvl[kMaxWave];
   __shared__ int32_t* s_par[kMaxWave];
@@ -578,7 +585,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
   unsigned long long cnt_lo = 0ull, cnt_hi = 0ull;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool ordered = nn * 8 > a.n;  // a full pass pays only when a large share of vertices was claimed
+  const bool ordered = !COUNT_ONLY && nn * 8 > a.n;  // a full pass pays only when many vertices were claimed
   const int64_t items = ordered ? (a.n + 31) / 32 : (nn + 31) / 32;
   for (int64_t w = gwarp; w < items; w += nwarps) {
     int32_t v = -1, vc = -1;  // internal id (masks, events) and caller id (outputs)
@@ -599,12 +606,12 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     int ne = 0;
     int32_t eu[kEventSlots];
     unsigned long long em[kEventSlots];
-    if (f) {
+    if (f && !COUNT_ONLY) {
       ne = min(a.evc[v], kEventSlots);
 #pragma unroll
       for (int k = 0; k < kEventSlots; ++k) {
         if (k < ne) {
-          const ClaimEvent ce = a.ev[(size_t)v * kEventSlots + k];
+          const ClaimEvent ce = a.ev[(size_t)v * a.ev_slots + k];
           eu[k] = ce.u;
           em[k] = ce.mask;
         } else {
@@ -624,7 +631,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
         const unsigned c = __popc(__ballot_sync(0xffffffffu, (f >> b) & 1ull));
         if (lane == (b & 31)) (b < 32 ? cnt_lo : cnt_hi) += c;
       }
-      if ((f >> b) & 1ull) {
+      if (!COUNT_ONLY && ((f >> b) & 1ull)) {
         s_lvl[b][vc] = L - s_start[b];
 #pragma unroll
         for (int k = 0; k < kEventSlots; ++k)
@@ -633,7 +640,8 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     }
   }
   // overflow events (after every slot event of the level is consumed above)
-  const long long novf = min((long long)*(volatile unsigned long long*)&ctl->ovf_count, a.ovf_cap);
+  const long long novf =
+      COUNT_ONLY ? 0 : min((long long)*(volatile unsigned long long*)&ctl->ovf_count, a.ovf_cap);
   for (long long o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < novf; o += (int64_t)gridDim.x * blockDim.x) {
     const OvfEvent e = a.ovf[o];
     for (unsigned long long bits = e.mask; bits; bits &= bits - 1) {
@@ -653,7 +661,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     __threadfence();
     if (atomicAdd(&ctl->emit_done, 1u) == gridDim.x - 1) {
       __threadfence();
-      ctl->ovf_count = 0;
+      if (!COUNT_ONLY) ctl->ovf_count = 0;  // with deferred outputs the overflow list lasts the wave
       ctl->emit_done = 0;
       if (a.allow_bu) {
         // A bottom-up level makes every vertex look for the bits of every active root, so a
@@ -676,7 +684,96 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
 
 template <typename OffT>
 void launch_batch_emit(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
-  k_batch_emit<OffT><<<num_sms * 8, 256, 0, st>>>(a);
+  k_batch_emit<OffT, false><<<num_sms * 8, 256, 0, st>>>(a);
+}
+
+template <typename OffT>
+void launch_batch_count(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
+  k_batch_emit<OffT, true><<<num_sms * 8, 256, 0, st>>>(a);
+}
+
+// The outputs of a wave with deferred outputs, written once after its last level. Every
+// event of the wave is still in the per-vertex slots (with its wave level), so entry
+// (b, vc) is: -1 if bit b never reached vc; else the level and parent of the event holding
+// bit b. A warp takes 32 consecutive caller ids and writes, for every slot b, 32 consecutive
+// entries of b's level row and of its parent row: every output line is written exactly once
+// (no fill beforehand, no partial lines per level). Entries with no event are left alone:
+// the roots (written when seeded), and claims that did not fit the slots, which the overflow
+// list applies here too (those entries are disjoint from the ones written from slots).
+template <typename OffT>
+__global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
+  constexpr int K = kEventSlotsWave;
+  __shared__ int32_t* s_lvl[kMaxWave];
+  __shared__ int32_t* s_par[kMaxWave];
+  __shared__ int32_t s_start[kMaxWave];
+  if (threadIdx.x < kMaxWave) {
+    s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
+    s_par[threadIdx.x] = a.slots->par[threadIdx.x];
+    s_start[threadIdx.x] = a.slots->start[threadIdx.x];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nb = a.n_slots;
+  for (int64_t w = gwarp; w * 32 < a.n; w += nwarps) {
+    const int64_t x = w * 32 + lane;
+    const bool in = x < a.n;
+    const int32_t vc = (int32_t)x;
+    unsigned long long vis = 0ull;
+    int ne = 0;
+    int32_t eu[K], el[K];
+    unsigned long long em[K];
+    if (in) {
+      const int32_t v = a.new_id ? __ldg(a.new_id + vc) : vc;
+      vis = a.visited[v];
+      if (vis) ne = min(a.evc[v], K);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        eu[k] = 0;
+        el[k] = 0;
+        em[k] = 0ull;
+        if (k < ne) {
+          const ClaimEvent ce = a.ev[(size_t)v * K + k];
+          eu[k] = ce.u;
+          el[k] = ce.level;
+          em[k] = ce.mask;
+        }
+      }
+    }
+    for (int b = 0; b < nb; ++b) {
+      int32_t lv = -1, pu = -1;
+      bool write = in;
+      if ((vis >> b) & 1ull) {
+        write = false;  // reached: only from an event (roots and overflow claims are written apart)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if ((em[k] >> b) & 1ull) {
+            lv = el[k] - s_start[b];
+            pu = eu[k];
+            write = true;
+          }
+      }
+      if (write) {
+        s_lvl[b][vc] = lv;
+        s_par[b][vc] = pu;
+      }
+    }
+  }
+  const long long novf = min((long long)*(volatile unsigned long long*)&a.ctl->ovf_count, a.ovf_cap);
+  for (long long o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < novf; o += (int64_t)gridDim.x * blockDim.x) {
+    const OvfEvent e = a.ovf[o];
+    for (unsigned long long bits = e.mask; bits; bits &= bits - 1) {
+      const int b = __ffsll((long long)bits) - 1;
+      s_lvl[b][e.v] = e.level - s_start[b];
+      s_par[b][e.v] = e.u;
+    }
+  }
+}
+
+template <typename OffT>
+void launch_batch_final(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
+  k_batch_final<OffT><<<num_sms * 8, 256, 0, st>>>(a);
 }
 
 template <typename OffT, int BLOCK, int E, int CLAIM>
@@ -839,6 +936,8 @@ void launch_level_stats(const OffT* off, const int32_t* new_id, int64_t n, const
 #define INST(OffT)                                                                                          \
   template void launch_batch_clear<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
   template void launch_batch_emit<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                        \
+  template void launch_batch_count<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
+  template void launch_batch_final<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
   template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
   template cudaError_t launch_batch_expand<OffT>(int, const BatchArgs<OffT>&, int, cudaStream_t);           \
   template int batch_expand_grid<OffT>(int, int);                                                           \

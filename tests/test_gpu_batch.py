@@ -176,3 +176,27 @@ def test_waves_with_bottom_up_levels(torch_cuda, oracle_mod, graphs_mod, policy,
             check_wave(capi, oracle_mod, torch_cuda, h, g, roots[:5], host_out=True)
         finally:
             capi.bfs_graph_destroy(h)
+
+
+@pytest.mark.parametrize("bottom_up", [0, 1])
+def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, bottom_up):
+    """Hub vertices claimed by many frontier vertices with disjoint root bits: 64 roots at
+    the leaves of a star (every leaf's edge claims its own bit of the centre, 64 parent
+    events at one vertex in one level), and a second hub joined to every leaf, so that the
+    events of a wave spill past the per-vertex slots into the overflow list. Every root
+    still gets the oracle's levels and a valid tree."""
+    from paper_1408_1605_gb300 import capi
+
+    leaves = np.arange(1, 65, dtype=np.int32)
+    src = np.concatenate([np.zeros(64, np.int32), np.full(64, 65, np.int32), np.arange(65, 164, dtype=np.int32)])
+    dst = np.concatenate([leaves, leaves, np.arange(66, 165, dtype=np.int32)])  # hub 65 leads into a path
+    g = graphs_mod.from_edges(165, src, dst)
+    for flags in (0, capi.BFS_RELABEL_DEGREE):
+        h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64 | flags)
+        try:
+            capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, bottom_up)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, leaves)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, np.concatenate([leaves[:32], [0, 65] * 16]))
+            check_wave(capi, oracle_mod, torch_cuda, h, g, leaves[::-1].copy(), host_out=True)
+        finally:
+            capi.bfs_graph_destroy(h)
