@@ -359,6 +359,8 @@ def main() -> int:
     ap.add_argument("--loop", default="", choices=["", "persistent", "graph", "host"],
                     help="level loop of single-source searches (default: the tuner's choice)")
     ap.add_argument("--shape", type=int, default=-1, help="single-source expansion shape (default: the tuner's)")
+    ap.add_argument("--batch-shape", type=int, default=-1,
+                    help="batched expansion shape (default: the tuner's; with --no-autotune, the library's)")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-levels-per-round", type=int, default=0)
@@ -424,6 +426,8 @@ def main() -> int:
     lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
     pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
     shapes = {"single": single_shape(capi, h, args, tune_class, g, roots, lv, pr)}
+    if args.batch_shape >= 0:
+        capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_BATCH, args.batch_shape)
 
     args.keep = rank == 0 and world == 1 and not args.no_parity  # results kept for the oracle checks
     slots = DeviceSlots(len(roots), g.n, args.keep)
@@ -485,7 +489,8 @@ def main() -> int:
     batched = None
     if not args.no_batched:
         k = min(64 * max(args.batch_waves, 1), len(roots))
-        batched = batched_leg(capi, h, g, roots[:k], last[:k], None if args.no_autotune else tune_class, shapes,
+        tune_batch = not args.no_autotune and args.batch_shape < 0
+        batched = batched_leg(capi, h, g, roots[:k], last[:k], tune_class if tune_batch else None, shapes,
                               args.keep)
 
     # aggregate over replicas: sum of per-rank harmonic means; time = max over ranks

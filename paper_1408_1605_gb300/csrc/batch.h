@@ -68,7 +68,7 @@ struct BatchArgs {
   int32_t* qv[3];                 // frontier vertex lists
   OffT* cum[2];
   OffT* base[2];
-  int32_t* chunk[2];
+  TileDesc<OffT>* chunk[2];       // tile descriptors every kChunk edges (k, internal id of entry k, column)
   BatchCtl* ctl;
   const WaveSlots* slots;
   int32_t* evc;                   // events recorded per vertex this level (this wave, with defer)
@@ -96,7 +96,7 @@ struct BatchBufs {
   int32_t* qv[3] = {nullptr, nullptr, nullptr};
   void* cum[2] = {nullptr, nullptr};
   void* base[2] = {nullptr, nullptr};
-  int32_t* chunk[2] = {nullptr, nullptr};
+  void* chunk[2] = {nullptr, nullptr};  // TileDesc<OffT>[chunk_cap]
   int64_t chunk_cap = 0;
   BatchCtl* ctl = nullptr;
   WaveSlots* slots = nullptr;       // device
@@ -128,7 +128,7 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   for (int i = 0; i < 2; ++i) {
     a.cum[i] = reinterpret_cast<OffT*>(b.cum[i]);
     a.base[i] = reinterpret_cast<OffT*>(b.base[i]);
-    a.chunk[i] = b.chunk[i];
+    a.chunk[i] = reinterpret_cast<TileDesc<OffT>*>(b.chunk[i]);
   }
   a.ctl = b.ctl;
   a.slots = b.slots;

@@ -83,7 +83,7 @@ size_t batch_bufs_bytes(const GraphDev& g, int ev_slots) {
   const size_t osz = g.off64 ? 8 : 4;
   const size_t ovf_cap = (size_t)g.n / 4 + 65536;
   return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots) +
-         ovf_cap * sizeof(OvfEvent) + 2 * 4 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
+         ovf_cap * sizeof(OvfEvent) + 2 * 16 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
 }
 
 cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots) {
@@ -97,7 +97,7 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots) {
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = dalloc(reinterpret_cast<char**>(&b.cum[i]), (size_t)g.n * osz);
     if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&b.base[i]), (size_t)g.n * osz);
-    if (e == cudaSuccess) e = dalloc(&b.chunk[i], (size_t)b.chunk_cap);
+    if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&b.chunk[i]), (size_t)b.chunk_cap * 16);
   }
   if (e == cudaSuccess) e = dalloc(&b.ctl, 1);
   if (e == cudaSuccess) e = dalloc(&b.slots, 1);

@@ -78,8 +78,8 @@ void launch_clear_bits(unsigned long long* visited, int64_t n, unsigned long lon
 // the block writes the chunk index of their rows (a hub root's row spans many chunks).
 template <typename OffT>
 __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_seeds, int fresh) {
-  __shared__ OffT s_cum[kMaxWave], s_deg[kMaxWave];
-  __shared__ int32_t s_k[kMaxWave];
+  __shared__ OffT s_cum[kMaxWave], s_deg[kMaxWave], s_base[kMaxWave];
+  __shared__ int32_t s_k[kMaxWave], s_v[kMaxWave];
   __shared__ int s_new, s_cur;
   if (threadIdx.x == 0) {
     BatchCtl* c = a.ctl;
@@ -122,7 +122,9 @@ __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_see
         a.base[cur][cnt] = o - (OffT)e;
         s_cum[added] = (OffT)e;
         s_deg[added] = d;
+        s_base[added] = o - (OffT)e;
         s_k[added] = (int32_t)cnt;
+        s_v[added] = v;
         ++added;
         ++cnt;
         e += (long long)d;
@@ -134,10 +136,11 @@ __global__ void k_batch_seed(BatchArgs<OffT> a, const RootSeed* seeds, int n_see
     s_cur = cur;
   }
   __syncthreads();
-  int32_t* chunk = a.chunk[s_cur];
+  TileDesc<OffT>* chunk = a.chunk[s_cur];
   for (int r = 0; r < s_new; ++r) {
     const OffT c0 = (s_cum[r] + kChunk - 1) / kChunk, c1 = (s_cum[r] + s_deg[r] + kChunk - 1) / kChunk;
-    for (OffT ch = c0 + (OffT)threadIdx.x; ch < c1; ch += (OffT)blockDim.x) chunk[ch] = s_k[r];
+    for (OffT ch = c0 + (OffT)threadIdx.x; ch < c1; ch += (OffT)blockDim.x)
+      chunk[ch] = TileDesc<OffT>{s_k[r], s_v[r], s_base[r] + ch * (OffT)kChunk};
   }
 }
 
@@ -177,16 +180,18 @@ __device__ __forceinline__ void batch_flush(const BatchArgs<OffT>& a, int nxt, i
   for (int t = 0; t < P; ++t) {  // uniform trip count: the chunk writes are warp-collective
     const int i = lo + t;
     const bool valid = i < hi;
-    OffT d = 0;
+    OffT d = 0, b = 0;
+    int32_t v = 0;
     const int32_t slot = (int32_t)(slot0 + i);
     if (valid) {
-      const int32_t v = s_claim[i].x;
+      v = s_claim[i].x;
       d = (OffT)s_claim[i].y;
+      b = a.off[v] - run;
       a.qv[q3n][slot] = v;
       a.cum[nxt][slot] = run;
-      a.base[nxt][slot] = a.off[v] - run;
+      a.base[nxt][slot] = b;
     }
-    write_chunks_warp(a.chunk[nxt], valid, run, d, slot);
+    write_descs_warp(a.chunk[nxt], valid, run, d, slot, v, b);
     run += d;
   }
 }
@@ -210,16 +215,18 @@ __device__ __forceinline__ void batch_warp_flush(const BatchArgs<OffT>& a, int n
   for (int t = 0; t < P; ++t) {  // uniform trip count: the chunk writes are warp-collective
     const int i = lo + t;
     const bool valid = i < hi;
-    OffT d = 0;
+    OffT d = 0, b = 0;
+    int32_t v = 0;
     const int32_t slot = (int32_t)(slot0 + i);
     if (valid) {
-      const int32_t v = buf[i].x;
+      v = buf[i].x;
       d = (OffT)buf[i].y;
+      b = a.off[v] - run;
       a.qv[q3n][slot] = v;
       a.cum[nxt][slot] = run;
-      a.base[nxt][slot] = a.off[v] - run;
+      a.base[nxt][slot] = b;
     }
-    write_chunks_warp(a.chunk[nxt], valid, run, d, slot);
+    write_descs_warp(a.chunk[nxt], valid, run, d, slot, v, b);
     run += d;
   }
   __syncwarp();
@@ -315,17 +322,186 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
   if (mine) atomicOr(s_alive, mine);
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
+// The top-down step of a wave with warp-sized tiles (the batched form of the single-source
+// warp tiles): warp w expands tiles w, w + W, ... of 32 E edges on its own, so no CTA-wide
+// barrier is needed inside a level. Edge e's frontier entry k = max{k : cum[k] <= e}
+// (Algorithm 3 line 2): a tile inside one row takes it from its tile descriptor; a tile
+// over at most 32 entries holds them one per lane (row start in the tile, column base,
+// caller id, frontier mask) and searches them with shuffles; a tile over more entries
+// searches the scan. Per edge (u, v): new = F_t[u] & ~V[v], claimed = new & ~atomicOr(V[v],
+// new); each claim records a parent event, and the first claim of v in this level appends v
+// to frontier t + 1 through the warp's claim buffer.
+template <typename OffT, int E, int WCAP>
+__device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt, int q3, int q3n, int64_t nf,
+                              OffT r, int2* wbuf, int32_t* const* s_par, int32_t* const* s_lvl,
+                              const int32_t* s_start, unsigned long long* s_alive) {
+  constexpr int TW = 32 * E;
+  static_assert(TW % kChunk == 0, "warp tiles must start on chunk-index boundaries");
+  static_assert(WCAP >= TW && WCAP % 32 == 0, "claim buffer must hold one full tile");
+  constexpr int P = WCAP / 32;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  BatchCtl* ctl = a.ctl;
+  const unsigned long long* F = a.fmask[q3];
+  unsigned long long* Fn = a.fmask[q3n];
+  const int32_t* qv = a.qv[q3];
+  const OffT* cum = a.cum[cur];
+  const OffT* basep = a.base[cur];
+  const TileDesc<OffT>* din = a.chunk[cur];
+  const int64_t ntiles = ((int64_t)r + TW - 1) / TW;
+  const int64_t wpb = blockDim.x >> 5;
+  int nc = 0;  // warp-uniform
+  unsigned long long mine = 0ull;
+  for (int64_t tile = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles; tile += (int64_t)gridDim.x * wpb) {
+    const OffT e0 = (OffT)(tile * TW);
+    const int cnt = (int)min((OffT)TW, r - e0);
+    const TileDesc<OffT> d0 = din[e0 / kChunk];
+    const int32_t klo = d0.k;
+    const int32_t kend = (e0 + cnt < r) ? din[(e0 + cnt) / kChunk].k : (int32_t)(nf - 1);
+    const bool one_row = klo == kend;
+    const int s = kend - klo + 1;
+    const bool fast = s <= 32;
+    // entry data: the row's (one_row, same on every lane) or entry klo + lane's
+    int32_t e_rel = 0x7fffffff, e_u = 0;
+    OffT e_base = 0;
+    unsigned long long e_f = 0ull;
+    if (one_row) {
+      e_f = F[d0.u];
+      e_u = a.old_id ? __ldg(a.old_id + d0.u) : d0.u;
+    } else if (fast && lane < s) {
+      const int32_t u = qv[klo + lane];
+      e_rel = (int32_t)max(cum[klo + lane] - e0, (OffT)0);  // entry klo starts at or before the tile
+      e_base = basep[klo + lane];
+      e_f = F[u];
+      e_u = a.old_id ? __ldg(a.old_id + u) : u;
+    }
+    int32_t vv[E], uu[E];
+    unsigned long long ff[E];
+    OffT col[E];
+    bool ok[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int er = lane + 32 * j;
+      ok[j] = er < cnt;
+      uu[j] = e_u;
+      ff[j] = e_f;
+      col[j] = d0.col + er;
+      if (!one_row && fast) {
+        // k = max{i : rel_i <= er} by a binary search over the lanes (rel_0 = 0 <= er)
+        int k = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int rc = __shfl_sync(full, e_rel, k + step);
+          if (rc <= er) k += step;
+        }
+        col[j] = __shfl_sync(full, e_base, k) + e0 + er;
+        uu[j] = __shfl_sync(full, e_u, k);
+        ff[j] = __shfl_sync(full, e_f, k);
+      }
+      if (ok[j] && !one_row && !fast) {
+        // more than 32 entries (short rows): search the scan directly
+        const OffT e = e0 + er;
+        const int32_t kk = binsearch_maxle(cum, (int64_t)klo, (int64_t)kend + 1, e);
+        const int32_t u = qv[kk];
+        col[j] = basep[kk] + e;
+        uu[j] = a.old_id ? __ldg(a.old_id + u) : u;
+        ff[j] = F[u];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) vv[j] = ok[j] ? ld_nc(a.cols + col[j]) : 0;
+    unsigned long long nb[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (ok[j] && (uint32_t)vv[j] >= (uint64_t)a.n) {
+        atomicOr(&ctl->error, kErrColumnRange);
+        ok[j] = false;
+      }
+      nb[j] = ok[j] ? (ff[j] & ~a.visited[vv[j]]) : 0ull;
+    }
+    unsigned long long claimed[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) claimed[j] = nb[j] ? nb[j] & ~atomicOr(a.visited + vv[j], nb[j]) : 0ull;
+    unsigned wc = 0;  // bit j: some lane of the warp claimed with edge j (warp-uniform)
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+      if (__ballot_sync(full, claimed[j] != 0ull)) wc |= 1u << j;
+    if (!wc) continue;  // most edges of a large level find every bit taken
+    int slot[E];
+    unsigned long long fold[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      slot[j] = 0;
+      fold[j] = 1ull;
+      if (claimed[j]) {
+        slot[j] = atomicAdd(a.evc + vv[j], 1);
+        fold[j] = atomicOr(Fn + vv[j], claimed[j]);
+      }
+    }
+    bool first[E];
+    int32_t deg[E];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int32_t v = vv[j];
+      first[j] = claimed[j] && fold[j] == 0ull;
+      deg[j] = first[j] ? (int32_t)(a.off[v + 1] - a.off[v]) : 0;
+      tot += __popc(__ballot_sync(full, first[j]));
+      if (claimed[j]) {
+        mine |= claimed[j];
+        // Parent event: the outputs are written after the wave (or the level) from it.
+        if (slot[j] < a.ev_slots) {
+          ClaimEvent ce;
+          ce.u = uu[j];
+          ce.level = L;
+          ce.mask = claimed[j];
+          a.ev[(size_t)v * a.ev_slots + slot[j]] = ce;
+        } else {
+          const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
+          const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
+          if ((long long)o < a.ovf_cap) {
+            a.ovf[o] = OvfEvent{vc, uu[j], claimed[j], L, 0};
+          } else {
+            for (unsigned long long bits = claimed[j]; bits; bits &= bits - 1) {  // no room: write now
+              const int b = __ffsll((long long)bits) - 1;
+              s_par[b][vc] = uu[j];
+              s_lvl[b][vc] = L - s_start[b];
+            }
+          }
+        }
+      }
+    }
+    if (nc + tot > WCAP) {
+      __syncwarp();
+      batch_warp_flush<OffT, P>(a, nxt, q3n, wbuf, nc);
+      nc = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const unsigned b = __ballot_sync(full, first[j]);
+      if (first[j]) wbuf[nc + __popc(b & lanemask_lt())] = make_int2(vv[j], deg[j]);
+      nc += __popc(b);
+    }
+  }
+  __syncwarp();
+  if (nc > 0) batch_warp_flush<OffT, P>(a, nxt, q3n, wbuf, nc);
+  // OR of the lanes' claimed bits, one shared atomic per warp
+  unsigned lo = __reduce_or_sync(full, (unsigned)mine), hi = __reduce_or_sync(full, (unsigned)(mine >> 32));
+  if (lane == 0 && (lo | hi)) atomicOr(s_alive, ((unsigned long long)hi << 32) | lo);
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
   using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
   constexpr int T = S::T, CAP = S::CAP;
-  static_assert(CLAIM >= T, "claim buffer must hold one full tile");
+  static_assert(WT || CLAIM >= T, "claim buffer must hold one full tile");
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* s_f = reinterpret_cast<unsigned long long*>(smem + S::off_f);
   OffT* s_base = reinterpret_cast<OffT*>(smem + S::off_base);
   int32_t* s_rel = reinterpret_cast<int32_t*>(smem + S::off_rel);
   int32_t* s_u = reinterpret_cast<int32_t*>(smem + S::off_u);
-  int2* s_claim = reinterpret_cast<int2*>(smem + S::off_claim);
+  // claim buffers: the CTA's (CTA tiles), or CLAIM entries per warp (warp tiles)
+  int2* s_claim = reinterpret_cast<int2*>(smem + (WT ? 0 : S::off_claim));
   __shared__ int32_t* s_lvl[kMaxWave];
   __shared__ int32_t* s_par[kMaxWave];
   __shared__ int32_t s_start[kMaxWave];
@@ -363,23 +539,27 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
   const int32_t* qv = a.qv[q3];
   const OffT* cum = a.cum[cur];
   const OffT* basep = a.base[cur];
-  const int32_t* chunk_in = a.chunk[cur];
+  const TileDesc<OffT>* chunk_in = a.chunk[cur];
   const int64_t ntiles = ((int64_t)r + T - 1) / T;
   const int bu = a.allow_bu ? *(volatile int*)&ctl->bu : 0;  // chosen when the previous level closed
 
+  constexpr int WCAP = WT ? CLAIM : CLAIM / (BLOCK / 32);  // claim entries per warp
   if (bu) {
     __syncthreads();  // slot pointers staged
-    constexpr int WCAP = CLAIM / (BLOCK / 32);
     batch_bu_level<OffT, WCAP>(a, F, Fn, *(volatile unsigned long long*)&ctl->alive[cur], nxt, q3n,
                                s_claim + warp * WCAP, s_par, s_lvl, s_start, L, &s_alive);
+  } else if constexpr (WT) {
+    __syncthreads();  // slot pointers staged
+    batch_td_warp<OffT, E, WCAP>(a, L, cur, nxt, q3, q3n, nf, r, s_claim + warp * WCAP, s_par, s_lvl, s_start,
+                                 &s_alive);
   }
-  for (int64_t tile = bu ? ntiles : (int64_t)blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = (bu || WT) ? ntiles : (int64_t)blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const OffT e0 = (OffT)(tile * T);
     const int cnt = (int)min((OffT)T, r - e0);
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_klo = chunk_in[e0 / kChunk];
-      s_kend = (e0 + cnt < r) ? chunk_in[(e0 + cnt) / kChunk] : (int32_t)(nf - 1);
+      s_klo = chunk_in[e0 / kChunk].k;
+      s_kend = (e0 + cnt < r) ? chunk_in[(e0 + cnt) / kChunk].k : (int32_t)(nf - 1);
     }
     __syncthreads();
     const int klo = s_klo;
@@ -703,16 +883,19 @@ void launch_batch_count(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) 
 template <typename OffT>
 __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
   constexpr int K = kEventSlotsWave;
+  static_assert(K == 8, "the event index of a bit is assembled from three masks");
   __shared__ int32_t* s_lvl[kMaxWave];
   __shared__ int32_t* s_par[kMaxWave];
   __shared__ int32_t s_start[kMaxWave];
+  __shared__ int32_t s_el[8][K][32];  // per warp: event k's level and claimer, lane-major
+  __shared__ int32_t s_eu[8][K][32];
   if (threadIdx.x < kMaxWave) {
     s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
     s_par[threadIdx.x] = a.slots->par[threadIdx.x];
     s_start[threadIdx.x] = a.slots->start[threadIdx.x];
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int nb = a.n_slots;
@@ -720,45 +903,44 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
     const int64_t x = w * 32 + lane;
     const bool in = x < a.n;
     const int32_t vc = (int32_t)x;
-    unsigned long long vis = 0ull;
-    int ne = 0;
-    int32_t eu[K], el[K];
-    unsigned long long em[K];
+    unsigned long long vis = 0ull, evm = 0ull, m0 = 0ull, m1 = 0ull, m2 = 0ull;
     if (in) {
       const int32_t v = a.new_id ? __ldg(a.new_id + vc) : vc;
       vis = a.visited[v];
-      if (vis) ne = min(a.evc[v], K);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        eu[k] = 0;
-        el[k] = 0;
-        em[k] = 0ull;
-        if (k < ne) {
-          const ClaimEvent ce = a.ev[(size_t)v * K + k];
-          eu[k] = ce.u;
-          el[k] = ce.level;
-          em[k] = ce.mask;
-        }
+      const int ne = vis ? min(a.evc[v], K) : 0;
+      for (int k = 0; k < ne; ++k) {
+        const ClaimEvent ce = a.ev[(size_t)v * K + k];
+        s_el[wib][k][lane] = ce.level;
+        s_eu[wib][k][lane] = ce.u;
+        // events hold disjoint bits: bit i of the index of bit b's event is bit b of m_i
+        evm |= ce.mask;
+        if (k & 1) m0 |= ce.mask;
+        if (k & 2) m1 |= ce.mask;
+        if (k & 4) m2 |= ce.mask;
       }
     }
-    for (int b = 0; b < nb; ++b) {
-      int32_t lv = -1, pu = -1;
-      bool write = in;
-      if ((vis >> b) & 1ull) {
-        write = false;  // reached: only from an event (roots and overflow claims are written apart)
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if ((em[k] >> b) & 1ull) {
-            lv = el[k] - s_start[b];
-            pu = eu[k];
-            write = true;
-          }
-      }
-      if (write) {
+    __syncwarp();
+    // Bits reached without an event (roots, overflow claims) are written apart: skip them.
+    const unsigned long long skip = vis & ~evm;
+    for (int half = 0; half < 2; ++half) {
+      const unsigned vlo = (unsigned)(vis >> (32 * half)), slo = (unsigned)(skip >> (32 * half));
+      const unsigned a0 = (unsigned)(m0 >> (32 * half)), a1 = (unsigned)(m1 >> (32 * half)),
+                     a2 = (unsigned)(m2 >> (32 * half));
+      const int bend = min(32, nb - 32 * half);
+      for (int i = 0; i < bend; ++i) {
+        const int b = 32 * half + i;
+        if (!in || ((slo >> i) & 1u)) continue;
+        int32_t lv = -1, pu = -1;
+        if ((vlo >> i) & 1u) {
+          const int k = ((a0 >> i) & 1u) | (((a1 >> i) & 1u) << 1) | (((a2 >> i) & 1u) << 2);
+          lv = s_el[wib][k][lane] - s_start[b];
+          pu = s_eu[wib][k][lane];
+        }
         s_lvl[b][vc] = lv;
         s_par[b][vc] = pu;
       }
     }
+    __syncwarp();
   }
   const long long novf = min((long long)*(volatile unsigned long long*)&a.ctl->ovf_count, a.ovf_cap);
   for (long long o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < novf; o += (int64_t)gridDim.x * blockDim.x) {
@@ -776,39 +958,51 @@ void launch_batch_final(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) 
   k_batch_final<OffT><<<num_sms * 8, 256, 0, st>>>(a);
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
+// Dynamic shared memory of a batched shape: CTA tiles stage their entries and share one
+// claim buffer; warp tiles need only CLAIM claim entries per warp.
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+constexpr size_t batch_smem_bytes() {
+  return WT ? (size_t)(BLOCK / 32) * CLAIM * sizeof(int2) : BatchSmem<OffT, BLOCK, E, CLAIM>::bytes;
+}
+
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 static cudaError_t launch_batch_expand_t(const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
-  using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM>;
+  constexpr size_t bytes = batch_smem_bytes<OffT, BLOCK, E, CLAIM, WT>();
+  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM, WT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  kern<<<grid, BLOCK, S::bytes, st>>>(a);
+  kern<<<grid, BLOCK, bytes, st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
 static int batch_grid_t(int num_sms) {
-  using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
-  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  constexpr size_t bytes = batch_smem_bytes<OffT, BLOCK, E, CLAIM, WT>();
+  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM, WT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, S::bytes) != cudaSuccess) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
   return (per_sm > 0 ? per_sm : 1) * num_sms;
 }
 
-// Compiled shapes of the batched expansion (BLOCK, E, CLAIM); the autotuner picks one.
+// Compiled shapes of the batched expansion (BLOCK, E, CLAIM, tiles): tiles 0 = CTA tiles of
+// BLOCK x E edges (CLAIM = CTA claim buffer), 1 = warp tiles of 32 x E edges (CLAIM = claim
+// entries per warp). The autotuner picks one.
 #define GBFS_BATCH_SHAPES(X) \
-  X(0, 256, 4, 2048)         \
-  X(1, 256, 2, 2048)         \
-  X(2, 128, 4, 1024)         \
-  X(3, 512, 2, 2048)
+  X(0, 256, 4, 2048, 0)      \
+  X(1, 256, 2, 2048, 0)      \
+  X(2, 128, 4, 1024, 0)      \
+  X(3, 512, 2, 2048, 0)      \
+  X(4, 256, 4, 128, 1)       \
+  X(5, 128, 4, 128, 1)       \
+  X(6, 256, 8, 256, 1)
 
 const ExpandShape kBatchShapes[] = {
-#define X(id, b, e, c) {id, b, e, c, 0},
+#define X(id, b, e, c, w) {id, b, e, c, w},
     GBFS_BATCH_SHAPES(X)
 #undef X
 };
@@ -817,8 +1011,8 @@ const int kNumBatchShapes = sizeof(kBatchShapes) / sizeof(kBatchShapes[0]);
 template <typename OffT>
 cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
-#define X(id, b, e, c) \
-  case id: return launch_batch_expand_t<OffT, b, e, c>(a, grid, st);
+#define X(id, b, e, c, w) \
+  case id: return launch_batch_expand_t<OffT, b, e, c, w != 0>(a, grid, st);
     GBFS_BATCH_SHAPES(X)
 #undef X
   }
@@ -828,8 +1022,8 @@ cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, c
 template <typename OffT>
 int batch_expand_grid(int shape, int num_sms) {
   switch (shape) {
-#define X(id, b, e, c) \
-  case id: return batch_grid_t<OffT, b, e, c>(num_sms);
+#define X(id, b, e, c, w) \
+  case id: return batch_grid_t<OffT, b, e, c, w != 0>(num_sms);
     GBFS_BATCH_SHAPES(X)
 #undef X
   }

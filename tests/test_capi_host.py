@@ -112,7 +112,7 @@ def test_shape_tables(capi):
             assert info["block"] % 32 == 0 and info["edges_per_thread"] >= 1
             tile = (32 if info["warp_tiles"] else info["block"]) * info["edges_per_thread"]
             assert info["claim_buffer"] >= tile and tile % 128 == 0
-            assert info["warp_tiles"] in (0, 1) and (kind == capi.BFS_KERNEL_SINGLE or not info["warp_tiles"])
+            assert info["warp_tiles"] in (0, 1)
     assert capi.bfs_shape_count(7) == 0
     # tests/test_gpu_bfs.py runs every single-source shape: keep its list in step
     assert capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE) == 9

@@ -200,3 +200,32 @@ def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, botto
             check_wave(capi, oracle_mod, torch_cuda, h, g, leaves[::-1].copy(), host_out=True)
         finally:
             capi.bfs_graph_destroy(h)
+
+
+@pytest.mark.parametrize("shape", list(range(7)))
+@pytest.mark.parametrize("force64", [False, True])
+def test_every_batch_shape(torch_cuda, oracle_mod, graphs_mod, shape, force64):
+    """Every compiled batched shape (CTA tiles and warp tiles), both offset widths, on R-MAT
+    (input order and degree-relabelled), a grid, a uniform multigraph-free graph and a graph
+    with an isolated vertex, top-down waves and waves with bottom-up levels; every slot has
+    the oracle's levels and a valid tree."""
+    from paper_1408_1605_gb300 import capi
+
+    fx = load_golden("two_components.txt")
+    gs = [(graphs_mod.rmat(15, 16, seed=23), 0), (graphs_mod.rmat(15, 16, seed=23), capi.BFS_RELABEL_DEGREE),
+          (graphs_mod.grid3d(13, 11, 9), 0), (graphs_mod.uniform(12000, 60000, seed=4), 0),
+          (graphs_mod.from_edges(fx["n"], fx["src"], fx["dst"]), 0)]
+    for g, relabel in gs:
+        rng = np.random.default_rng(g.n + shape)
+        roots = rng.integers(0, g.n, size=min(64, g.n))
+        roots[2] = roots[1]  # a repeated root
+        h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64 | relabel
+                                  | (capi.BFS_KEEP_INT64 if force64 else 0))
+        try:
+            capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_BATCH, shape)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, roots)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, roots[:7])
+            capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, 1)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, roots)
+        finally:
+            capi.bfs_graph_destroy(h)
