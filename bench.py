@@ -353,7 +353,11 @@ def main() -> int:
     ap.add_argument("--no-batched-config", action="store_true",
                     help="skip the R-MAT scale-22 leg of 256 roots in 4 batched waves")
     ap.add_argument("--batch-waves", type=int, default=1, help="64-root waves in the batched leg")
+    ap.add_argument("--no-wide", action="store_true",
+                    help="skip the leg on R-MAT s26 edge factor 17 (more than 2^31 - 1 CSR entries: 64-bit offsets)")
     ap.add_argument("--no-direction", action="store_true")
+    ap.add_argument("--no-frontier-bitmap", action="store_true",
+                    help="skip the leg that times the same searches with the list-or-bitmap frontier switch")
     ap.add_argument("--mode", default="single", choices=["single", "serve", "multigraph"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--loop", default="", choices=["", "persistent", "graph", "host"],
@@ -482,6 +486,10 @@ def main() -> int:
     e2e_hm = harmonic_mean(e2e_teps)
     del hl, hp
 
+    bitmap_leg = None
+    if not args.no_frontier_bitmap:
+        bitmap_leg = frontier_bitmap_leg(capi, h, g, roots, args, lv, pr, hm)
+
     direction = None
     if not args.no_direction:
         direction = direction_leg(capi, h, g, roots, args, lv, pr)
@@ -502,19 +510,26 @@ def main() -> int:
         if not args.no_cpu_baseline:
             cpu_baseline = cpu_baseline_leg(g, roots, checks)
         if checks is not None:
-            parity = parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, args)
+            parity = parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, args, bitmap_leg)
             checks.close()
-    for leg in (direction, batched):  # release the kept outputs
+    for leg in (direction, batched, bitmap_leg):  # release the kept outputs
         for key in ("_slots", "_slots_do", "_options"):
             if leg is not None:
                 leg.pop(key, None)
     del slots
+    wide = None
     if rank == 0 and world == 1 and not args.no_batched_config and not args.no_batched \
             and wl.name != "rmat-s22-ef16":
         capi.bfs_graph_destroy(h)
         h = None
         torch.cuda.empty_cache()
         batched_config = batched_config_leg(capi, args)
+    if rank == 0 and world == 1 and not args.no_wide and wl.name == "rmat-s26-ef16":
+        if h is not None:
+            capi.bfs_graph_destroy(h)
+            h = None
+        torch.cuda.empty_cache()
+        wide = wide_offsets_leg(capi, args)
 
     if rank == 0:
         peaks = load_peaks()
@@ -543,12 +558,16 @@ def main() -> int:
                        "min_gteps": round(min(teps_of(s) for s in stats), 3),
                        "max_gteps": round(max(teps_of(s) for s in stats), 3)},
         }
+        if bitmap_leg is not None:
+            line["frontier_bitmap"] = bitmap_leg
         if direction is not None:
             line["direction_optimizing"] = direction
         if batched is not None:
             line["batched"] = batched
         if batched_config is not None:
             line["batched_rmat_s22_4x64"] = batched_config
+        if wide is not None:
+            line["wide_offsets_rmat_s26_ef17"] = wide
         if parity is not None:
             line["parity"] = parity
         if cpu_baseline is not None:
@@ -558,7 +577,8 @@ def main() -> int:
         capi.bfs_graph_destroy(h)
     if world > 1:
         torch.distributed.destroy_process_group()
-    ok = (parity is None or parity["ok"]) and (batched_config is None or batched_config.get("parity_ok", True))
+    ok = (parity is None or parity["ok"]) and (batched_config is None or batched_config.get("parity_ok", True)) \
+        and (wide is None or wide.get("parity_ok", True))
     return 0 if ok else 1
 
 
@@ -583,6 +603,26 @@ def single_shape(capi, h, args, tune_class, g, roots, lv, pr) -> dict:
     return {"shape": shape, **capi.bfs_shape_info(capi.BFS_KERNEL_SINGLE, shape), "cached": False,
             "loop": names[capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP)],
             "persist_ctas_per_sm": capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS)}
+
+
+def frontier_bitmap_leg(capi, h, g, roots, args, lv, pr, list_hm) -> dict:
+    """The same searches (same loop and shape) with the list-or-bitmap switch of the
+    paper's Sec. 5 (BFS_FRONTIER_AUTO): a level whose next frontier would hold more than
+    n / 32 ids hands it over as a bitmap, unpacked in vertex order. Reports whether it pays
+    against the list-only figure; each root's result is kept for the oracle checks."""
+    capi.bfs_graph_set_option(h, capi.BFS_OPT_FRONTIER, capi.BFS_FRONTIER_AUTO)
+    try:
+        single_pass(capi, h, roots[:3], lv, pr)
+        slots = DeviceSlots(len(roots), g.n, args.keep)
+        st = single_pass(capi, h, roots, lv, pr, slots)
+        unpacked = capi.bfs_graph_get_option(h, capi.BFS_OPT_UNPACKED_LEVELS)
+    finally:
+        capi.bfs_graph_set_option(h, capi.BFS_OPT_FRONTIER, capi.BFS_FRONTIER_LIST)
+    hm = harmonic_mean([teps_of(s) for s in st])
+    return {"value": round(hm, 3), "unit": UNIT, "searches": len(st), "mode": "auto (list while <= n/32 ids)",
+            "mean_device_ms": round(sum(s["device_ms"] for s in st) / len(st), 4),
+            "unpacked_levels_last_search": unpacked, "vs_list": round(hm / list_hm, 3) if list_hm else None,
+            "pays": bool(list_hm and hm > list_hm), "_slots": slots}
 
 
 def direction_leg(capi, h, g, roots, args, lv, pr):
@@ -623,6 +663,7 @@ def run_waves(capi, h, roots, lv, pr, wave=64):
     """Device ms and edges of the roots run as consecutive waves of up to 64 roots; wave i
     writes rows [64 i, 64 i + len) of lv / pr."""
     edges, ms, bu, waves = 0, 0.0, 0, 0
+    diag = {"loop_ms": 0.0, "levels": 0, "overflow_records": 0}
     for i in range(0, len(roots), wave):
         part = roots[i:i + wave]
         st = capi.bfs_run_batch(h, part, lv[i:i + len(part)], pr[i:i + len(part)], want_stats=True)
@@ -630,6 +671,10 @@ def run_waves(capi, h, roots, lv, pr, wave=64):
         ms += st[0].device_ms
         bu += st[0].bottom_up_levels
         waves += 1
+        diag["loop_ms"] += st[0].expand_ms
+        diag["levels"] += capi.bfs_graph_get_option(h, capi.BFS_OPT_WAVE_LEVELS)
+        diag["overflow_records"] += capi.bfs_graph_get_option(h, capi.BFS_OPT_WAVE_OVERFLOW)
+    run_waves.last = {k: round(v / max(waves, 1), 3) for k, v in diag.items()}  # per wave
     return edges, ms, bu, waves
 
 
@@ -653,6 +698,7 @@ def batched_leg(capi, h, g, roots, single_stats, graph_class=None, shapes=None, 
         log(f"[bench] batch shape {rec['shape']} ms per shape {rec.get('ms')}")
     capi.bfs_run_batch(h, roots[:k], lv[:k], pr[:k], want_stats=True)  # warm-up (buffers, graph)
     edges, ms, _, waves = run_waves(capi, h, roots, lv, pr)
+    per_wave = run_waves.last
     single_agg = sum(s["edges_traversed"] for s in single_stats) / (sum(s["device_ms"] for s in single_stats) * 1e-3)
     agg = edges / (ms * 1e-3)
     slots = DeviceSlots(0, 0, False)
@@ -665,17 +711,69 @@ def batched_leg(capi, h, g, roots, single_stats, graph_class=None, shapes=None, 
         slots_do, slots = slots, None
     capi.bfs_run_batch(h, roots[:k], slots_do.lv[:k], slots_do.pr[:k], want_stats=True)  # warm-up (new loop)
     edges_do, ms_do, bu_levels, _ = run_waves(capi, h, roots, slots_do.lv, slots_do.pr)
+    per_wave_do = run_waves.last
     capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, saved_bu)
     agg_do = edges_do / (ms_do * 1e-3)
     assert len(single_stats) == len(roots)
     return {"waves": waves, "roots_per_wave": 64, "roots": len(roots), "aggregate_gteps": round(agg / 1e9, 3),
             "single_source_aggregate_gteps": round(single_agg / 1e9, 3), "ratio": round(agg / single_agg, 3),
-            "ms_per_wave": round(ms / waves, 3),
+            "ms_per_wave": round(ms / waves, 3), "per_wave": per_wave,
             "direction_optimizing": {"aggregate_gteps": round(agg_do / 1e9, 3),
                                      "ratio_vs_single_top_down": round(agg_do / single_agg, 3),
                                      "ms_per_wave": round(ms_do / waves, 3),
-                                     "bottom_up_levels_per_wave": round(bu_levels / waves, 2)},
+                                     "bottom_up_levels_per_wave": round(bu_levels / waves, 2),
+                                     "per_wave": per_wave_do},
             "_slots": slots, "_slots_do": slots_do}
+
+
+def wide_offsets_leg(capi, args, n_roots: int = 4) -> dict:
+    """R-MAT scale 26 with edge factor 17: the cleaned graph has more than 2^31 - 1 CSR
+    entries, so the library keeps 64-bit row offsets, frontier scan values and tile
+    descriptors. A few seeded roots run single-source and as one batched wave, with the
+    same tuned shapes as the scale-26 edge-factor-16 graph; every result is checked against
+    the oracle."""
+    import torch
+
+    from paper_1408_1605_gb300.workloads import WORKLOADS
+
+    wl = WORKLOADS["rmat-s26-ef17"]
+    t = time.perf_counter()
+    g = wl.make()
+    roots = wl.pick_roots(g, n_roots)
+    relabel = use_relabel(wl.kind, args.relabel)
+    h = create_graph(capi, g, relabel)
+    log(f"[bench] wide offsets {wl.name}: n={g.n} nnz={g.nnz} ({time.perf_counter() - t:.1f}s)")
+    try:
+        lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        sub = argparse.Namespace(**vars(args))
+        tune_class = wl.kind + ("-relabel" if relabel else "")
+        single = single_shape(capi, h, sub, tune_class, g, roots, lv, pr)
+        single_pass(capi, h, roots[:1], lv, pr)
+        slots = DeviceSlots(len(roots), g.n, not args.no_parity)
+        stats = single_pass(capi, h, roots, lv, pr, slots)
+        res = {"n_vertices": g.n, "csr_entries": g.nnz, "offsets": "int64" if g.nnz > 2**31 - 1 else "int32",
+               "roots": len(roots), "single_source_hm_gteps": round(harmonic_mean([teps_of(s) for s in stats]), 3),
+               "mean_device_ms": round(sum(s["device_ms"] for s in stats) / len(stats), 3), "single_shape": single}
+        bl = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
+        bp = torch.empty((len(roots), g.n), dtype=torch.int32, device="cuda")
+        bst = capi.bfs_run_batch(h, roots, bl, bp, want_stats=True)
+        res["batched_wave_ms"] = round(bst[0].device_ms, 3)
+        if not args.no_parity:
+            checks = OracleChecks(g, args.parity_threads)
+            checks.compute(roots)
+            for i, r in enumerate(roots):
+                checks.submit("single", i, r, *fetch(capi, h, r, slots, i, lv, pr))
+                checks.submit("batched", i, r, bl[i].cpu().numpy(), bp[i].cpu().numpy())
+            rep = checks.report()
+            checks.close()
+            res["parity"] = rep
+            res["parity_ok"] = all(v["ok"] for v in rep.values())
+        del slots, bl, bp
+        return res
+    finally:
+        capi.bfs_graph_destroy(h)
+        torch.cuda.empty_cache()
 
 
 def batched_config_leg(capi, args) -> dict:
@@ -1022,7 +1120,7 @@ def cpu_baseline_leg(g, roots, checks, budget_s: float = 15.0) -> dict:
                       "one thread", **host_cpu()}
 
 
-def parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, args) -> dict:
+def parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, args, bitmap_leg=None) -> dict:
     """Every timed root's result against the oracle: the top-down searches of the last timed
     step, the direction-optimizing searches and the batched waves' slots (all kept on the
     device), plus, on 3D grids, levels equal to the Manhattan distance on sampled roots."""
@@ -1034,6 +1132,11 @@ def parity_leg(capi, h, g, roots, checks, slots, lv, pr, direction, batched, arg
         f"({checks.threads} threads)")
     for i, r in enumerate(roots):
         checks.submit("single_source", i, r, *fetch(capi, h, r, slots, i, lv, pr))
+    if bitmap_leg is not None:
+        sl = bitmap_leg.get("_slots")
+        if sl is not None and sl.kept:
+            for i, r in enumerate(roots):
+                checks.submit("frontier_bitmap", i, r, *fetch(capi, h, r, sl, i, lv, pr))
     if direction is not None:
         sl = direction.get("_slots")
         if sl is None or not sl.kept:

@@ -134,7 +134,21 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *   BFS_OPT_RELABELED (read only): 1 if the graph was created with BFS_RELABEL_DEGREE.
  *   BFS_OPT_PERSIST_CTAS: CTAs per SM of a persistent search (0, the default: as many as
  *     fit). Fewer CTAs make each level boundary cheaper, which pays on graphs of hundreds
- *     of small levels (3D grids); large levels want them all. */
+ *     of small levels (3D grids); large levels want them all.
+ *   BFS_OPT_FRONTIER: how a top-down level hands its next frontier to the next level
+ *     (Sec. 5, the switch between a vertex list and a bitmap of the vertices by size).
+ *     BFS_FRONTIER_LIST (default): a list of vertex ids with its degree scan, built by the
+ *     appends of the expansion. BFS_FRONTIER_AUTO: the same while the list holds at most
+ *     ceil(n / 32) entries, i.e. while its 32-bit ids take fewer bits than an n-bit bitmap;
+ *     past that the level records its claims only in a bitmap of the next frontier, and the
+ *     list is rebuilt from the bitmap after the level (in vertex order, by a warp-centric
+ *     unpack that writes ids, scan and tile descriptors). BFS_FRONTIER_BITMAP: every
+ *     top-down level hands over a bitmap. Results are the same BFS in every mode.
+ *   BFS_OPT_UNPACKED_LEVELS (read only): levels of the last persistent search whose next
+ *     frontier was rebuilt from a bitmap (-1 after a search in another loop mode).
+ *   BFS_OPT_WAVE_LEVELS, BFS_OPT_WAVE_OVERFLOW (read only): levels run by the last batched
+ *     wave on this graph, and how many of its claim records did not fit the per-vertex
+ *     slots (they are applied from an overflow list when the wave's outputs are written). */
 #define BFS_OPT_LOOP 1
 #define BFS_OPT_BOTTOM_UP 2
 #define BFS_OPT_ALPHA 3
@@ -143,6 +157,13 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
 #define BFS_OPT_PROBE 6
 #define BFS_OPT_RELABELED 7
 #define BFS_OPT_PERSIST_CTAS 8
+#define BFS_OPT_WAVE_LEVELS 9
+#define BFS_OPT_WAVE_OVERFLOW 10
+#define BFS_OPT_FRONTIER 11
+#define BFS_OPT_UNPACKED_LEVELS 12
+#define BFS_FRONTIER_LIST 0
+#define BFS_FRONTIER_AUTO 1
+#define BFS_FRONTIER_BITMAP 2
 #define BFS_LOOP_PERSISTENT 0
 #define BFS_LOOP_GRAPH 1
 #define BFS_LOOP_HOST 2
@@ -204,6 +225,19 @@ GBFS_API bfs_status bfs_run_batch(bfs_graph_t g, const int32_t *roots, int n_roo
 GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n_frontier, int32_t level,
                                uint32_t *bitmap, int32_t *levels, int32_t *parents, int32_t *next,
                                int64_t *next_count, void *stream);
+
+/* One top-down level on caller-held state, as bfs_expand, that hands over its next frontier
+ * as a bitmap (Sec. 5: the specialized expansion that produces a bitmap instead of a list):
+ *   next_bitmap uint32[ceil(n/32)] (device): cleared by the call, then bit v % 32 of word
+ *     v / 32 set for every vertex v the level claims;
+ *   next int32[n] (device) or NULL: if given, the claimed vertices unpacked from next_bitmap
+ *     by the warp-centric unpack (each once; in increasing order within each run of
+ *     consecutive bitmap words a CTA unpacks, runs in unspecified order);
+ *   next_count int64 (device): the number of claimed vertices.
+ * Other arguments, the synchronization and the failures as for bfs_expand. */
+GBFS_API bfs_status bfs_expand_bitmap(bfs_graph_t g, const int32_t *frontier, int64_t n_frontier, int32_t level,
+                                      uint32_t *bitmap, int32_t *levels, int32_t *parents, uint32_t *next_bitmap,
+                                      int32_t *next, int64_t *next_count, void *stream);
 
 /* Single-source BFS that allocates nothing, for callers that may not allocate device
  * memory at call time: code whose framework allocator owns all device memory, loops in

@@ -34,6 +34,13 @@ BFS_OPT_WAIT_LIMIT = 5
 BFS_OPT_PROBE = 6
 BFS_OPT_RELABELED = 7
 BFS_OPT_PERSIST_CTAS = 8
+BFS_OPT_WAVE_LEVELS = 9
+BFS_OPT_WAVE_OVERFLOW = 10
+BFS_OPT_FRONTIER = 11
+BFS_OPT_UNPACKED_LEVELS = 12
+BFS_FRONTIER_LIST = 0
+BFS_FRONTIER_AUTO = 1
+BFS_FRONTIER_BITMAP = 2
 BFS_LOOP_PERSISTENT = 0
 BFS_LOOP_GRAPH = 1
 BFS_LOOP_HOST = 2
@@ -102,6 +109,7 @@ def lib():
             "bfs_graph_info": [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
             "bfs_run": [_P, i32, _P, _P, _P, ctypes.POINTER(bfs_stats)],
             "bfs_expand": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P],
+            "bfs_expand_bitmap": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P, _P],
             "bfs_run_noalloc": [_P, _P, i64, i64, i32, _P, _P, _P],
             "bfs_run_batch": [_P, _P, ctypes.c_int, _P, _P, _P, _P],
             "bfs_serve_create": [ctypes.POINTER(bfs_serve_config), ctypes.POINTER(_P)],
@@ -252,6 +260,12 @@ def bfs_expand(graph: int, frontier, n_frontier: int, level: int, bitmap, levels
                stream=None) -> None:
     check(lib().bfs_expand(graph, ptr(frontier), int(n_frontier), int(level), ptr(bitmap), ptr(levels), ptr(parents),
                            ptr(next_), ptr(next_count), stream_handle(stream)))
+
+
+def bfs_expand_bitmap(graph: int, frontier, n_frontier: int, level: int, bitmap, levels, parents, next_bitmap,
+                      next_, next_count, stream=None) -> None:
+    check(lib().bfs_expand_bitmap(graph, ptr(frontier), int(n_frontier), int(level), ptr(bitmap), ptr(levels),
+                                  ptr(parents), ptr(next_bitmap), ptr(next_), ptr(next_count), stream_handle(stream)))
 
 
 def bfs_run_noalloc(row_offsets, cols, n_vertices: int, n_entries: int, root: int, levels, parents,

@@ -24,6 +24,8 @@ struct BatchState {
   cudaEvent_t ev0 = nullptr, ev_mid = nullptr, ev1 = nullptr;
   BatchCtl* ctl_host = nullptr;      // pinned
   long long* stats_host = nullptr;   // pinned, 3 * kMaxWave
+  long long last_levels = 0;         // levels and overflow records of the last wave
+  long long last_overflow = 0;
   int32_t* stage_lvl = nullptr;      // device staging when outputs are host memory
   int32_t* stage_par = nullptr;
   int stage_roots = 0;
@@ -48,6 +50,9 @@ static void free_batch(BatchState* S) {
   if (S->ctl_host) cudaFreeHost(S->ctl_host);
   if (S->stats_host) cudaFreeHost(S->stats_host);
 }
+
+long long batch_last_levels(const bfs_graph_s* G) { return G->batch ? G->batch->last_levels : 0; }
+long long batch_last_overflow(const bfs_graph_s* G) { return G->batch ? G->batch->last_overflow : 0; }
 
 void destroy_batch_state(bfs_graph_s* G) {
   if (G->batch) {
@@ -295,6 +300,8 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
   if (stats || host_out) {
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "batch search");
     if (S->ctl_host->error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
+    S->last_levels = S->ctl_host->level - 1;
+    S->last_overflow = (long long)S->ctl_host->ovf_count;
     if (stats) {
       float ms = 0.f, loop_ms = 0.f;
       cudaEventElapsedTime(&ms, S->ev0, S->ev1);

@@ -140,6 +140,13 @@ ExpandArgs<OffT> make_args(const bfs_graph_s* G, uint32_t* bitmap) {
   a.use_cond = 0;
   a.probe_mode = G->probe_mode;
   a.old_id = g.old_id;
+  a.fbm[0] = a.fbm[1] = nullptr;
+  a.list_cap = -1;
+  if (G->frontier_mode != BFS_FRONTIER_LIST) {  // next-frontier bitmaps by level parity
+    a.fbm[0] = ws.fbm[0];
+    a.fbm[1] = ws.fbm[1];
+    a.list_cap = frontier_list_cap(G->frontier_mode, g.n);
+  }
   return a;
 }
 
@@ -183,6 +190,7 @@ static bfs_status build_loop_graph(bfs_graph_s* G, cudaStream_t st) {
     return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
   }
   cudaError_t le = launch_expand<OffT>(G->shape, a, G->grid, cs);
+  if (a.fbm[0]) launch_unpack_level<OffT>(G->g, a, cs);  // frontier-bitmap mode
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
   cudaStreamDestroy(cs);
@@ -232,7 +240,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
   if (persistent)
     launch_init_persist<OffT>(G->g, root, dl, dp, ws, st);
   else
-    launch_init_single<OffT>(G->g, root, dl, dp, ws, st);
+    launch_init_single<OffT>(G->g, root, dl, dp, ws, st, G->frontier_mode != BFS_FRONTIER_LIST);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "init kernel");
   if ((e = cudaEventRecord(ws.ev_mid, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if (persistent) {
@@ -257,6 +265,8 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     pa.probe_mode = G->probe_mode;
     pa.spin_limit = G->wait_limit;
     pa.old_id = G->g.old_id;
+    pa.bitmap_mode = G->frontier_mode != BFS_FRONTIER_LIST;
+    pa.list_cap = frontier_list_cap(G->frontier_mode, G->g.n);
     int& pg = G->pgrid[G->bottom_up ? 1 : 0];
     if (!pg) {
       pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
@@ -268,6 +278,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     ExpandArgs<OffT> a = make_args<OffT>(G, ws.bitmap);
     for (int64_t it = 0; it <= G->g.n; ++it) {
       if ((e = launch_expand<OffT>(G->shape, a, G->grid, st)) != cudaSuccess) return cuda_fail(e, "expand kernel");
+      if (a.fbm[0]) launch_unpack_level<OffT>(G->g, a, st);  // frontier-bitmap mode
       if ((e = cudaMemcpyAsync(&ws.ctl_host->cont, &ws.ctl->cont, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
           cudaSuccess)
         return cuda_fail(e, "level flag copy");
@@ -312,6 +323,7 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
       const long long edges2 = persistent ? ws.pctl_host->edges2 : ws.ctl_host->edges2;
       stats->depth = depth;
       stats->bottom_up_levels = persistent ? ws.pctl_host->steps_bottom_up : 0;
+      G->last_unpacked = persistent ? ws.pctl_host->unpacked_levels : -1;
       stats->vertices_reached = reached;
       stats->edges_traversed = edges2 / 2;
       stats->device_ms = ms;
@@ -340,6 +352,47 @@ static bfs_status expand_one(bfs_graph_s* G, const int32_t* front, int64_t nf, i
   if (c.error & kErrFrontierRange) return fail(BFS_ERR_INVALID_ARG, "a frontier vertex is outside [0, n)");
   if (c.error & kErrCounterOverflow) return fail(BFS_ERR_INVALID_ARG, "frontier edge total exceeds capacity");
   if (c.error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
+  return BFS_OK;
+}
+
+// One level producing its next frontier as a bitmap only (the list cap is -1: no appends),
+// then, if `next` is given, the warp-centric unpack of that bitmap into a list.
+template <typename OffT>
+static bfs_status expand_bitmap_one(bfs_graph_s* G, const int32_t* front, int64_t nf, int32_t level, uint32_t* bitmap,
+                                    int32_t* levels, int32_t* parents, uint32_t* next_bitmap, int32_t* next,
+                                    int64_t* next_count, cudaStream_t st) {
+  SingleWs& ws = G->ws;
+  cudaError_t e;
+  if (G->last_done) cudaStreamWaitEvent(st, G->last_done, 0);
+  const size_t words = (size_t)(G->g.n + 31) / 32;
+  if ((e = cudaMemsetAsync(next_bitmap, 0, words * sizeof(uint32_t), st)) != cudaSuccess)
+    return cuda_fail(e, "memset");
+  if (nf > 0) {
+    launch_scan_frontier<OffT>(G->g, front, nf, level, levels, parents, ws, st);
+    ExpandArgs<OffT> a = make_args<OffT>(G, bitmap);
+    const int nxt = level & 1;  // the expansion of `level` writes parity level & 1
+    a.fbm[0] = a.fbm[1] = nullptr;
+    a.fbm[nxt] = next_bitmap;
+    a.list_cap = -1;  // bitmap only
+    if ((e = cudaMemsetAsync(&ws.ctl->dropped, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_expand<OffT>(G->shape, a, G->grid, st)) != cudaSuccess) return cuda_fail(e, "expand kernel");
+  }
+  launch_write_count(ws.ctl, G->g.pk, next_count, st);
+  if (nf == 0 && (e = cudaMemsetAsync(next_count, 0, sizeof(int64_t), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemcpyAsync(ws.ctl_host, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "control copy");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "expand");
+  const Ctl& c = *ws.ctl_host;
+  if (nf > 0) {
+    if (c.error & kErrFrontierRange) return fail(BFS_ERR_INVALID_ARG, "a frontier vertex is outside [0, n)");
+    if (c.error & kErrCounterOverflow) return fail(BFS_ERR_INVALID_ARG, "frontier edge total exceeds capacity");
+    if (c.error & kErrColumnRange) return fail(BFS_ERR_INVALID_GRAPH, "a column id outside [0, n) was met");
+  }
+  if (next && (e = unpack_bitmap_to_list<OffT>(G->g, ws, level & 1, next_bitmap, next, next_count, st)) != cudaSuccess)
+    return cuda_fail(e, "bitmap unpack");
+  if (!G->last_done && (e = cudaEventCreateWithFlags(&G->last_done, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate");
+  cudaEventRecord(G->last_done, st);
   return BFS_OK;
 }
 
@@ -579,6 +632,14 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
         G->pgrid[0] = G->pgrid[1] = 0;
       }
       return BFS_OK;
+    case BFS_OPT_FRONTIER:
+      if (value < BFS_FRONTIER_LIST || value > BFS_FRONTIER_BITMAP) return fail(BFS_ERR_INVALID_ARG, "unknown frontier mode");
+      if (G->frontier_mode != (int)value) {
+        if (G->last_done) cudaEventSynchronize(G->last_done);
+        G->frontier_mode = (int)value;
+        set_single_shape(G, G->shape);  // the captured level loop holds the old mode
+      }
+      return BFS_OK;
     case BFS_OPT_PROBE:
       if (value < 0 || value > 1) return fail(BFS_ERR_INVALID_ARG, "probe mode outside [0, 1]");
       if (G->probe_mode != (int)value) {
@@ -603,6 +664,10 @@ GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* val
     case BFS_OPT_PROBE: *value = G->probe_mode; return BFS_OK;
     case BFS_OPT_PERSIST_CTAS: *value = G->persist_ctas; return BFS_OK;
     case BFS_OPT_RELABELED: *value = G->g.new_id != nullptr; return BFS_OK;
+    case BFS_OPT_FRONTIER: *value = G->frontier_mode; return BFS_OK;
+    case BFS_OPT_UNPACKED_LEVELS: *value = G->last_unpacked; return BFS_OK;
+    case BFS_OPT_WAVE_LEVELS: *value = batch_last_levels(G); return BFS_OK;
+    case BFS_OPT_WAVE_OVERFLOW: *value = batch_last_overflow(G); return BFS_OK;
   }
   return fail(BFS_ERR_INVALID_ARG, "unknown option");
 }
@@ -648,6 +713,30 @@ GBFS_API bfs_status bfs_run(bfs_graph_t G, int32_t root, int32_t* levels, int32_
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return G->g.off64 ? run_single<int64_t>(G, root, levels, parents, st, stats)
                     : run_single<int32_t>(G, root, levels, parents, st, stats);
+}
+
+GBFS_API bfs_status bfs_expand_bitmap(bfs_graph_t G, const int32_t* frontier, int64_t n_frontier, int32_t level,
+                                      uint32_t* bitmap, int32_t* levels, int32_t* parents, uint32_t* next_bitmap,
+                                      int32_t* next, int64_t* next_count, void* stream) {
+  t_last_error.clear();
+  if (!G) return fail(BFS_ERR_INVALID_ARG, "graph is NULL");
+  if (n_frontier < 0 || n_frontier > G->g.n) return fail(BFS_ERR_INVALID_ARG, "n_frontier outside [0, n]");
+  if (n_frontier > 0 && !frontier) return fail(BFS_ERR_INVALID_ARG, "frontier is NULL");
+  if (!bitmap || !levels || !parents || !next_bitmap || !next_count) return fail(BFS_ERR_INVALID_ARG, "NULL output");
+  if (level < 1) return fail(BFS_ERR_INVALID_ARG, "level must be >= 1");
+  if (G->g.new_id)
+    return fail(BFS_ERR_INVALID_ARG,
+                "bfs_expand_bitmap works in the graph's own numbering: create it without BFS_RELABEL_DEGREE");
+  std::lock_guard<std::mutex> lock(G->mu);
+  cudaError_t e = cudaSetDevice(G->g.device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  bfs_status s = ensure_single_ws(G);
+  if (s != BFS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return G->g.off64 ? expand_bitmap_one<int64_t>(G, frontier, n_frontier, level, bitmap, levels, parents, next_bitmap,
+                                                 next, next_count, st)
+                    : expand_bitmap_one<int32_t>(G, frontier, n_frontier, level, bitmap, levels, parents, next_bitmap,
+                                                 next, next_count, st);
 }
 
 GBFS_API bfs_status bfs_expand(bfs_graph_t G, const int32_t* frontier, int64_t n_frontier, int32_t level,

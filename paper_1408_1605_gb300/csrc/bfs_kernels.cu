@@ -40,7 +40,7 @@ namespace gbfs {
 template <typename OffT>
 __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t root, const int32_t* new_id,
                               int32_t* levels, int32_t* parents, uint32_t* bitmap, FrontierBuf<OffT> f0,
-                              TileDesc<OffT>* chunk0, Ctl* ctl, Packed pk) {
+                              TileDesc<OffT>* chunk0, Ctl* ctl, Packed pk, uint32_t* fbm0, uint32_t* fbm1) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < n; i += stride) {  // outputs are indexed by caller ids
@@ -50,7 +50,13 @@ __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t r
   }
   const int32_t rn = new_id ? new_id[root] : root;  // the root's internal id
   const int64_t nw = (n + 31) / 32;
-  for (int64_t w = tid; w < nw; w += stride) bitmap[w] = (w == (rn >> 5)) ? (1u << (rn & 31)) : 0u;
+  for (int64_t w = tid; w < nw; w += stride) {
+    bitmap[w] = (w == (rn >> 5)) ? (1u << (rn & 31)) : 0u;
+    if (fbm0) {  // frontier-bitmap mode: next-frontier bitmaps start cleared
+      fbm0[w] = 0u;
+      fbm1[w] = 0u;
+    }
+  }
   const OffT o0 = off[rn], deg = off[rn + 1] - o0;
   // chunk starts of the root's row, spread over the grid (a hub root spans many chunks)
   const int64_t nchunks = ((int64_t)deg + kChunk - 1) / kChunk;
@@ -70,6 +76,8 @@ __global__ void k_init_single(const OffT* __restrict__ off, int64_t n, int32_t r
     ctl->cont = deg > 0;
     ctl->levels = levels;
     ctl->parents = parents;
+    ctl->dropped = 0;
+    ctl->bm_counter = 0;
   }
 }
 
@@ -206,7 +214,31 @@ struct LevelIO {
   const int32_t* old_id;            // internal -> caller id for the outputs (NULL: identity)
   int64_t nf;                       // current frontier size
   OffT r;                           // current frontier's degree sum
+  long long list_cap;               // frontier-bitmap mode: most list entries (kNoListCap: list only)
+  unsigned* dropped;                // set when a claim was left out of the list (bitmap only)
 };
+
+constexpr long long kNoListCap = 0x7fffffffffffffffll;
+
+// Frontier-bitmap mode, per warp: keep appending claims to the next-frontier list while the
+// list stays within the cap; past it, record that the level dropped its list and only count
+// the claims (they are all in the next-frontier bitmap). Returns whether to append.
+template <typename OffT>
+__device__ __forceinline__ bool keep_listing(const LevelIO<OffT>& io, Packed pk, int pending) {
+  if (io.list_cap == kNoListCap) return true;
+  unsigned long long c = 0;
+  if ((threadIdx.x & 31) == 0) c = *(volatile unsigned long long*)io.counter_out;
+  c = __shfl_sync(0xffffffffu, c, 0);
+  return pk.count(c) + pending <= io.list_cap;
+}
+
+template <typename OffT>
+__device__ __forceinline__ void count_only(const LevelIO<OffT>& io, Packed pk, int claims) {
+  if ((threadIdx.x & 31) == 0 && claims > 0) {
+    *(volatile unsigned*)io.dropped = 1u;
+    atomicAdd(io.counter_out, pk.make(claims, 0));
+  }
+}
 
 // Appends the CTA's buffered claims to the next frontier: one 64-bit atomic reserves the
 // slots and the exclusive-scan range of their degrees (Sec. 3.4 scan, fused).
@@ -243,6 +275,28 @@ __device__ __forceinline__ void flush_claims(const OffT* off, Packed pk, const L
     write_descs_warp(io.chunk_out, valid, run, d, slot, vc, b);
     run += d;
   }
+}
+
+// The CTA's buffered claims: appended (flush_claims) while the list stays within the cap of
+// the frontier-bitmap mode, else only counted. Every thread of the CTA calls it.
+template <typename OffT, int BLOCK, int CLAIM>
+__device__ __forceinline__ void cta_flush_or_count(const OffT* off, Packed pk, const LevelIO<OffT>& io,
+                                                   int2* s_claim, int nc, ExpandShared<OffT>& sh) {
+  if (io.list_cap != kNoListCap) {
+    if (threadIdx.x == 0) {
+      const unsigned long long c = *(volatile unsigned long long*)io.counter_out;
+      sh.klo = pk.count(c) + nc <= io.list_cap;
+      if (!sh.klo) {
+        *(volatile unsigned*)io.dropped = 1u;
+        atomicAdd(io.counter_out, pk.make(nc, 0));
+      }
+    }
+    __syncthreads();
+    const bool listing = sh.klo != 0;
+    __syncthreads();
+    if (!listing) return;
+  }
+  flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
 }
 
 // A claim buffered by a warp: everything the append needs, so that it reads nothing more
@@ -428,14 +482,14 @@ __device__ void td_level(const OffT* __restrict__ off, const int32_t* __restrict
     __syncthreads();
     const int nc = sh.nclaim;
     if (nc > CLAIM - T) {
-      flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
+      cta_flush_or_count<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
       __syncthreads();
       if (threadIdx.x == 0) sh.nclaim = 0;
     }
   }
   __syncthreads();
   const int nc = sh.nclaim;
-  if (nc > 0) flush_claims<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
+  if (nc > 0) cta_flush_or_count<OffT, BLOCK, CLAIM>(off, pk, io, s_claim, nc, sh);
   __syncthreads();
 }
 
@@ -559,8 +613,16 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       if (b) wc |= 1u << j;
       tot += __popc(b);
     }
+    // Frontier-bitmap mode: past the list cap the claims are only counted (they are in the
+    // next-frontier bitmap), and the buffered ones with them.
+    bool listing = true;
+    if (wc && !keep_listing(io, pk, nc + tot)) {
+      listing = false;
+      count_only(io, pk, nc + tot);
+      nc = 0;
+    }
     // Room for this tile's claims first, while few registers are live.
-    if (nc + tot > WCAP) {
+    if (listing && nc + tot > WCAP) {
       __syncwarp();
       warp_flush<OffT, P>(pk, io, sm.claim, nc);
       nc = 0;
@@ -574,8 +636,10 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       ov[j] = vv[j];
       if ((wc >> j) & 1u) {
         if (claimed[j]) {
-          o0[j] = off[vv[j]];
-          o1[j] = off[vv[j] + 1];
+          if (listing) {
+            o0[j] = off[vv[j]];
+            o1[j] = off[vv[j] + 1];
+          }
           if (io.old_id) ov[j] = __ldg(io.old_id + vv[j]);
         }
       }
@@ -588,15 +652,86 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
           io.parents[ov[j]] = uu[j];
           if (io.fbm_out) atomicOr(io.fbm_out + (vv[j] >> 5), 1u << (vv[j] & 31));
         }
-        const unsigned b = __ballot_sync(full, claimed[j]);
-        if (claimed[j])
-          sm.claim[nc + __popc(b & lanemask_lt())] = ClaimRec<OffT>{ov[j], (int32_t)(o1[j] - o0[j]), o0[j]};
-        nc += __popc(b);
+        if (listing) {
+          const unsigned b = __ballot_sync(full, claimed[j]);
+          if (claimed[j])
+            sm.claim[nc + __popc(b & lanemask_lt())] = ClaimRec<OffT>{ov[j], (int32_t)(o1[j] - o0[j]), o0[j]};
+          nc += __popc(b);
+        }
       }
     }
   }
   __syncwarp();
-  if (nc > 0) warp_flush<OffT, P>(pk, io, sm.claim, nc);
+  if (nc > 0) {
+    if (keep_listing(io, pk, nc))
+      warp_flush<OffT, P>(pk, io, sm.claim, nc);
+    else
+      count_only(io, pk, nc);
+  }
+}
+
+// Frontier-bitmap unpack (the paper's warp-centric unpacking of a vertex bitmap into a
+// list, Sec. 5): rounds of blockDim.x bitmap words per CTA, thread t taking word t of its
+// round. A block scan of the words' vertex counts and degree sums gives each thread its
+// place; one 64-bit atomicAdd per round on `counter` reserves the CTA's list slots and edge
+// range (the same packed (count, edges) word as the expansion's appends), and the entries
+// of a round are written in vertex order: id (caller numbering), scan value, column base and
+// the tile descriptors of every kChunk-th edge, a warp-wide loop over the set bits. With
+// `clear`, the words are zeroed as they are read. Every thread of the CTA calls it.
+template <typename OffT>
+__device__ void unpack_bitmap(const OffT* __restrict__ off, const int32_t* old_id, uint32_t* fbm, int64_t n,
+                              Packed pk, FrontierBuf<OffT> out, TileDesc<OffT>* chunk_out,
+                              unsigned long long* counter, bool clear, ExpandShared<OffT>& sh, int64_t round0,
+                              int64_t rstride) {
+  const int64_t nwords = (n + 31) / 32;
+  const unsigned full = 0xffffffffu;
+  for (int64_t round = round0; round * blockDim.x < nwords; round += rstride) {
+    const int64_t w = round * blockDim.x + threadIdx.x;
+    uint32_t word = 0;
+    if (w < nwords) {
+      word = fbm[w];
+      if (clear && word) fbm[w] = 0u;
+    }
+    OffT cnt = (OffT)__popc(word), dsum = 0;
+    for (uint32_t rem = word; rem; rem &= rem - 1) {
+      const int64_t v = w * 32 + __ffs(rem) - 1;
+      dsum += off[v + 1] - off[v];
+    }
+    OffT tot_cnt, tot_deg;
+    const OffT ex_cnt = block_exclusive_scan(cnt, sh.warp, &tot_cnt);
+    const OffT ex_deg = block_exclusive_scan(dsum, sh.warp, &tot_deg);
+    if (tot_cnt == 0) continue;  // block-uniform
+    if (threadIdx.x == 0) sh.resv = atomicAdd(counter, pk.make((long long)tot_cnt, (long long)tot_deg));
+    __syncthreads();
+    const unsigned long long resv = sh.resv;
+    __syncthreads();
+    int64_t slot = pk.count(resv) + (int64_t)ex_cnt;
+    OffT run = (OffT)pk.edges(resv) + ex_deg;
+    // uniform trip count per warp: the descriptor writes are warp-collective
+    const int qmax = __reduce_max_sync(full, (unsigned)cnt);
+    uint32_t rem = word;
+    for (int q = 0; q < qmax; ++q) {
+      const bool valid = rem != 0;
+      int32_t v = 0, vc = 0;
+      OffT d = 0, b = 0;
+      if (valid) {
+        v = (int32_t)(w * 32 + __ffs(rem) - 1);
+        rem &= rem - 1;
+        const OffT o0 = off[v];
+        d = off[v + 1] - o0;
+        vc = old_id ? __ldg(old_id + v) : v;
+        b = o0 - run;
+        out.v[slot] = vc;
+        out.cum[slot] = run;
+        out.base[slot] = b;
+      }
+      write_descs_warp(chunk_out, valid, run, d, (int32_t)slot, vc, b);
+      if (valid) {
+        ++slot;
+        run += d;
+      }
+    }
+  }
 }
 
 // Dynamic shared memory of an expansion shape: CTA tiles (staging + CTA claim buffer) or
@@ -624,12 +759,14 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand(ExpandArgs<OffT> 
   io.counter_out = &ctl->counter[nxt];
   io.levels = *(int32_t* volatile*)&ctl->levels;
   io.parents = *(int32_t* volatile*)&ctl->parents;
-  io.fbm_out = nullptr;
+  io.fbm_out = a.fbm[nxt];  // NULL unless in frontier-bitmap mode
   io.L = L;
   io.probe_mode = a.probe_mode;
   io.old_id = a.old_id;
   io.nf = a.pk.count(pc);
   io.r = (OffT)a.pk.edges(pc);
+  io.list_cap = a.fbm[nxt] ? a.list_cap : kNoListCap;
+  io.dropped = &ctl->dropped;
   if constexpr (WT) {
     auto* wsm = reinterpret_cast<WarpTileSmem<OffT, E, CLAIM>*>(smem) + (threadIdx.x >> 5);
     td_level_warp<OffT, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &ctl->error, io, *wsm,
@@ -658,7 +795,44 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand(ExpandArgs<OffT> 
       ctl->done[cur] = 0;
       ctl->level = L + 1;
       ctl->cont = nn > 0;
+      ctl->bm_counter = 0;  // the unpack after this level, if the level dropped its list
       if (a.use_cond) cudaGraphSetConditional(a.cond, nn > 0 ? 1u : 0u);
+    }
+  }
+}
+
+// After an expansion in frontier-bitmap mode (graph or host loop): if the level dropped its
+// list, rebuild the next frontier (list, scan, descriptors) from its bitmap, which is cleared
+// on the way; else just clear the bitmap. The last CTA installs the rebuilt counter.
+template <typename OffT>
+__global__ void __launch_bounds__(256) k_unpack_level(ExpandArgs<OffT> a) {
+  __shared__ ExpandShared<OffT> sh;
+  Ctl* ctl = a.ctl;
+  const int par = (*(volatile int*)&ctl->level - 1) & 1;  // parity of the next expansion's input
+  uint32_t* fbm = a.fbm[par];
+  const bool dropped = *(volatile unsigned*)&ctl->dropped != 0;
+  if (dropped) {
+    unpack_bitmap<OffT>(a.off, a.old_id, fbm, a.n, a.pk, a.fr[par], a.chunk[par], &ctl->bm_counter, true, sh,
+                        blockIdx.x, gridDim.x);
+  } else {
+    const int64_t nwords = (a.n + 31) / 32;
+    uint4* p = reinterpret_cast<uint4*>(fbm);
+    const int64_t nv = nwords / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+      p[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = nv * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+         i += (int64_t)gridDim.x * blockDim.x)
+      fbm[i] = 0u;
+    return;  // grid-uniform: no counter to install
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->done[par], 1u) == gridDim.x - 1) {
+      __threadfence();
+      ctl->counter[par] = *(volatile unsigned long long*)&ctl->bm_counter;
+      ctl->done[par] = 0;
+      ctl->dropped = 0;
     }
   }
 }
@@ -817,11 +991,14 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU && TPS > 1024 ? 1024 : TPS) / 
         bottom_up = !(nf * (long long)a.beta < a.n && nf < prev_nf);
     }
     prev_nf = nf;
+    const bool keep_fbm = WITH_BU || a.bitmap_mode;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       c->counter[old3] = 0;
       c->steps_bottom_up += bottom_up ? 1 : 0;
+      c->dropped[nxt3] = 0;     // for level it + 1 (last read before level it - 1 ended)
+      c->bm_counter[nxt3] = 0;
     }
-    if (WITH_BU)
+    if (keep_fbm)
       for (int64_t w = gtid; w < nwords; w += gstride) a.fbm[old3][w] = 0u;  // collects level it + 2
     LevelIO<OffT> io;
     io.in = a.fr[it & 1];
@@ -831,12 +1008,14 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU && TPS > 1024 ? 1024 : TPS) / 
     io.counter_out = &c->counter[nxt3];
     io.levels = a.levels;
     io.parents = a.parents;
-    io.fbm_out = WITH_BU ? a.fbm[nxt3] : nullptr;
+    io.fbm_out = keep_fbm ? a.fbm[nxt3] : nullptr;
     io.L = it + 1;
     io.probe_mode = a.probe_mode;
     io.old_id = a.old_id;
     io.nf = nf;
     io.r = (OffT)r;
+    io.list_cap = (a.bitmap_mode && !bottom_up) ? a.list_cap : kNoListCap;
+    io.dropped = &c->dropped[cur3];
     if (WITH_BU && bottom_up)
       bu_level<OffT, BU_WCAP>(a.off, a.cols, a.bitmap, a.fbm[cur3], a.n, a.pk, io, bu_buf,
                               (int64_t)blockIdx.x * (BLOCK / 32) + warp, (int64_t)gridDim.x * (BLOCK / 32));
@@ -847,6 +1026,20 @@ __global__ void __launch_bounds__(BLOCK, (WITH_BU && TPS > 1024 ? 1024 : TPS) / 
       td_level<OffT, BLOCK, E, CLAIM>(a.off, a.cols, a.bitmap, a.n, a.pk, &c->error, io, smem, sh, blockIdx.x,
                                       gridDim.x);
     grid_barrier(c, gridDim.x, a.spin_limit);
+    if (a.bitmap_mode) {
+      // the level dropped its list: rebuild it from the next-frontier bitmap (kept: a
+      // bottom-up level reads it), then every CTA installs the rebuilt counter
+      if (threadIdx.x == 0) s_stop = *(volatile unsigned*)&c->dropped[cur3] != 0;
+      __syncthreads();
+      if (s_stop) {
+        unpack_bitmap<OffT>(a.off, a.old_id, a.fbm[nxt3], a.n, a.pk, a.fr[(it + 1) & 1], a.chunk[(it + 1) & 1],
+                            &c->bm_counter[cur3], false, sh, blockIdx.x, gridDim.x);
+        grid_barrier(c, gridDim.x, a.spin_limit);
+        if (threadIdx.x == 0) c->counter[nxt3] = *(volatile unsigned long long*)&c->bm_counter[cur3];
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->unpacked_levels += 1;
+      }
+      __syncthreads();
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (it < kMaxLevelTimes) {
         unsigned long long ns;
@@ -902,6 +1095,11 @@ __global__ void k_init_persist(const OffT* __restrict__ off, int64_t n, int32_t 
     c->reached = 1;
     c->edges2 = 0;
     c->steps_bottom_up = 0;
+    c->unpacked_levels = 0;
+    for (int i = 0; i < 3; ++i) {
+      c->bm_counter[i] = 0;
+      c->dropped[i] = 0;
+    }
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(c->start_ns));
   }
 }
@@ -921,11 +1119,51 @@ void launch_write_count(Ctl* ctl, Packed pk, int64_t* out, cudaStream_t st) {
 
 template <typename OffT>
 void launch_init_single(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool clear_fbm) {
   const int block = 256;
   const int grid = g.num_sms * 8;
   k_init_single<OffT><<<grid, block, 0, st>>>(reinterpret_cast<const OffT*>(g.off), g.n, root, g.new_id, levels,
-                                               parents, ws.bitmap, ws.fr<OffT>(0), ws.desc<OffT>(0), ws.ctl, g.pk);
+                                               parents, ws.bitmap, ws.fr<OffT>(0), ws.desc<OffT>(0), ws.ctl, g.pk,
+                                               clear_fbm ? ws.fbm[0] : nullptr, clear_fbm ? ws.fbm[1] : nullptr);
+}
+
+template <typename OffT>
+void launch_unpack_level(const GraphDev& g, const ExpandArgs<OffT>& a, cudaStream_t st) {
+  k_unpack_level<OffT><<<g.num_sms * 4, 256, 0, st>>>(a);
+}
+
+// Unpack of a caller's bitmap into the workspace frontier of parity `par` (bfs_expand_bitmap):
+// the vertex list is copied out to `next` and its length to *count_dev.
+template <typename OffT>
+__global__ void __launch_bounds__(256) k_unpack_caller(const OffT* __restrict__ off, uint32_t* bitmap, int64_t n,
+                                                       Packed pk, FrontierBuf<OffT> out, TileDesc<OffT>* chunk,
+                                                       unsigned long long* counter) {
+  __shared__ ExpandShared<OffT> sh;
+  unpack_bitmap<OffT>(off, nullptr, bitmap, n, pk, out, chunk, counter, false, sh, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_count_out(const unsigned long long* counter, Packed pk, int64_t* out) {
+  *out = pk.count(*counter);
+}
+
+template <typename OffT>
+cudaError_t unpack_bitmap_to_list(const GraphDev& g, SingleWs& ws, int par, const uint32_t* bitmap, int32_t* next,
+                                  int64_t* count_dev, cudaStream_t st) {
+  unsigned long long* counter = &ws.ctl->bm_counter;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_unpack_caller<OffT><<<g.num_sms * 4, 256, 0, st>>>(reinterpret_cast<const OffT*>(g.off),
+                                                        const_cast<uint32_t*>(bitmap), g.n, g.pk, ws.fr<OffT>(par),
+                                                        ws.desc<OffT>(par), counter);
+  k_count_out<<<1, 1, 0, st>>>(counter, g.pk, count_dev);
+  int64_t count = 0;
+  if ((e = cudaMemcpyAsync(&count, count_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return e;
+  if (count > 0 && (e = cudaMemcpyAsync(next, ws.v[par], sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToDevice,
+                                        st)) != cudaSuccess)
+    return e;
+  return cudaStreamSynchronize(st);
 }
 
 template <typename OffT>
@@ -1069,8 +1307,14 @@ int expand_grid(int shape, int num_sms) {
   return num_sms;
 }
 
-template void launch_init_single<int32_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
-template void launch_init_single<int64_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t);
+template void launch_init_single<int32_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t, bool);
+template void launch_init_single<int64_t>(const GraphDev&, int32_t, int32_t*, int32_t*, SingleWs&, cudaStream_t, bool);
+template void launch_unpack_level<int32_t>(const GraphDev&, const ExpandArgs<int32_t>&, cudaStream_t);
+template void launch_unpack_level<int64_t>(const GraphDev&, const ExpandArgs<int64_t>&, cudaStream_t);
+template cudaError_t unpack_bitmap_to_list<int32_t>(const GraphDev&, SingleWs&, int, const uint32_t*, int32_t*,
+                                                    int64_t*, cudaStream_t);
+template cudaError_t unpack_bitmap_to_list<int64_t>(const GraphDev&, SingleWs&, int, const uint32_t*, int32_t*,
+                                                    int64_t*, cudaStream_t);
 template void launch_scan_frontier<int32_t>(const GraphDev&, const int32_t*, int64_t, int32_t, int32_t*,
                                             int32_t*, SingleWs&, cudaStream_t);
 template void launch_scan_frontier<int64_t>(const GraphDev&, const int32_t*, int64_t, int32_t, int32_t*,

@@ -38,6 +38,8 @@ struct bfs_graph_s {
   int probe_mode = 1;       // bitmap pre-check through L2 (1) or default caching (0)
   long long wait_limit = 1ll << 27;  // grid-barrier polls before a wait gives up
   int persist_ctas = 0;     // CTAs per SM of a persistent search (0: as many as fit)
+  int frontier_mode = 0;    // BFS_FRONTIER_LIST / _AUTO / _BITMAP
+  long long last_unpacked = -1;  // levels unpacked from a bitmap by the last persistent search
   int pgrid[2] = {0, 0};    // CTAs of the persistent kernel (top-down only, with bottom-up)
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
@@ -50,4 +52,6 @@ bfs_status ensure_single_ws(bfs_graph_s* G);
 void set_batch_shape(bfs_graph_s* G, int shape);
 void set_single_shape(bfs_graph_s* G, int shape);
 void destroy_batch_state(bfs_graph_s* G);
+long long batch_last_levels(const bfs_graph_s* G);    // levels of the last wave (0: none yet)
+long long batch_last_overflow(const bfs_graph_s* G);  // its claim records beyond the per-vertex slots
 }  // namespace gbfs

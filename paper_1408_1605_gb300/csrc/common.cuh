@@ -61,6 +61,9 @@ struct Ctl {
   int cont;                  // 1 while the next frontier is non-empty
   int32_t* levels;           // output arrays of the running search
   int32_t* parents;
+  unsigned int dropped;      // frontier-bitmap mode: the level stopped appending to the list
+  int pad;
+  unsigned long long bm_counter;  // packed (count, edges) of the list unpacked from the bitmap
 };
 
 // Control block of a persistent (one-launch) search: counters rotate by 3 so that level
@@ -75,6 +78,9 @@ struct PCtl {
   long long reached;
   long long edges2;
   int steps_bottom_up;
+  int unpacked_levels;                          // levels whose next frontier was unpacked from a bitmap
+  unsigned long long bm_counter[3];             // by level % 3: reservations of the bitmap unpack
+  unsigned int dropped[3];                      // by level % 3: the level stopped appending to the list
   int pad;
   unsigned long long start_ns;                  // device clock when the search was set up
   unsigned long long level_ns[kMaxLevelTimes];  // device clock at the end of each level

@@ -76,6 +76,8 @@ struct ExpandArgs {
   int use_cond;
   int probe_mode;   // bitmap pre-check: 0 default caching, 1 L2 only
   const int32_t* old_id;  // internal -> caller vertex id (NULL: identity)
+  uint32_t* fbm[2];       // next-frontier bitmaps by level parity (frontier-bitmap mode), else NULL
+  long long list_cap;     // frontier-bitmap mode: most list entries a level appends (-1: none)
 };
 
 template <typename OffT>
@@ -98,6 +100,8 @@ struct PersistArgs {
   int probe_mode;
   long long spin_limit;  // polls of a grid-barrier wait before it gives up (kErrTimeout)
   const int32_t* old_id;  // internal -> caller vertex id (NULL: identity)
+  int bitmap_mode;        // frontier-bitmap mode: top-down levels also record claims in fbm
+  long long list_cap;     // most list entries a top-down level appends (-1: none) in that mode
 };
 
 struct ExpandShape {
@@ -107,9 +111,30 @@ struct ExpandShape {
 extern const ExpandShape kExpandShapes[];
 extern const int kNumExpandShapes;
 
+// Frontier-bitmap mode (the paper's list-or-bitmap switch, Sec. 5): a top-down level
+// appends to the next-frontier list only while it holds at most list_cap entries, the
+// point past which a list of 32-bit ids is larger than an n-bit bitmap; every claim is also
+// set in the next-frontier bitmap, and a level that stopped appending has its list rebuilt
+// from the bitmap afterwards.
+inline long long frontier_list_cap(int mode, int64_t n) {
+  return mode == 2 ? -1 : (n + 31) / 32;  // 1: auto (list bits > n switches), 2: bitmap always
+}
+
+// After an expansion of a level-loop launch (graph or host loop): when the level dropped
+// its list, rebuild the next frontier from the bitmap (vertex order, warp-centric unpack);
+// in every case leave the bitmap cleared for reuse.
+template <typename OffT>
+void launch_unpack_level(const GraphDev& g, const ExpandArgs<OffT>& a, cudaStream_t st);
+// The same unpack on caller state (bfs_expand_bitmap): the vertices of `bitmap` as a list
+// (next[0 .. *count)), plus the scan and tile descriptors in the workspace buffers of parity
+// `par`. Synchronous.
+template <typename OffT>
+cudaError_t unpack_bitmap_to_list(const GraphDev& g, SingleWs& ws, int par, const uint32_t* bitmap, int32_t* next,
+                                  int64_t* count_dev, cudaStream_t st);
+
 template <typename OffT>
 void launch_init_single(const GraphDev& g, int32_t root, int32_t* levels, int32_t* parents, SingleWs& ws,
-                        cudaStream_t st);
+                        cudaStream_t st, bool clear_fbm = false);
 template <typename OffT>
 void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, int32_t level, int32_t* levels,
                           int32_t* parents, SingleWs& ws, cudaStream_t st);

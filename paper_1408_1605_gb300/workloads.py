@@ -91,6 +91,9 @@ WORKLOADS = {w.name: w for w in [
              description="R-MAT scale 26, edge factor 16, 64 roots (int64 offsets in; the library narrows them to int32 when the cleaned entry count fits)"),
     Workload("uniform-s26-ef16", "uniform", 26, group=2, roots=64,
              description="uniform G(n, m), n = 2^26, m = 16 n, 64 roots"),
+    Workload("rmat-s26-ef17", "rmat", 26, edge_factor=17, group=5, roots=64,
+             description="R-MAT scale 26, edge factor 17: more than 2^31 - 1 CSR entries after cleaning, so the "
+                         "row offsets, scan values and tile descriptors stay 64-bit"),
     Workload("rmat-s24-ef16", "rmat", 24, group=4, roots=64, description="R-MAT scale 24, edge factor 16"),
     Workload("rmat-s20-ef16", "rmat", 20, group=4, roots=64, description="R-MAT scale 20, edge factor 16"),
     Workload("grid3d-192", "grid3d", dims=(192, 192, 192), group=4, roots=64, description="3D grid 192^3"),

@@ -258,6 +258,114 @@ def test_expand_one_level(torch_cuda, oracle_mod, graphs_mod, force64):
         capi.bfs_graph_destroy(h)
 
 
+@pytest.mark.parametrize("force64", [False, True])
+@pytest.mark.parametrize("shape", [1, 7])
+def test_expand_one_level_to_bitmap(torch_cuda, oracle_mod, graphs_mod, force64, shape):
+    """The expansion that hands over its next frontier as a bitmap (Sec. 5) and the
+    warp-centric unpack of that bitmap into a list, against the oracle's one-level step, on
+    frontiers with repeated vertices, zero-degree vertices, a hub and ragged sizes, for a
+    CTA-tile shape and a warp-tile shape: bitmap bit-exact, list = the same set, each
+    vertex once, ascending within runs."""
+    from paper_1408_1605_gb300 import capi
+
+    torch = torch_cuda
+    g = graphs_mod.rmat(15, 16, seed=21)
+    deg = g.degrees()
+    rng = np.random.default_rng(6)
+    zero = np.flatnonzero(deg == 0)
+    hub = int(np.argmax(deg))
+    h = _upload(capi, g, force64, shape=shape)
+    words = (g.n + 31) // 32
+    try:
+        cases = [
+            np.array([hub], dtype=np.int32),
+            np.array([hub, hub, int(zero[0]), hub], dtype=np.int32),
+            rng.choice(g.n, 1, replace=False).astype(np.int32),
+            rng.choice(g.n, 777, replace=False).astype(np.int32),
+            np.concatenate([zero[:3000], rng.choice(g.n, 3000)]).astype(np.int32),
+            rng.choice(g.n, 20000, replace=False).astype(np.int32),
+        ]
+        for level, front in enumerate(cases, start=1):
+            visited = np.union1d(rng.choice(g.n, g.n // 3, replace=False), front)
+            bm, lv, pr = _expand_state(torch, g, visited, level - 1)
+            ref_bm, ref_lv, ref_pr = bm.copy(), lv.copy(), pr.copy()
+            ref_next = oracle_mod.expand_level(g.offsets, g.cols, front, level, ref_bm, ref_lv, ref_pr)
+            want_bits = np.zeros(words, dtype=np.uint32)
+            np.bitwise_or.at(want_bits, ref_next // 32, (np.uint32(1) << (ref_next % 32).astype(np.uint32)))
+            d_front = torch.from_numpy(front).cuda()
+            d_bm = torch.from_numpy(bm.view(np.int32)).cuda()
+            d_lv = torch.from_numpy(lv).cuda()
+            d_pr = torch.from_numpy(pr).cuda()
+            d_nbm = torch.full((words,), -1, dtype=torch.int32, device="cuda")  # cleared by the call
+            d_next = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+            d_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            capi.bfs_expand_bitmap(h, d_front, front.size, level, d_bm, d_lv, d_pr, d_nbm, d_next, d_cnt)
+            cnt = int(d_cnt.item())
+            assert cnt == ref_next.size
+            assert np.array_equal(d_nbm.cpu().numpy().view(np.uint32), want_bits)
+            nxt = d_next[:cnt].cpu().numpy()
+            assert np.array_equal(np.sort(nxt), np.sort(ref_next))  # each vertex once
+            runs = np.flatnonzero(np.diff(nxt) < 0)  # ascending within each unpacked run
+            assert runs.size <= max(1, words // 64)
+            assert np.array_equal(d_bm.cpu().numpy().view(np.uint32), ref_bm)
+            assert np.array_equal(d_lv.cpu().numpy(), ref_lv)
+            got_pr = d_pr.cpu().numpy()
+            assert np.all(np.delete(got_pr, ref_next) == np.delete(ref_pr, ref_next))
+            fset = set(front.tolist())
+            for v in ref_next[:5000]:
+                p = int(got_pr[v])
+                assert p in fset and v in g.cols[g.offsets[p]:g.offsets[p + 1]]
+            # the bitmap alone (no list)
+            capi.bfs_expand_bitmap(h, d_front, front.size, level, d_bm, d_lv, d_pr, d_nbm, None, d_cnt)
+            assert int(d_cnt.item()) == 0 and not d_nbm.any()  # everything was claimed by the first call
+        # empty frontier
+        d_cnt = torch.full((1,), 5, dtype=torch.int64, device="cuda")
+        capi.bfs_expand_bitmap(h, None, 0, 3, d_bm, d_lv, d_pr, d_nbm, d_next, d_cnt)
+        assert int(d_cnt.item()) == 0 and not d_nbm.any()
+    finally:
+        capi.bfs_graph_destroy(h)
+
+
+FRONTIER_MODES = ("list", "auto", "bitmap")
+
+
+@pytest.mark.parametrize("loop", ["graph", "persistent", "host"])
+@pytest.mark.parametrize("mode", FRONTIER_MODES)
+def test_frontier_modes_end_to_end(torch_cuda, oracle_mod, graphs_mod, loop, mode):
+    """Whole searches with the list-or-bitmap switch off, automatic and forced on, in every
+    level loop, on graphs whose large levels cross the switch (R-MAT, input order and
+    relabelled; uniform) and graphs whose levels never do (grid, path, binary tree), with
+    both offset widths and CTA-tile and warp-tile shapes: levels equal the oracle's, parents
+    valid, m_c equal."""
+    from paper_1408_1605_gb300 import capi
+
+    loops = {"graph": capi.BFS_LOOP_GRAPH, "persistent": capi.BFS_LOOP_PERSISTENT, "host": capi.BFS_LOOP_HOST}
+    modes = {"list": capi.BFS_FRONTIER_LIST, "auto": capi.BFS_FRONTIER_AUTO, "bitmap": capi.BFS_FRONTIER_BITMAP}
+    gs = [(graphs_mod.rmat(17, 16, seed=5), 0), (graphs_mod.rmat(17, 16, seed=5), capi.BFS_RELABEL_DEGREE),
+          (graphs_mod.uniform(50000, 400000, seed=9), 0), (graphs_mod.grid3d(23, 19, 17), 0),
+          (graphs_mod.from_edges(3000, *path_edges(3000)), 0),
+          (graphs_mod.from_edges(4095, *binary_tree_edges(4095)), 0)]
+    for i, (g, relabel) in enumerate(gs):
+        for force64, shape in ((False, 7), (True, 1)):
+            h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64 | relabel
+                                      | (capi.BFS_KEEP_INT64 if force64 else 0))
+            try:
+                capi.bfs_graph_set_shape(h, capi.BFS_KERNEL_SINGLE, shape)
+                capi.bfs_graph_set_option(h, capi.BFS_OPT_LOOP, loops[loop])
+                capi.bfs_graph_set_option(h, capi.BFS_OPT_FRONTIER, modes[mode])
+                assert capi.bfs_graph_get_option(h, capi.BFS_OPT_FRONTIER) == modes[mode]
+                roots = graphs_mod.pick_roots(g, 2, 40 + i)
+                for r in roots:
+                    check_root(capi, oracle_mod, torch_cuda, h, g, int(r))
+                    if loop == "persistent":
+                        unpacked = capi.bfs_graph_get_option(h, capi.BFS_OPT_UNPACKED_LEVELS)
+                        assert (unpacked == 0) if mode == "list" else (unpacked >= 0)
+                        if mode == "bitmap" and g.n > 10000:
+                            assert unpacked >= 1
+            finally:
+                capi.bfs_graph_destroy(h)
+
+
 @pytest.mark.parametrize("scale", [20])
 def test_rmat_larger(torch_cuda, oracle_mod, graphs_mod, scale):
     from paper_1408_1605_gb300 import capi
