@@ -368,6 +368,8 @@ def main() -> int:
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-levels-per-round", type=int, default=0)
+    ap.add_argument("--serve-cohort-wait-us", type=int, default=0,
+                    help="idle wave's wait for a fuller cohort while a sibling runs (0: library default)")
     ap.add_argument("--relabel", default="auto", choices=["auto", "on", "off"],
                     help="BFS_RELABEL_DEGREE at graph creation (auto: R-MAT graphs only)")
     args = ap.parse_args()
@@ -856,7 +858,8 @@ def run_serve(args) -> int:
               for _ in range(n_buf)] for g in gs]
     results = []
     for rate in [float(x) for x in args.serve_rates.split(",")]:
-        srv = capi.bfs_serve_create(memory_cap_bytes=64 << 30, levels_per_round=args.serve_levels_per_round)
+        srv = capi.bfs_serve_create(memory_cap_bytes=64 << 30, levels_per_round=args.serve_levels_per_round,
+                                    cohort_wait_us=args.serve_cohort_wait_us)
         ids = [capi.bfs_serve_add_graph(srv, h) for h in hs]
         nq = int(min(4000, max(200, rate * args.serve_seconds)))
         arrivals, gsel, roots = serving.poisson_schedule(nq, rate, [g.n for g in gs], seed=20140806 + 4)
@@ -897,6 +900,7 @@ def run_serve(args) -> int:
                           "config": {"workload": "serve: rmat-s20, rmat-s24, grid3d-192, uniform-n8M-deg8",
                                      "roots": "seeded uniform per graph", "wave": 64,
                                      "levels_per_round": args.serve_levels_per_round or 8,
+                                     "cohort_wait_us": args.serve_cohort_wait_us or 20000,
                                      "memory_cap_bytes": 64 << 30,
                                      "relabel": args.relabel},
                           "rates": results}), flush=True)

@@ -275,6 +275,10 @@ GBFS_API bfs_status bfs_run_noalloc(const int32_t *row_offsets, const int32_t *c
  *     admission. Queries share row reads only while their searches are in step, so a
  *     running wave admits only while its cohort is young (admit_window); otherwise an idle
  *     wave of the graph starts a new cohort.
+ *   - A wave's cost depends little on how many of its slots are busy (on skewed graphs every
+ *     root's large level covers most of the graph), so an idle wave does not start a cohort
+ *     for a single query while a sibling wave of the graph is running: it waits until the
+ *     pending queries fill a wave or the oldest has waited cohort_wait_us.
  *   - Admission is gated by memory_cap_bytes: the graphs' wave state plus, for each
  *     running query whose outputs are host memory, a device staging buffer of 8 bytes
  *     per vertex. A query waits in the queue until a slot and the memory are free.
@@ -291,7 +295,9 @@ typedef struct bfs_serve_config {
   int32_t admit_window;      /* a running wave admits only while its cohort is at most this
                                 many levels old (0 = 3); raised to a quarter of the graph's
                                 mean query depth on deep graphs */
-  int32_t reserved;
+  int32_t cohort_wait_us;    /* while another wave of the graph is running, an idle wave starts
+                                a new cohort only once max_wave queries are pending or the
+                                oldest has waited this long (0 = 20000; < 0: start at once) */
 } bfs_serve_config;
 
 typedef struct bfs_serve_report {

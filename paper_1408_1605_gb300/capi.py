@@ -60,7 +60,7 @@ class BfsError(RuntimeError):
 class bfs_serve_config(ctypes.Structure):
     _fields_ = [("memory_cap_bytes", ctypes.c_uint64), ("max_wave", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
                 ("levels_per_round", ctypes.c_int32), ("waves_per_graph", ctypes.c_int32),
-                ("admit_window", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("admit_window", ctypes.c_int32), ("cohort_wait_us", ctypes.c_int32)]
 
 
 class bfs_serve_report(ctypes.Structure):
@@ -281,9 +281,10 @@ def bfs_run_noalloc(row_offsets, cols, n_vertices: int, n_entries: int, root: in
 
 
 def bfs_serve_create(memory_cap_bytes: int = 0, max_wave: int = 0, queue_capacity: int = 0,
-                     levels_per_round: int = 0, waves_per_graph: int = 0, admit_window: int = 0) -> int:
+                     levels_per_round: int = 0, waves_per_graph: int = 0, admit_window: int = 0,
+                     cohort_wait_us: int = 0) -> int:
     cfg = bfs_serve_config(int(memory_cap_bytes), int(max_wave), int(queue_capacity), int(levels_per_round),
-                           int(waves_per_graph), int(admit_window), 0)
+                           int(waves_per_graph), int(admit_window), int(cohort_wait_us))
     out = _P()
     check(lib().bfs_serve_create(ctypes.byref(cfg), ctypes.byref(out)))
     return out.value

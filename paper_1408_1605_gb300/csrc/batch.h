@@ -164,7 +164,7 @@ void launch_batch_seed(const BatchArgs<OffT>& a, const RootSeed* seeds_dev, int 
                        bool fresh, cudaStream_t st);
 extern const ExpandShape kBatchShapes[];
 extern const int kNumBatchShapes;
-constexpr int kDefaultBatchShape = 0;
+constexpr int kDefaultBatchShape = 4;  // warp tiles of 128 edges, 256 threads
 template <typename OffT>
 cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, cudaStream_t st);
 template <typename OffT>

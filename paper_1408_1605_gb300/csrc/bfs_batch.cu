@@ -84,9 +84,16 @@ void free_batch_bufs(BatchBufs& b) {
   b = BatchBufs{};
 }
 
+// Room for claim records beyond the per-vertex slots: a wave that keeps its records to the
+// end (bfs_run_batch) spills more (the hubs' records of every level) than one that writes
+// its outputs level by level (serving).
+static long long overflow_cap(const GraphDev& g, int ev_slots) {
+  return (ev_slots == kEventSlotsWave ? g.n : g.n / 4) + 65536;
+}
+
 size_t batch_bufs_bytes(const GraphDev& g, int ev_slots) {
   const size_t osz = g.off64 ? 8 : 4;
-  const size_t ovf_cap = (size_t)g.n / 4 + 65536;
+  const size_t ovf_cap = (size_t)overflow_cap(g, ev_slots);
   return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots) +
          ovf_cap * sizeof(OvfEvent) + 2 * 16 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
 }
@@ -108,7 +115,7 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots) {
   if (e == cudaSuccess) e = dalloc(&b.slots, 1);
   if (e == cudaSuccess) e = dalloc(&b.stats, 3 * kMaxWave);
   if (e == cudaSuccess) e = dalloc(&b.roots_dev, 4 * kMaxWave);
-  b.ovf_cap = g.n / 4 + 65536;
+  b.ovf_cap = overflow_cap(g, ev_slots);
   if (e == cudaSuccess) e = dalloc(&b.evc, (size_t)g.n);
   b.ev_slots = ev_slots;
   if (e == cudaSuccess) e = dalloc(&b.ev, (size_t)g.n * ev_slots);

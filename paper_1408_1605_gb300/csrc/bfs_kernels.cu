@@ -220,24 +220,25 @@ struct LevelIO {
 
 constexpr long long kNoListCap = 0x7fffffffffffffffll;
 
-// Frontier-bitmap mode, per warp: keep appending claims to the next-frontier list while the
-// list stays within the cap; past it, record that the level dropped its list and only count
-// the claims (they are all in the next-frontier bitmap). Returns whether to append.
+// Frontier-bitmap mode, per warp, decided where a full claim buffer would be appended: keep
+// appending while the list stays within the cap; past it the level drops its list (flagged
+// once) and the warp only counts its claims, which are all in the next-frontier bitmap.
 template <typename OffT>
 __device__ __forceinline__ bool keep_listing(const LevelIO<OffT>& io, Packed pk, int pending) {
   if (io.list_cap == kNoListCap) return true;
   unsigned long long c = 0;
   if ((threadIdx.x & 31) == 0) c = *(volatile unsigned long long*)io.counter_out;
   c = __shfl_sync(0xffffffffu, c, 0);
-  return pk.count(c) + pending <= io.list_cap;
+  const bool keep = pk.count(c) + pending <= io.list_cap;
+  if (!keep && (threadIdx.x & 31) == 0) *(volatile unsigned*)io.dropped = 1u;
+  return keep;
 }
 
+// The claims a warp counted without appending them, added to the list's count once, at the
+// end of the warp's share of the level (one atomic per warp, not per tile).
 template <typename OffT>
-__device__ __forceinline__ void count_only(const LevelIO<OffT>& io, Packed pk, int claims) {
-  if ((threadIdx.x & 31) == 0 && claims > 0) {
-    *(volatile unsigned*)io.dropped = 1u;
-    atomicAdd(io.counter_out, pk.make(claims, 0));
-  }
+__device__ __forceinline__ void add_counted(const LevelIO<OffT>& io, Packed pk, long long counted) {
+  if ((threadIdx.x & 31) == 0 && counted > 0) atomicAdd(io.counter_out, pk.make(counted, 0));
 }
 
 // Appends the CTA's buffered claims to the next frontier: one 64-bit atomic reserves the
@@ -525,6 +526,9 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
   const int L = io.L;
   const int probe_mode = io.probe_mode;
   int nc = 0;  // claims buffered (warp-uniform)
+  // frontier-bitmap mode: appending until the list would pass the cap, then counting only
+  bool listing = io.list_cap >= 0;
+  long long counted = 0;
   // (Loading the next tile's entry range and staged entries one tile ahead was measured:
   // no faster, and slower once it made the kernel spill.)
   for (int64_t tile = tile0; tile < ntiles; tile += tstride) {
@@ -613,20 +617,19 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
       if (b) wc |= 1u << j;
       tot += __popc(b);
     }
-    // Frontier-bitmap mode: past the list cap the claims are only counted (they are in the
-    // next-frontier bitmap), and the buffered ones with them.
-    bool listing = true;
-    if (wc && !keep_listing(io, pk, nc + tot)) {
-      listing = false;
-      count_only(io, pk, nc + tot);
-      nc = 0;
-    }
-    // Room for this tile's claims first, while few registers are live.
+    // Room for this tile's claims first, while few registers are live. In frontier-bitmap
+    // mode a full buffer past the list cap is counted instead of appended.
     if (listing && nc + tot > WCAP) {
       __syncwarp();
-      warp_flush<OffT, P>(pk, io, sm.claim, nc);
+      if (keep_listing(io, pk, nc)) {
+        warp_flush<OffT, P>(pk, io, sm.claim, nc);
+      } else {
+        listing = false;
+        counted += nc;
+      }
       nc = 0;
     }
+    if (!listing) counted += tot;
     // Most edges of a large level find their vertex visited: the claim work below is
     // skipped by a warp-uniform branch wherever no lane of the warp claimed.
 #pragma unroll
@@ -666,7 +669,11 @@ __device__ void td_level_warp(const OffT* __restrict__ off, const int32_t* __res
     if (keep_listing(io, pk, nc))
       warp_flush<OffT, P>(pk, io, sm.claim, nc);
     else
-      count_only(io, pk, nc);
+      counted += nc;
+  }
+  if (io.list_cap != kNoListCap) {
+    if (io.list_cap < 0 && counted > 0 && (threadIdx.x & 31) == 0) *(volatile unsigned*)io.dropped = 1u;
+    add_counted(io, pk, counted);
   }
 }
 

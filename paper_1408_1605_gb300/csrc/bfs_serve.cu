@@ -194,6 +194,25 @@ static bool sibling_takes(const bfs_server_s* S, const Wave* w, int cap_slots) {
   return false;
 }
 
+// Whether an idle wave may start a new cohort now (with S->mu held). A wave costs nearly
+// the same whether one slot or all are busy, so while a sibling wave of the graph keeps the
+// device busy, a new cohort waits until the pending queries fill it or the oldest has
+// waited cohort_wait_us; *wait_left receives the time still to wait.
+static bool cohort_ready(const bfs_server_s* S, const Wave* w, int cap_slots, Clock::duration* wait_left) {
+  *wait_left = Clock::duration::zero();
+  const std::deque<ServeReq*>& pending = w->sg->pending;
+  if (pending.empty()) return false;
+  bool sibling_busy = false;
+  for (const Wave* x : w->sg->waves) sibling_busy |= x != w && x->active;
+  const int wait_us = S->cfg.cohort_wait_us == 0 ? 20000 : S->cfg.cohort_wait_us;
+  if (!sibling_busy || wait_us < 0 || (int)pending.size() >= cap_slots) return true;
+  const auto waited = Clock::now() - pending.front()->t_submit;
+  const auto budget = std::chrono::microseconds(wait_us);
+  if (waited >= budget) return true;
+  *wait_left = budget - waited;
+  return false;
+}
+
 // One round of a wave: admission, seeding, a burst of levels, retirement. Each wave has
 // its own scheduler thread, so a slow wave never holds back the others; the shared
 // request bookkeeping is guarded by the server lock.
@@ -213,7 +232,9 @@ static void wave_round(bfs_server_s* S, Wave* w) {
       }
     }
     const int cap_slots = std::max(1, std::min(kMaxWave, S->cfg.max_wave > 0 ? S->cfg.max_wave : kMaxWave));
-    const bool may_admit = wave_can_admit(S, w, cap_slots) && (w->active || !sibling_takes(S, w, cap_slots));
+    Clock::duration wait_left;
+    const bool may_admit = wave_can_admit(S, w, cap_slots) &&
+                           (w->active || (!sibling_takes(S, w, cap_slots) && cohort_ready(S, w, cap_slots, &wait_left)));
     while (may_admit && !pending.empty()) {
       int free_bit = -1;
       for (int b = 0; b < cap_slots; ++b)
@@ -393,7 +414,10 @@ static void wave_main(bfs_server_s* S, Wave* w) {
         if (w->sg->pending.empty()) return false;
         for (ServeReq* r : w->sg->pending)
           if (r->cancel) return true;
-        return S->stop || !sibling_takes(S, w, cap_slots);
+        if (S->stop) return true;
+        if (sibling_takes(S, w, cap_slots)) return false;
+        Clock::duration left;
+        return cohort_ready(S, w, cap_slots, &left);  // else looked at again within 2 ms
       };
       S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || busy(); });
       if (S->stop && !w->active) {  // drain: cancel what has not started, then leave
