@@ -900,7 +900,7 @@ def run_serve(args) -> int:
                           "config": {"workload": "serve: rmat-s20, rmat-s24, grid3d-192, uniform-n8M-deg8",
                                      "roots": "seeded uniform per graph", "wave": 64,
                                      "levels_per_round": args.serve_levels_per_round or 8,
-                                     "cohort_wait_us": args.serve_cohort_wait_us or 20000,
+                                     "cohort_wait_us": args.serve_cohort_wait_us or "mean cohort duration",
                                      "memory_cap_bytes": 64 << 30,
                                      "relabel": args.relabel},
                           "rates": results}), flush=True)

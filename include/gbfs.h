@@ -226,6 +226,21 @@ GBFS_API bfs_status bfs_expand(bfs_graph_t g, const int32_t *frontier, int64_t n
                                uint32_t *bitmap, int32_t *levels, int32_t *parents, int32_t *next,
                                int64_t *next_count, void *stream);
 
+/* The paper's 2D-partitioned search (Sec. 3.2 Algorithm 2, Sec. 3.4 Algorithm 3 with
+ * destinations owned by other processor columns, Sec. 3.5 frontier update), emulated on this
+ * GPU: the graph is split over an R x C grid of virtual processors (vertex block j R + i
+ * owned by P_ij; edge (u, v) held by the processor of u's column block j and v's row block
+ * mod R), each with its own local CSC, level and predecessor arrays and visited bitmap, and
+ * the expand (within a grid column) and fold (within a grid row) exchanges are copies between
+ * their device buffers. Results are the same BFS as bfs_run's (levels identical; parents a
+ * valid tree, assembled from the sender-column predecessors of the update kernel).
+ *   R, C in [1, 64]; levels, parents: device int32[n_vertices].
+ * The partition is built for the call and freed after it; the call synchronizes `stream`.
+ * Not available on graphs created with BFS_RELABEL_DEGREE. Failures: BFS_ERR_INVALID_ARG,
+ * BFS_ERR_INVALID_GRAPH (a column id out of range), BFS_ERR_OOM, BFS_ERR_CUDA. */
+GBFS_API bfs_status bfs_run_2d(bfs_graph_t g, int R, int C, int32_t root, int32_t *levels, int32_t *parents,
+                               void *stream);
+
 /* One top-down level on caller-held state, as bfs_expand, that hands over its next frontier
  * as a bitmap (Sec. 5: the specialized expansion that produces a bitmap instead of a list):
  *   next_bitmap uint32[ceil(n/32)] (device): cleared by the call, then bit v % 32 of word
@@ -297,7 +312,8 @@ typedef struct bfs_serve_config {
                                 mean query depth on deep graphs */
   int32_t cohort_wait_us;    /* while another wave of the graph is running, an idle wave starts
                                 a new cohort only once max_wave queries are pending or the
-                                oldest has waited this long (0 = 20000; < 0: start at once) */
+                                oldest has waited this long (0: the moving average of the
+                                graph's cohort durations; < 0: start at once) */
 } bfs_serve_config;
 
 typedef struct bfs_serve_report {

@@ -19,7 +19,7 @@ LIB_BFS = os.path.join(HERE, "libgbfs.so")
 LIB_GEN = os.path.join(HERE, "libgbfs_graphgen.so")
 
 BFS_CU = ["bfs_kernels.cu", "bfs_capi.cu", "bfs_batch_kernels.cu", "bfs_batch.cu", "bfs_serve.cu", "bfs_tune.cu", "bfs_noalloc.cu",
-          "bfs_relabel.cu"]
+          "bfs_relabel.cu", "bfs_2d.cu"]
 
 
 def _stale(target: str, sources: list[str]) -> bool:

@@ -110,6 +110,7 @@ def lib():
             "bfs_run": [_P, i32, _P, _P, _P, ctypes.POINTER(bfs_stats)],
             "bfs_expand": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P],
             "bfs_expand_bitmap": [_P, _P, i64, i32, _P, _P, _P, _P, _P, _P, _P],
+            "bfs_run_2d": [_P, ctypes.c_int, ctypes.c_int, i32, _P, _P, _P],
             "bfs_run_noalloc": [_P, _P, i64, i64, i32, _P, _P, _P],
             "bfs_run_batch": [_P, _P, ctypes.c_int, _P, _P, _P, _P],
             "bfs_serve_create": [ctypes.POINTER(bfs_serve_config), ctypes.POINTER(_P)],
@@ -260,6 +261,14 @@ def bfs_expand(graph: int, frontier, n_frontier: int, level: int, bitmap, levels
                stream=None) -> None:
     check(lib().bfs_expand(graph, ptr(frontier), int(n_frontier), int(level), ptr(bitmap), ptr(levels), ptr(parents),
                            ptr(next_), ptr(next_count), stream_handle(stream)))
+
+
+def bfs_run_2d(graph: int, R: int, C: int, root: int, levels, parents, stream=None) -> None:
+    if _numel(levels) is not None or _numel(parents) is not None:
+        n = bfs_graph_info(graph)[0]
+        _check_int32_out("levels", levels, n)
+        _check_int32_out("parents", parents, n)
+    check(lib().bfs_run_2d(graph, int(R), int(C), int(root), ptr(levels), ptr(parents), stream_handle(stream)))
 
 
 def bfs_expand_bitmap(graph: int, frontier, n_frontier: int, level: int, bitmap, levels, parents, next_bitmap,

@@ -78,6 +78,7 @@ struct Wave {
   long long* stats_host = nullptr;    // pinned, 3 per slot
   long long* stats_dev = nullptr;     // device, 3 per slot
   unsigned long long pending_clear = 0;  // bits to clear from V before reuse
+  Clock::time_point t_cohort;           // when the running cohort started
 };
 
 // A resident graph: its queue of pending queries, shared by its waves, and the mean depth
@@ -89,6 +90,7 @@ struct ServeGraph {
   std::vector<Wave*> waves;
   double depth_sum = 0;
   long long depth_n = 0;
+  double wave_ms = 0;  // moving average of a cohort's duration, start to last retirement
 };
 
 }  // namespace gbfs
@@ -204,7 +206,9 @@ static bool cohort_ready(const bfs_server_s* S, const Wave* w, int cap_slots, Cl
   if (pending.empty()) return false;
   bool sibling_busy = false;
   for (const Wave* x : w->sg->waves) sibling_busy |= x != w && x->active;
-  const int wait_us = S->cfg.cohort_wait_us == 0 ? 20000 : S->cfg.cohort_wait_us;
+  // default: as long as the graph's cohorts take (the wait then costs at most one cohort)
+  const long long wait_us = S->cfg.cohort_wait_us != 0 ? (long long)S->cfg.cohort_wait_us
+                                                       : (long long)(1000.0 * w->sg->wave_ms);
   if (!sibling_busy || wait_us < 0 || (int)pending.size() >= cap_slots) return true;
   const auto waited = Clock::now() - pending.front()->t_submit;
   const auto budget = std::chrono::microseconds(wait_us);
@@ -289,6 +293,7 @@ static void wave_round(bfs_server_s* S, Wave* w) {
     const bool fresh = !w->active;
     if (fresh) {
       w->t = 0;
+      w->t_cohort = Clock::now();
       for (ServeReq* r : admitted) r->start = 0;
     } else if (w->pending_clear) {
       launch_clear_bits(w->b.visited, w->g.n, w->pending_clear, w->g.num_sms, w->stream);
@@ -349,7 +354,12 @@ static void wave_round(bfs_server_s* S, Wave* w) {
       ServeReq* r = w->slot_req[b];
       if (r && r->start <= t_expanded && !((alive >> b) & 1ull)) retire.push_back(b);
     }
-    if (!w->ctl_host->cont) w->active = false;
+    if (!w->ctl_host->cont) {
+      w->active = false;
+      const double ms = std::chrono::duration<double, std::milli>(Clock::now() - w->t_cohort).count();
+      std::lock_guard<std::mutex> lk(S->mu);
+      w->sg->wave_ms = w->sg->wave_ms == 0 ? ms : 0.75 * w->sg->wave_ms + 0.25 * ms;
+    }
     // statistics and host copies of the retiring slots
     for (int b : retire) {
       ServeReq* r = w->slot_req[b];
