@@ -35,6 +35,7 @@ struct BatchCtl {
   int bu_levels;                  // bottom-up levels so far
   long long seen;                 // degree sum of the frontiers expanded so far
   unsigned long long bitcnt[kMaxWave];  // per-root size of the new frontier (bottom-up choice)
+  unsigned long long dense_count; // dense rows handed out in this wave
 };
 
 // Parent event of a claim: at wave level `level`, vertex u's edge claimed the bits `mask`
@@ -86,6 +87,13 @@ struct BatchArgs {
   int ev_slots;                   // event slots per vertex (kEventSlots or kEventSlotsWave)
   int defer;                      // 1: events kept for the whole wave, outputs written once at its end
   int n_slots;                    // slots (roots) of the wave whose outputs the final pass writes
+  // Waves with deferred outputs: a vertex whose claims outgrow its event slots gets a dense
+  // row (parent and wave level per root bit, and the mask of bits set there) from a pool.
+  int32_t* dense_idx;             // [n]: the vertex's row, -1 if none (NULL: no dense rows)
+  int32_t* dense_par;             // [dense_cap][64]
+  int32_t* dense_lvl;             // [dense_cap][64]
+  unsigned long long* dense_mask; // [dense_cap]
+  long long dense_cap;
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -107,6 +115,11 @@ struct BatchBufs {
   OvfEvent* ovf = nullptr;
   long long ovf_cap = 0;
   int ev_slots = kEventSlots;
+  int32_t* dense_idx = nullptr;   // dense rows (waves with deferred outputs only)
+  int32_t* dense_par = nullptr;
+  int32_t* dense_lvl = nullptr;
+  unsigned long long* dense_mask = nullptr;
+  long long dense_cap = 0;
 };
 
 struct RootSeed {
@@ -144,7 +157,37 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.ev_slots = b.ev_slots;
   a.defer = 0;
   a.n_slots = kMaxWave;
+  a.dense_idx = b.dense_idx;
+  a.dense_par = b.dense_par;
+  a.dense_lvl = b.dense_lvl;
+  a.dense_mask = b.dense_mask;
+  a.dense_cap = b.dense_cap;
   return a;
+}
+
+// The dense row of vertex v, handed out on first use (-1 when there are none or the pool is
+// spent). Two claimers racing for a new row both take one; the loser's stays unused.
+template <typename OffT>
+__device__ __forceinline__ int32_t dense_row(const BatchArgs<OffT>& a, int32_t v) {
+  if (!a.dense_idx) return -1;
+  const int32_t row = *(volatile int32_t*)(a.dense_idx + v);
+  if (row >= 0) return row;
+  const unsigned long long t = atomicAdd(&a.ctl->dense_count, 1ull);
+  if ((long long)t >= a.dense_cap) return -1;
+  const int32_t prev = atomicCAS(a.dense_idx + v, -1, (int32_t)t);
+  return prev < 0 ? (int32_t)t : prev;
+}
+
+// Claim bits of vertex v with parent u at wave level L, written into its dense row.
+template <typename OffT>
+__device__ __forceinline__ void dense_write(const BatchArgs<OffT>& a, int32_t row, unsigned long long bits,
+                                            int32_t u, int32_t L) {
+  for (unsigned long long m = bits; m; m &= m - 1) {
+    const int b = __ffsll((long long)m) - 1;
+    a.dense_par[(size_t)row * kMaxWave + b] = u;
+    a.dense_lvl[(size_t)row * kMaxWave + b] = L;
+  }
+  atomicOr(a.dense_mask + row, bits);
 }
 
 // Statistics of one output array: out[0] = degree sum of reached vertices (2 m_c),

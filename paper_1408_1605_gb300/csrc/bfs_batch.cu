@@ -81,6 +81,10 @@ void free_batch_bufs(BatchBufs& b) {
   cudaFree(b.evc);
   cudaFree(b.ev);
   cudaFree(b.ovf);
+  cudaFree(b.dense_idx);
+  cudaFree(b.dense_par);
+  cudaFree(b.dense_lvl);
+  cudaFree(b.dense_mask);
   b = BatchBufs{};
 }
 
@@ -93,11 +97,18 @@ static long long overflow_cap(const GraphDev& g, int ev_slots) {
   return g.n / 4 + 65536;
 }
 
+// Dense rows of the waves that keep their claim records to the end: one per 16 vertices.
+static long long dense_rows_cap(const GraphDev& g, int ev_slots) {
+  return ev_slots == kEventSlotsWave ? g.n / 16 + 1024 : 0;
+}
+
 size_t batch_bufs_bytes(const GraphDev& g, int ev_slots) {
   const size_t osz = g.off64 ? 8 : 4;
   const size_t ovf_cap = (size_t)overflow_cap(g, ev_slots);
-  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots) +
-         ovf_cap * sizeof(OvfEvent) + 2 * 16 * (size_t)(g.nnz / kChunk + 2) + 64 * 1024;
+  const size_t dense = (size_t)dense_rows_cap(g, ev_slots);
+  return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots + (dense ? 4 : 0)) +
+         ovf_cap * sizeof(OvfEvent) + 2 * 16 * (size_t)(g.nnz / kChunk + 2) + dense * (8 * kMaxWave + 8) +
+         64 * 1024;
 }
 
 cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots) {
@@ -122,6 +133,13 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots) {
   b.ev_slots = ev_slots;
   if (e == cudaSuccess) e = dalloc(&b.ev, (size_t)g.n * ev_slots);
   if (e == cudaSuccess) e = dalloc(&b.ovf, (size_t)b.ovf_cap);
+  b.dense_cap = dense_rows_cap(g, ev_slots);
+  if (b.dense_cap > 0) {
+    if (e == cudaSuccess) e = dalloc(&b.dense_idx, (size_t)g.n);
+    if (e == cudaSuccess) e = dalloc(&b.dense_par, (size_t)b.dense_cap * kMaxWave);
+    if (e == cudaSuccess) e = dalloc(&b.dense_lvl, (size_t)b.dense_cap * kMaxWave);
+    if (e == cudaSuccess) e = dalloc(&b.dense_mask, (size_t)b.dense_cap);
+  }
   if (e == cudaSuccess) e = cudaMemset(b.evc, 0, sizeof(int32_t) * (size_t)g.n);
   if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
   if (e != cudaSuccess) {

@@ -271,7 +271,6 @@ static bfs_status run_single(bfs_graph_s* G, int32_t root, int32_t* levels, int3
     if (!pg) {
       pg = persistent_grid<OffT>(G->shape, G->g.num_sms, G->bottom_up != 0);
       if (G->persist_ctas > 0) pg = std::min(pg, G->persist_ctas * G->g.num_sms);
-      pg = std::min(pg, kMaxBarGroups * kBarGroup);  // the grid barrier's group counters
     }
     if ((e = launch_persistent<OffT>(G->shape, pa, pg, st)) != cudaSuccess)
       return cuda_fail(e, "persistent search kernel");

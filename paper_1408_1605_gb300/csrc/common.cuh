@@ -69,11 +69,6 @@ struct Ctl {
 // Control block of a persistent (one-launch) search: counters rotate by 3 so that level
 // it reads counter[it % 3], fills counter[(it + 1) % 3] and clears counter[(it + 2) % 3].
 constexpr int kMaxLevelTimes = 64;
-// Grid barrier arrivals: CTAs arrive in groups of kBarGroup on per-group counters (one
-// 128-byte line each), the last of each group on the top counter.
-constexpr int kBarGroup = 32;
-constexpr int kMaxBarGroups = 128;  // up to 4096 CTAs
-constexpr int kBarStride = 32;      // words between group counters
 struct PCtl {
   unsigned long long counter[3];
   unsigned int bar_count;
@@ -91,7 +86,6 @@ struct PCtl {
   unsigned long long level_ns[kMaxLevelTimes];  // device clock at the end of each level
   long long level_nf[kMaxLevelTimes];           // frontier size of each level
   int level_bu[kMaxLevelTimes];                 // 1 if the level ran bottom-up
-  unsigned int bar_group[kMaxBarGroups * kBarStride];  // group arrival counters
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
