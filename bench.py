@@ -466,6 +466,7 @@ def main() -> int:
     hm = harmonic_mean([teps_of(s) for s in stats])
     loop = shapes["single"]["loop"]
     kernel = "k_bfs_persistent" if loop == "persistent" else "k_expand"
+    kernel_key = f"{kernel}/shape{shapes['single']['shape']}"  # traffic figures are per compiled shape
     total_bytes = sum(alg_bytes_expand(s["edges_traversed"], s["vertices_reached"], off_bytes) for s in stats)
     expand_ms = sum(s["expand_ms"] for s in stats)
     levels_run = sum(s["depth"] for s in stats)
@@ -535,7 +536,7 @@ def main() -> int:
 
     if rank == 0:
         peaks = load_peaks()
-        traffic = profiled_traffic(wl.name, relabel, kernel)
+        traffic = profiled_traffic(wl.name, relabel, kernel_key)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -544,7 +545,8 @@ def main() -> int:
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4),
                          "traffic": round(traffic) if traffic else None,
-                         "kernel": kernel, "launches": launches_kernel, "levels": levels_run,
+                         "kernel": kernel, "shape": shapes["single"]["shape"], "launches": launches_kernel,
+                         "levels": levels_run,
                          "peak_source": peaks["source"],
                          "alg_bytes_per_launch": round(total_bytes / max(launches_kernel, 1))},
             "e2e": {"value": round(e2e_hm, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * len(roots),

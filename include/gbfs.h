@@ -146,6 +146,11 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *     top-down level hands over a bitmap. Results are the same BFS in every mode.
  *   BFS_OPT_UNPACKED_LEVELS (read only): levels of the last persistent search whose next
  *     frontier was rebuilt from a bitmap (-1 after a search in another loop mode).
+ *   BFS_OPT_WAVE_DENSE_ROWS: a batched wave records each claim (root bits, parent, level) in
+ *     one of 8 slots of the claimed vertex; a vertex claimed more often gets a dense row of
+ *     64 parents and levels from a pool of n / 16 + 1024 rows. This option caps the rows a
+ *     wave may use (-1, the default: the whole pool; 0: none). Claims left without room go to
+ *     an overflow list of n / 4 + 65536 records, and past it are written out at once.
  *   BFS_OPT_WAVE_LEVELS, BFS_OPT_WAVE_OVERFLOW (read only): levels run by the last batched
  *     wave on this graph, and how many of its claim records did not fit the per-vertex
  *     slots (they are applied from an overflow list when the wave's outputs are written). */
@@ -161,6 +166,7 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
 #define BFS_OPT_WAVE_OVERFLOW 10
 #define BFS_OPT_FRONTIER 11
 #define BFS_OPT_UNPACKED_LEVELS 12
+#define BFS_OPT_WAVE_DENSE_ROWS 13
 #define BFS_FRONTIER_LIST 0
 #define BFS_FRONTIER_AUTO 1
 #define BFS_FRONTIER_BITMAP 2
@@ -284,7 +290,8 @@ GBFS_API bfs_status bfs_run_noalloc(const int32_t *row_offsets, const int32_t *c
  *   - Each added graph gets waves_per_graph waves of up to max_wave slots; each wave has its
  *     own CUDA stream and scheduler thread, so waves run concurrently on the device.
  *   - A wave advances in bursts of levels (levels_per_round when it cannot admit, else
- *     one). Between two bursts, finished queries retire (their bit left every frontier)
+ *     one; on deep graphs an eighth, resp. a thirty-second, of the graph's mean query depth
+ *     if that is more). Between two bursts, finished queries retire (their bit left every frontier)
  *     and pending queries of its graph are admitted into free slots in arrival order,
  *     starting from their root at the current wave level; a wave is never restarted for
  *     admission. Queries share row reads only while their searches are in step, so a

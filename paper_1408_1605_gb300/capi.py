@@ -38,6 +38,7 @@ BFS_OPT_WAVE_LEVELS = 9
 BFS_OPT_WAVE_OVERFLOW = 10
 BFS_OPT_FRONTIER = 11
 BFS_OPT_UNPACKED_LEVELS = 12
+BFS_OPT_WAVE_DENSE_ROWS = 13
 BFS_FRONTIER_LIST = 0
 BFS_FRONTIER_AUTO = 1
 BFS_FRONTIER_BITMAP = 2

@@ -179,6 +179,8 @@ BatchArgs<OffT> batch_args(const bfs_graph_s* G) {
   a.alpha = G->alpha;
   a.beta = G->beta;
   a.defer = 1;  // every event kept until the wave ends; the outputs are written once, after it
+  if (G->dense_rows >= 0) a.dense_cap = std::min(a.dense_cap, G->dense_rows);
+  if (a.dense_cap <= 0) a.dense_idx = nullptr;  // no dense rows: overflow list, then direct writes
   return a;
 }
 

@@ -47,10 +47,14 @@ __global__ void k_batch_clear(BatchArgs<OffT> a) {
     a.fmask[1][v] = 0ull;
     a.fmask[2][v] = 0ull;
     a.evc[v] = 0;
+    if (a.dense_idx) a.dense_idx[v] = -1;
   }
+  if (a.dense_idx)
+    for (int64_t r = tid; r < a.dense_cap; r += stride) a.dense_mask[r] = 0ull;
   if (tid == 0) {
     a.ctl->ovf_count = 0;
     a.ctl->emit_done = 0;
+    a.ctl->dense_count = 0;
   }
 }
 
@@ -275,12 +279,15 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
           if (f) {
             acc |= f;
             const int32_t uc = a.old_id ? __ldg(a.old_id + u) : (int32_t)u;
+            int32_t drow = -1;
             if (nev < a.ev_slots) {
               ClaimEvent ce;
               ce.u = uc;
               ce.level = L;
               ce.mask = f;
               a.ev[(size_t)v * a.ev_slots + nev] = ce;
+            } else if ((drow = dense_row(a, v)) >= 0) {
+              dense_write(a, drow, f, uc, L);
             } else {
               const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;
               const unsigned long long o = atomicAdd(&a.ctl->ovf_count, 1ull);
@@ -450,12 +457,15 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
       if (claimed[j]) {
         mine |= claimed[j];
         // Parent event: the outputs are written after the wave (or the level) from it.
+        int32_t drow = -1;
         if (slot[j] < a.ev_slots) {
           ClaimEvent ce;
           ce.u = uu[j];
           ce.level = L;
           ce.mask = claimed[j];
           a.ev[(size_t)v * a.ev_slots + slot[j]] = ce;
+        } else if ((drow = dense_row(a, v)) >= 0) {
+          dense_write(a, drow, claimed[j], uu[j], L);
         } else {
           const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
           const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
@@ -490,8 +500,9 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
   if (lane == 0 && (lo | hi)) atomicOr(s_alive, ((unsigned long long)hi << 32) | lo);
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
-__global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
+// TPS: resident threads per SM the registers are sized for (0: the compiler's choice).
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
+__global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<OffT> a) {
   using S = BatchSmem<OffT, BLOCK, E, CLAIM>;
   constexpr int T = S::T, CAP = S::CAP;
   static_assert(WT || CLAIM >= T, "claim buffer must hold one full tile");
@@ -653,12 +664,15 @@ __global__ void __launch_bounds__(BLOCK) k_expand_batch(BatchArgs<OffT> a) {
       if (claimed[j]) {
         mine |= claimed[j];
         // Parent event: the outputs are written in vertex order after the level (emit).
+        int32_t drow = -1;
         if (slot[j] < a.ev_slots) {
           ClaimEvent ce;
           ce.u = uu[j];
           ce.level = L;
           ce.mask = claimed[j];
           a.ev[(size_t)v * a.ev_slots + slot[j]] = ce;
+        } else if ((drow = dense_row(a, v)) >= 0) {
+          dense_write(a, drow, claimed[j], uu[j], L);
         } else {
           const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
           const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
@@ -903,11 +917,16 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
     const int64_t x = w * 32 + lane;
     const bool in = x < a.n;
     const int32_t vc = (int32_t)x;
-    unsigned long long vis = 0ull, evm = 0ull, m0 = 0ull, m1 = 0ull, m2 = 0ull;
+    unsigned long long vis = 0ull, evm = 0ull, m0 = 0ull, m1 = 0ull, m2 = 0ull, dm = 0ull;
+    int32_t drow = -1;
     if (in) {
       const int32_t v = a.new_id ? __ldg(a.new_id + vc) : vc;
       vis = a.visited[v];
       const int ne = vis ? min(a.evc[v], K) : 0;
+      if (ne == K && a.dense_idx) {  // claims past the slots went to the vertex's dense row
+        drow = a.dense_idx[v];
+        if (drow >= 0) dm = a.dense_mask[drow];
+      }
       for (int k = 0; k < ne; ++k) {
         const ClaimEvent ce = a.ev[(size_t)v * K + k];
         s_el[wib][k][lane] = ce.level;
@@ -920,18 +939,22 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
       }
     }
     __syncwarp();
-    // Bits reached without an event (roots, overflow claims) are written apart: skip them.
-    const unsigned long long skip = vis & ~evm;
+    // Bits reached without an event or a dense-row entry (roots, claims on the overflow list
+    // or written at claim time) are written apart: skip them.
+    const unsigned long long skip = vis & ~evm & ~dm;
     for (int half = 0; half < 2; ++half) {
       const unsigned vlo = (unsigned)(vis >> (32 * half)), slo = (unsigned)(skip >> (32 * half));
       const unsigned a0 = (unsigned)(m0 >> (32 * half)), a1 = (unsigned)(m1 >> (32 * half)),
-                     a2 = (unsigned)(m2 >> (32 * half));
+                     a2 = (unsigned)(m2 >> (32 * half)), dlo = (unsigned)(dm >> (32 * half));
       const int bend = min(32, nb - 32 * half);
       for (int i = 0; i < bend; ++i) {
         const int b = 32 * half + i;
         if (!in || ((slo >> i) & 1u)) continue;
         int32_t lv = -1, pu = -1;
-        if ((vlo >> i) & 1u) {
+        if ((dlo >> i) & 1u) {
+          lv = a.dense_lvl[(size_t)drow * kMaxWave + b] - s_start[b];
+          pu = a.dense_par[(size_t)drow * kMaxWave + b];
+        } else if ((vlo >> i) & 1u) {
           const int k = ((a0 >> i) & 1u) | (((a1 >> i) & 1u) << 1) | (((a2 >> i) & 1u) << 2);
           lv = s_el[wib][k][lane] - s_start[b];
           pu = s_eu[wib][k][lane];
@@ -965,10 +988,10 @@ constexpr size_t batch_smem_bytes() {
   return WT ? (size_t)(BLOCK / 32) * CLAIM * sizeof(int2) : BatchSmem<OffT, BLOCK, E, CLAIM>::bytes;
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static cudaError_t launch_batch_expand_t(const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
   constexpr size_t bytes = batch_smem_bytes<OffT, BLOCK, E, CLAIM, WT>();
-  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM, WT>;
+  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM, WT, TPS>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -979,30 +1002,33 @@ static cudaError_t launch_batch_expand_t(const BatchArgs<OffT>& a, int grid, cud
   return cudaGetLastError();
 }
 
-template <typename OffT, int BLOCK, int E, int CLAIM, bool WT>
+template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static int batch_grid_t(int num_sms) {
   constexpr size_t bytes = batch_smem_bytes<OffT, BLOCK, E, CLAIM, WT>();
-  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM, WT>;
+  auto kern = k_expand_batch<OffT, BLOCK, E, CLAIM, WT, TPS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
   return (per_sm > 0 ? per_sm : 1) * num_sms;
 }
 
-// Compiled shapes of the batched expansion (BLOCK, E, CLAIM, tiles): tiles 0 = CTA tiles of
-// BLOCK x E edges (CLAIM = CTA claim buffer), 1 = warp tiles of 32 x E edges (CLAIM = claim
-// entries per warp). The autotuner picks one.
-#define GBFS_BATCH_SHAPES(X) \
-  X(0, 256, 4, 2048, 0)      \
-  X(1, 256, 2, 2048, 0)      \
-  X(2, 128, 4, 1024, 0)      \
-  X(3, 512, 2, 2048, 0)      \
-  X(4, 256, 4, 128, 1)       \
-  X(5, 128, 4, 128, 1)       \
-  X(6, 256, 8, 256, 1)
+// Compiled shapes of the batched expansion (BLOCK, E, CLAIM, tiles, TPS): tiles 0 = CTA
+// tiles of BLOCK x E edges (CLAIM = CTA claim buffer), 1 = warp tiles of 32 x E edges (CLAIM
+// = claim entries per warp); TPS = resident threads per SM the registers are sized for (0:
+// the compiler's choice). The autotuner picks one.
+#define GBFS_BATCH_SHAPES(X)  \
+  X(0, 256, 4, 2048, 0, 0)    \
+  X(1, 256, 2, 2048, 0, 0)    \
+  X(2, 128, 4, 1024, 0, 0)    \
+  X(3, 512, 2, 2048, 0, 0)    \
+  X(4, 256, 4, 128, 1, 0)     \
+  X(5, 128, 4, 128, 1, 0)     \
+  X(6, 256, 8, 256, 1, 0)     \
+  X(7, 128, 4, 128, 1, 1280)  \
+  X(8, 128, 4, 128, 1, 1536)
 
 const ExpandShape kBatchShapes[] = {
-#define X(id, b, e, c, w) {id, b, e, c, w},
+#define X(id, b, e, c, w, t) {id, b, e, c, w},
     GBFS_BATCH_SHAPES(X)
 #undef X
 };
@@ -1011,8 +1037,8 @@ const int kNumBatchShapes = sizeof(kBatchShapes) / sizeof(kBatchShapes[0]);
 template <typename OffT>
 cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, cudaStream_t st) {
   switch (shape) {
-#define X(id, b, e, c, w) \
-  case id: return launch_batch_expand_t<OffT, b, e, c, w != 0>(a, grid, st);
+#define X(id, b, e, c, w, t) \
+  case id: return launch_batch_expand_t<OffT, b, e, c, w != 0, t>(a, grid, st);
     GBFS_BATCH_SHAPES(X)
 #undef X
   }
@@ -1022,8 +1048,8 @@ cudaError_t launch_batch_expand(int shape, const BatchArgs<OffT>& a, int grid, c
 template <typename OffT>
 int batch_expand_grid(int shape, int num_sms) {
   switch (shape) {
-#define X(id, b, e, c, w) \
-  case id: return batch_grid_t<OffT, b, e, c, w != 0>(num_sms);
+#define X(id, b, e, c, w, t) \
+  case id: return batch_grid_t<OffT, b, e, c, w != 0, t>(num_sms);
     GBFS_BATCH_SHAPES(X)
 #undef X
   }

@@ -632,6 +632,14 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
         G->pgrid[0] = G->pgrid[1] = 0;
       }
       return BFS_OK;
+    case BFS_OPT_WAVE_DENSE_ROWS:
+      if (value < -1 || value > (1ll << 40)) return fail(BFS_ERR_INVALID_ARG, "dense rows outside [-1, 2^40]");
+      if (G->dense_rows != value) {
+        if (G->last_done) cudaEventSynchronize(G->last_done);
+        G->dense_rows = value;
+        set_batch_shape(G, G->batch_shape);  // the captured wave loop holds the old arguments
+      }
+      return BFS_OK;
     case BFS_OPT_FRONTIER:
       if (value < BFS_FRONTIER_LIST || value > BFS_FRONTIER_BITMAP) return fail(BFS_ERR_INVALID_ARG, "unknown frontier mode");
       if (G->frontier_mode != (int)value) {
@@ -665,6 +673,7 @@ GBFS_API bfs_status bfs_graph_get_option(bfs_graph_t G, int option, int64_t* val
     case BFS_OPT_PERSIST_CTAS: *value = G->persist_ctas; return BFS_OK;
     case BFS_OPT_RELABELED: *value = G->g.new_id != nullptr; return BFS_OK;
     case BFS_OPT_FRONTIER: *value = G->frontier_mode; return BFS_OK;
+    case BFS_OPT_WAVE_DENSE_ROWS: *value = G->dense_rows; return BFS_OK;
     case BFS_OPT_UNPACKED_LEVELS: *value = G->last_unpacked; return BFS_OK;
     case BFS_OPT_WAVE_LEVELS: *value = batch_last_levels(G); return BFS_OK;
     case BFS_OPT_WAVE_OVERFLOW: *value = batch_last_overflow(G); return BFS_OK;

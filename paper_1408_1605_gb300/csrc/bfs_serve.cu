@@ -280,9 +280,13 @@ static void wave_round(bfs_server_s* S, Wave* w) {
     // When this wave cannot take the queries that are waiting (none waiting, no slot, or
     // its cohort is too old), run several levels before looking again: a root's bit never
     // returns to a frontier once its search is done, so the alive mask after the burst
-    // still shows every query that finished in it.
+    // still shows every query that finished in it. Deep graphs (hundreds of levels) run
+    // longer bursts, also while admitting: a round trip to the host per level would cost
+    // far more than the level itself.
     const int lpr = S->cfg.levels_per_round > 0 ? S->cfg.levels_per_round : 8;
-    w->burst = (pending.empty() || !wave_can_admit(S, w, cap_slots)) ? lpr : 1;
+    const int depth = w->sg->depth_n ? (int)(w->sg->depth_sum / (double)w->sg->depth_n) : 0;
+    const bool admitting = !pending.empty() && wave_can_admit(S, w, cap_slots);
+    w->burst = admitting ? std::max(1, depth / 32) : std::max(lpr, depth / 8);
     for (int b = 0; b < kMaxWave; ++b) {
       ServeReq* r = w->slot_req[b];
       if (r && r->cancel && r->state == kRunning) drop |= 1ull << b;

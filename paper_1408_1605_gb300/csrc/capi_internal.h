@@ -40,6 +40,7 @@ struct bfs_graph_s {
   int persist_ctas = 0;     // CTAs per SM of a persistent search (0: as many as fit)
   int frontier_mode = 0;    // BFS_FRONTIER_LIST / _AUTO / _BITMAP
   long long last_unpacked = -1;  // levels unpacked from a bitmap by the last persistent search
+  long long dense_rows = -1;     // BFS_OPT_WAVE_DENSE_ROWS (-1: the allocated pool)
   int pgrid[2] = {0, 0};    // CTAs of the persistent kernel (top-down only, with bottom-up)
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;

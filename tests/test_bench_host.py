@@ -38,7 +38,7 @@ def test_config_names_the_reference_input_order():
     assert bench.config_for(wl, g, ref)["vertex_order"].startswith("as generated")
 
 
-def _traffic_file(tmp_path, h, order, kernel="k_bfs_persistent"):
+def _traffic_file(tmp_path, h, order, kernel="k_bfs_persistent/shape4"):
     import json
 
     (tmp_path / "traffic.json").write_text(json.dumps(
@@ -49,14 +49,16 @@ def test_traffic_only_for_matching_source_and_order(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
     h = bench.kernel_source_hash()
     _traffic_file(tmp_path, h, "relabelled")
-    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent") == 2.5e9
-    assert bench.profiled_traffic("rmat-s26-ef16", False, "k_bfs_persistent") is None  # other vertex order
-    assert bench.profiled_traffic("rmat-s22-ef16", True, "k_bfs_persistent") is None   # workload not profiled
-    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_expand") is None   # other kernel
+    k = "k_bfs_persistent/shape4"
+    assert bench.profiled_traffic("rmat-s26-ef16", True, k) == 2.5e9
+    assert bench.profiled_traffic("rmat-s26-ef16", False, k) is None  # other vertex order
+    assert bench.profiled_traffic("rmat-s22-ef16", True, k) is None   # workload not profiled
+    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent/shape7") is None  # other shape
+    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_expand/shape4") is None   # other kernel
     _traffic_file(tmp_path, "0" * 16, "relabelled")
-    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent") is None   # kernel changed since
+    assert bench.profiled_traffic("rmat-s26-ef16", True, k) is None   # kernel changed since
     (tmp_path / "traffic.json").write_text("not json")
-    assert bench.profiled_traffic("rmat-s26-ef16", True, "k_bfs_persistent") is None
+    assert bench.profiled_traffic("rmat-s26-ef16", True, k) is None
 
 
 def test_source_hash_ignores_comments():
@@ -77,7 +79,7 @@ def test_committed_traffic_figures_parse():
     assert re.fullmatch(r"[0-9a-f]{16}", db["kernel_source_hash"])
     for key, rec in db["entries"].items():
         workload, order, kernel = key.split("|")
-        assert order in ("relabelled", "as-generated") and kernel.startswith("k_")
+        assert order in ("relabelled", "as-generated") and kernel.startswith("k_") and "/shape" in kernel
         assert rec["traffic_per_launch"] > 0
         assert "--clock-control none" in rec["command"]
 

@@ -178,13 +178,15 @@ def test_waves_with_bottom_up_levels(torch_cuda, oracle_mod, graphs_mod, policy,
             capi.bfs_graph_destroy(h)
 
 
+@pytest.mark.parametrize("dense_rows", [-1, 1, 0])
 @pytest.mark.parametrize("bottom_up", [0, 1])
-def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, bottom_up):
+def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, bottom_up, dense_rows):
     """Hub vertices claimed by many frontier vertices with disjoint root bits: 64 roots at
     the leaves of a star (every leaf's edge claims its own bit of the centre, 64 parent
     events at one vertex in one level), and a second hub joined to every leaf, so that the
-    events of a wave spill past the per-vertex slots into the overflow list. Every root
-    still gets the oracle's levels and a valid tree."""
+    claims of a wave spill past the per-vertex slots: into dense rows (all the pool, one row,
+    none), then the overflow list. Every root still gets the oracle's levels and a valid
+    tree."""
     from paper_1408_1605_gb300 import capi
 
     leaves = np.arange(1, 65, dtype=np.int32)
@@ -195,6 +197,7 @@ def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, botto
         h = capi.bfs_graph_create(g.offsets, g.cols, g.n, g.nnz, capi.BFS_OFFSETS_INT64 | flags)
         try:
             capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, bottom_up)
+            capi.bfs_graph_set_option(h, capi.BFS_OPT_WAVE_DENSE_ROWS, dense_rows)
             check_wave(capi, oracle_mod, torch_cuda, h, g, leaves)
             check_wave(capi, oracle_mod, torch_cuda, h, g, np.concatenate([leaves[:32], [0, 65] * 16]))
             check_wave(capi, oracle_mod, torch_cuda, h, g, leaves[::-1].copy(), host_out=True)
@@ -202,7 +205,7 @@ def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, botto
             capi.bfs_graph_destroy(h)
 
 
-@pytest.mark.parametrize("shape", list(range(7)))
+@pytest.mark.parametrize("shape", list(range(9)))
 @pytest.mark.parametrize("force64", [False, True])
 def test_every_batch_shape(torch_cuda, oracle_mod, graphs_mod, shape, force64):
     """Every compiled batched shape (CTA tiles and warp tiles), both offset widths, on R-MAT
