@@ -172,10 +172,22 @@ __device__ __forceinline__ int32_t dense_row(const BatchArgs<OffT>& a, int32_t v
   if (!a.dense_idx) return -1;
   const int32_t row = *(volatile int32_t*)(a.dense_idx + v);
   if (row >= 0) return row;
+  // a spent pool is seen by a plain read: no atomic on the shared count once it is full
+  if ((long long)*(volatile unsigned long long*)&a.ctl->dense_count >= a.dense_cap) return -1;
   const unsigned long long t = atomicAdd(&a.ctl->dense_count, 1ull);
   if ((long long)t >= a.dense_cap) return -1;
   const int32_t prev = atomicCAS(a.dense_idx + v, -1, (int32_t)t);
   return prev < 0 ? (int32_t)t : prev;
+}
+
+// A record slot in the overflow list, or -1 once the list is full. The count is read before
+// the atomic, so that claims past a full list (a deep graph's wave claims every vertex once
+// per root, at different levels) write their outputs at once instead of serialising on
+// the one counter.
+__device__ __forceinline__ long long ovf_slot(BatchCtl* ctl, long long cap) {
+  if ((long long)*(volatile unsigned long long*)&ctl->ovf_count >= cap) return -1;
+  const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
+  return (long long)o < cap ? (long long)o : -1;
 }
 
 // Claim bits of vertex v with parent u at wave level L, written into its dense row.
@@ -188,6 +200,54 @@ __device__ __forceinline__ void dense_write(const BatchArgs<OffT>& a, int32_t ro
     a.dense_lvl[(size_t)row * kMaxWave + b] = L;
   }
   atomicOr(a.dense_mask + row, bits);
+}
+
+// True when a claim carries a single root bit: it is written out at once (that root's level
+// and parent, two stores) instead of becoming a record. On graphs whose roots' frontiers
+// rarely meet (grids: one bit per claim) this takes the record atomics and the later output
+// pass off the claim path; claims of many bits at once (R-MAT) keep their records, whose
+// outputs are written in whole lines.
+__device__ __forceinline__ bool single_bit(unsigned long long bits) { return bits && !(bits & (bits - 1)); }
+
+// Writes the level (wave level L minus the slot's start) and the parent u of every bit of
+// `bits` of caller vertex vc.
+__device__ __forceinline__ void write_claim_now(unsigned long long bits, int32_t vc, int32_t u, int L,
+                                                int32_t* const* s_par, int32_t* const* s_lvl,
+                                                const int32_t* s_start) {
+  for (unsigned long long m = bits; m; m &= m - 1) {
+    const int b = __ffsll((long long)m) - 1;
+    s_par[b][vc] = u;
+    s_lvl[b][vc] = L - s_start[b];
+  }
+}
+
+// Where the claim of `bits` of vertex v (internal id) by u (caller id) at wave level L
+// goes: written at once if it carries one bit; else a record in the vertex's slot `slot`
+// (taken by the caller from its record count), past the slots its dense row, then the
+// overflow list, then written at once.
+template <typename OffT>
+__device__ __forceinline__ void record_claim(const BatchArgs<OffT>& a, int32_t v, unsigned long long bits, int32_t u,
+                                             int L, int slot, int32_t* const* s_par, int32_t* const* s_lvl,
+                                             const int32_t* s_start) {
+  int32_t drow = -1;
+  if (single_bit(bits)) {
+    write_claim_now(bits, a.old_id ? __ldg(a.old_id + v) : v, u, L, s_par, s_lvl, s_start);
+  } else if (slot < a.ev_slots) {
+    ClaimEvent ce;
+    ce.u = u;
+    ce.level = L;
+    ce.mask = bits;
+    a.ev[(size_t)v * a.ev_slots + slot] = ce;
+  } else if ((drow = dense_row(a, v)) >= 0) {
+    dense_write(a, drow, bits, u, L);
+  } else {
+    const long long o = ovf_slot(a.ctl, a.ovf_cap);
+    const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
+    if (o >= 0)
+      a.ovf[o] = OvfEvent{vc, u, bits, L, 0};
+    else
+      write_claim_now(bits, vc, u, L, s_par, s_lvl, s_start);  // no room
+  }
 }
 
 // Statistics of one output array: out[0] = degree sum of reached vertices (2 m_c),

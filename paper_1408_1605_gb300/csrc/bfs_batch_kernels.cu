@@ -279,29 +279,8 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
           if (f) {
             acc |= f;
             const int32_t uc = a.old_id ? __ldg(a.old_id + u) : (int32_t)u;
-            int32_t drow = -1;
-            if (nev < a.ev_slots) {
-              ClaimEvent ce;
-              ce.u = uc;
-              ce.level = L;
-              ce.mask = f;
-              a.ev[(size_t)v * a.ev_slots + nev] = ce;
-            } else if ((drow = dense_row(a, v)) >= 0) {
-              dense_write(a, drow, f, uc, L);
-            } else {
-              const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;
-              const unsigned long long o = atomicAdd(&a.ctl->ovf_count, 1ull);
-              if ((long long)o < a.ovf_cap) {
-                a.ovf[o] = OvfEvent{vc, uc, f, L, 0};
-              } else {
-                for (unsigned long long bits = f; bits; bits &= bits - 1) {  // no room: write now
-                  const int bb = __ffsll((long long)bits) - 1;
-                  s_par[bb][vc] = uc;
-                  s_lvl[bb][vc] = L - s_start[bb];
-                }
-              }
-            }
-            ++nev;
+            record_claim(a, v, f, uc, L, nev, s_par, s_lvl, s_start);
+            if (!single_bit(f)) ++nev;
           }
         }
         if (acc) {  // this lane owns v: plain stores
@@ -441,7 +420,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
       slot[j] = 0;
       fold[j] = 1ull;
       if (claimed[j]) {
-        slot[j] = atomicAdd(a.evc + vv[j], 1);
+        if (!single_bit(claimed[j])) slot[j] = atomicAdd(a.evc + vv[j], 1);
         fold[j] = atomicOr(Fn + vv[j], claimed[j]);
       }
     }
@@ -456,29 +435,8 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
       tot += __popc(__ballot_sync(full, first[j]));
       if (claimed[j]) {
         mine |= claimed[j];
-        // Parent event: the outputs are written after the wave (or the level) from it.
-        int32_t drow = -1;
-        if (slot[j] < a.ev_slots) {
-          ClaimEvent ce;
-          ce.u = uu[j];
-          ce.level = L;
-          ce.mask = claimed[j];
-          a.ev[(size_t)v * a.ev_slots + slot[j]] = ce;
-        } else if ((drow = dense_row(a, v)) >= 0) {
-          dense_write(a, drow, claimed[j], uu[j], L);
-        } else {
-          const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
-          const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
-          if ((long long)o < a.ovf_cap) {
-            a.ovf[o] = OvfEvent{vc, uu[j], claimed[j], L, 0};
-          } else {
-            for (unsigned long long bits = claimed[j]; bits; bits &= bits - 1) {  // no room: write now
-              const int b = __ffsll((long long)bits) - 1;
-              s_par[b][vc] = uu[j];
-              s_lvl[b][vc] = L - s_start[b];
-            }
-          }
-        }
+        // parent record: the outputs are written after the wave (or the level) from it
+        record_claim(a, v, claimed[j], uu[j], L, slot[j], s_par, s_lvl, s_start);
       }
     }
     if (nc + tot > WCAP) {
@@ -644,7 +602,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
       slot[j] = 0;
       fold[j] = 1ull;
       if (claimed[j]) {
-        slot[j] = atomicAdd(a.evc + vv[j], 1);
+        if (!single_bit(claimed[j])) slot[j] = atomicAdd(a.evc + vv[j], 1);
         fold[j] = atomicOr(Fn + vv[j], claimed[j]);
       }
     }
@@ -663,29 +621,8 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
       }
       if (claimed[j]) {
         mine |= claimed[j];
-        // Parent event: the outputs are written in vertex order after the level (emit).
-        int32_t drow = -1;
-        if (slot[j] < a.ev_slots) {
-          ClaimEvent ce;
-          ce.u = uu[j];
-          ce.level = L;
-          ce.mask = claimed[j];
-          a.ev[(size_t)v * a.ev_slots + slot[j]] = ce;
-        } else if ((drow = dense_row(a, v)) >= 0) {
-          dense_write(a, drow, claimed[j], uu[j], L);
-        } else {
-          const unsigned long long o = atomicAdd(&ctl->ovf_count, 1ull);
-          const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
-          if ((long long)o < a.ovf_cap) {
-            a.ovf[o] = OvfEvent{vc, uu[j], claimed[j], L, 0};
-          } else {
-            for (unsigned long long bits = claimed[j]; bits; bits &= bits - 1) {  // no room: write now
-              const int b = __ffsll((long long)bits) - 1;
-              s_par[b][vc] = uu[j];
-              s_lvl[b][vc] = L - s_start[b];
-            }
-          }
-        }
+        // parent record: the outputs are written after the wave (or the level) from it
+        record_claim(a, v, claimed[j], uu[j], L, slot[j], s_par, s_lvl, s_start);
       }
     }
     if (mine) atomicOr(&s_alive, mine);
@@ -744,13 +681,13 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
 }
 
 // After the expansion of frontier t (wave level L = t + 1): for every vertex v claimed in
-// it, F_{t+1}[v] holds the bits claimed and the per-vertex events hold their claimers.
-// Levels (L - start[b]) and parents are written in vertex order: a warp takes 32
-// consecutive vertices and loops over the union of their claimed bits, so each store
-// covers 32 consecutive entries of one root's row. When few vertices were claimed the
-// vertices come from the next frontier list instead (scattered, cheaper than a full pass).
-// Events that did not fit the per-vertex slots are applied last; the last CTA resets the
-// overflow count.
+// it, F_{t+1}[v] holds the bits claimed and the per-vertex records hold the claimers of
+// claims of several bits (single-bit claims were written at claim time). Their levels
+// (L - start[b]) and parents are written in vertex order: a warp takes 32 consecutive
+// vertices and loops over the union of their recorded bits, so each store covers 32
+// consecutive entries of one root's row. When few vertices were claimed the vertices come
+// from the next frontier list instead (scattered, cheaper than a full pass). Records that
+// did not fit the per-vertex slots are applied last; the last CTA resets the overflow count.
 // COUNT_ONLY (waves with deferred outputs and bottom-up levels allowed): only the per-root
 // frontier sizes and the direction choice; no output writes, and the events stay.
 template <typename OffT, bool COUNT_ONLY>
@@ -800,6 +737,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     int ne = 0;
     int32_t eu[kEventSlots];
     unsigned long long em[kEventSlots];
+    unsigned long long evb = 0ull;  // bits with a record (the others were written at claim time)
     if (f && !COUNT_ONLY) {
       ne = min(a.evc[v], kEventSlots);
 #pragma unroll
@@ -808,15 +746,17 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
           const ClaimEvent ce = a.ev[(size_t)v * a.ev_slots + k];
           eu[k] = ce.u;
           em[k] = ce.mask;
+          evb |= ce.mask;
         } else {
           eu[k] = 0;
           em[k] = 0ull;
         }
       }
-      a.evc[v] = 0;
+      if (ne) a.evc[v] = 0;
     }
-    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)f);
-    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(f >> 32));
+    const unsigned long long want = a.allow_bu ? f : evb;  // bits the loop below visits
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)want);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(want >> 32));
     unsigned long long any = ((unsigned long long)hi << 32) | lo;
     while (any) {
       const int b = __ffsll((long long)any) - 1;
@@ -825,7 +765,7 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
         const unsigned c = __popc(__ballot_sync(0xffffffffu, (f >> b) & 1ull));
         if (lane == (b & 31)) (b < 32 ? cnt_lo : cnt_hi) += c;
       }
-      if (!COUNT_ONLY && ((f >> b) & 1ull)) {
+      if (!COUNT_ONLY && ((evb >> b) & 1ull)) {
         s_lvl[b][vc] = L - s_start[b];
 #pragma unroll
         for (int k = 0; k < kEventSlots; ++k)
@@ -833,13 +773,14 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
       }
     }
   }
-  // overflow events (after every slot event of the level is consumed above)
+  // overflow records (after every slot record of the level is consumed above)
   const long long novf =
       COUNT_ONLY ? 0 : min((long long)*(volatile unsigned long long*)&ctl->ovf_count, a.ovf_cap);
   for (long long o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < novf; o += (int64_t)gridDim.x * blockDim.x) {
     const OvfEvent e = a.ovf[o];
     for (unsigned long long bits = e.mask; bits; bits &= bits - 1) {
       const int b = __ffsll((long long)bits) - 1;
+      s_lvl[b][e.v] = e.level - s_start[b];
       s_par[b][e.v] = e.u;
     }
   }
