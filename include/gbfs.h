@@ -146,11 +146,15 @@ GBFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
  *     top-down level hands over a bitmap. Results are the same BFS in every mode.
  *   BFS_OPT_UNPACKED_LEVELS (read only): levels of the last persistent search whose next
  *     frontier was rebuilt from a bitmap (-1 after a search in another loop mode).
- *   BFS_OPT_WAVE_DENSE_ROWS: a batched wave records each claim (root bits, parent, level) in
- *     one of 8 slots of the claimed vertex; a vertex claimed more often gets a dense row of
- *     64 parents and levels from a pool of n / 16 + 1024 rows. This option caps the rows a
- *     wave may use (-1, the default: the whole pool; 0: none). Claims left without room go to
- *     an overflow list of n / 4 + 65536 records, and past it are written out at once.
+ *   BFS_OPT_WAVE_DENSE_ROWS: a batched wave writes a claim of one root bit out at once and
+ *     records a claim of several bits (root bits, parent, level) in one of 8 slots of the
+ *     claimed vertex; a vertex claimed more often gets a dense row of 64 parents and levels
+ *     (512 bytes) from a pool. This option sizes the pool (-1, the default: a row per vertex
+ *     when those 520 bytes per vertex take at most a quarter of the free device memory when
+ *     the wave buffers are allocated, else n / 16 + 1024 rows; 0: none; at most n) and frees
+ *     the graph's wave buffers, which the next wave allocates again. Claims left without
+ *     room go to an overflow list of n / 4 + 65536 records, and past it are written out at
+ *     once.
  *   BFS_OPT_WAVE_LEVELS, BFS_OPT_WAVE_OVERFLOW (read only): levels run by the last batched
  *     wave on this graph, and how many of its claim records did not fit the per-vertex
  *     slots (they are applied from an overflow list when the wave's outputs are written). */

@@ -36,6 +36,8 @@ struct BatchCtl {
   long long seen;                 // degree sum of the frontiers expanded so far
   unsigned long long bitcnt[kMaxWave];  // per-root size of the new frontier (bottom-up choice)
   unsigned long long dense_count; // dense rows handed out in this wave
+  unsigned int recorded;          // the running expansion wrote claim records (per-level outputs)
+  unsigned int pad;
 };
 
 // Parent event of a claim: at wave level `level`, vertex u's edge claimed the bits `mask`
@@ -94,6 +96,7 @@ struct BatchArgs {
   int32_t* dense_lvl;             // [dense_cap][64]
   unsigned long long* dense_mask; // [dense_cap]
   long long dense_cap;
+  int dense_ident;                // the pool holds a row per vertex: row v is v's (no dense_idx)
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -120,6 +123,7 @@ struct BatchBufs {
   int32_t* dense_lvl = nullptr;
   unsigned long long* dense_mask = nullptr;
   long long dense_cap = 0;
+  bool dense_ident = false;
 };
 
 struct RootSeed {
@@ -162,13 +166,16 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.dense_lvl = b.dense_lvl;
   a.dense_mask = b.dense_mask;
   a.dense_cap = b.dense_cap;
+  a.dense_ident = b.dense_ident ? 1 : 0;
   return a;
 }
 
-// The dense row of vertex v, handed out on first use (-1 when there are none or the pool is
-// spent). Two claimers racing for a new row both take one; the loser's stays unused.
+// The dense row of vertex v: row v when the pool holds one per vertex, else handed out on
+// first use (-1 when there are none or the pool is spent). Two claimers racing for a new row
+// both take one; the loser's stays unused.
 template <typename OffT>
 __device__ __forceinline__ int32_t dense_row(const BatchArgs<OffT>& a, int32_t v) {
+  if (a.dense_ident) return v;
   if (!a.dense_idx) return -1;
   const int32_t row = *(volatile int32_t*)(a.dense_idx + v);
   if (row >= 0) return row;
@@ -224,30 +231,36 @@ __device__ __forceinline__ void write_claim_now(unsigned long long bits, int32_t
 // Where the claim of `bits` of vertex v (internal id) by u (caller id) at wave level L
 // goes: written at once if it carries one bit; else a record in the vertex's slot `slot`
 // (taken by the caller from its record count), past the slots its dense row, then the
-// overflow list, then written at once.
+// overflow list, then written at once. Returns whether a record was written.
 template <typename OffT>
-__device__ __forceinline__ void record_claim(const BatchArgs<OffT>& a, int32_t v, unsigned long long bits, int32_t u,
+__device__ __forceinline__ bool record_claim(const BatchArgs<OffT>& a, int32_t v, unsigned long long bits, int32_t u,
                                              int L, int slot, int32_t* const* s_par, int32_t* const* s_lvl,
                                              const int32_t* s_start) {
   int32_t drow = -1;
   if (single_bit(bits)) {
     write_claim_now(bits, a.old_id ? __ldg(a.old_id + v) : v, u, L, s_par, s_lvl, s_start);
-  } else if (slot < a.ev_slots) {
+    return false;
+  }
+  if (slot < a.ev_slots) {
     ClaimEvent ce;
     ce.u = u;
     ce.level = L;
     ce.mask = bits;
     a.ev[(size_t)v * a.ev_slots + slot] = ce;
-  } else if ((drow = dense_row(a, v)) >= 0) {
-    dense_write(a, drow, bits, u, L);
-  } else {
-    const long long o = ovf_slot(a.ctl, a.ovf_cap);
-    const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
-    if (o >= 0)
-      a.ovf[o] = OvfEvent{vc, u, bits, L, 0};
-    else
-      write_claim_now(bits, vc, u, L, s_par, s_lvl, s_start);  // no room
+    return true;
   }
+  if ((drow = dense_row(a, v)) >= 0) {
+    dense_write(a, drow, bits, u, L);
+    return true;
+  }
+  const long long o = ovf_slot(a.ctl, a.ovf_cap);
+  const int32_t vc = a.old_id ? __ldg(a.old_id + v) : v;  // outputs use caller ids
+  if (o >= 0) {
+    a.ovf[o] = OvfEvent{vc, u, bits, L, 0};
+    return true;
+  }
+  write_claim_now(bits, vc, u, L, s_par, s_lvl, s_start);  // no room
+  return false;
 }
 
 // Statistics of one output array: out[0] = degree sum of reached vertices (2 m_c),
@@ -256,9 +269,11 @@ template <typename OffT>
 void launch_level_stats(const OffT* off, const int32_t* new_id, int64_t n, const int32_t* levels, long long* out,
                         int num_sms, cudaStream_t st);
 
-cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots = kEventSlots);
+// dense_rows: rows of the dense-row pool of waves with ev_slots = kEventSlotsWave (-1: the
+// default, one per 16 vertices).
+cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots = kEventSlots, long long dense_rows = -1);
 void free_batch_bufs(BatchBufs& b);
-size_t batch_bufs_bytes(const GraphDev& g, int ev_slots = kEventSlots);
+size_t batch_bufs_bytes(const GraphDev& g, int ev_slots = kEventSlots, long long dense_rows = -1);
 
 template <typename OffT>
 void launch_batch_clear(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);

@@ -49,12 +49,13 @@ __global__ void k_batch_clear(BatchArgs<OffT> a) {
     a.evc[v] = 0;
     if (a.dense_idx) a.dense_idx[v] = -1;
   }
-  if (a.dense_idx)
+  if (a.dense_idx || a.dense_ident)
     for (int64_t r = tid; r < a.dense_cap; r += stride) a.dense_mask[r] = 0ull;
   if (tid == 0) {
     a.ctl->ovf_count = 0;
     a.ctl->emit_done = 0;
     a.ctl->dense_count = 0;
+    a.ctl->recorded = 0;
   }
 }
 
@@ -249,7 +250,7 @@ template <typename OffT, int WCAP>
 __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long long* __restrict__ F,
                                unsigned long long* Fn, unsigned long long active, int nxt, int q3n, int2* wbuf,
                                int32_t* const* s_par, int32_t* const* s_lvl, const int32_t* s_start, int L,
-                               unsigned long long* s_alive) {
+                               unsigned long long* s_alive, int* s_rec) {
   static_assert(WCAP >= 64, "per-warp claim buffer too small");
   constexpr int P = (WCAP + 31) / 32;
   const unsigned full = 0xffffffffu;
@@ -258,6 +259,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
   const int64_t nwarps = (int64_t)gridDim.x * wpb;
   int nc = 0;  // warp-uniform
   unsigned long long mine = 0ull;
+  bool rec = false;  // this thread wrote a claim record
   for (int64_t w = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); w * 32 < a.n; w += nwarps) {
     const int64_t x = w * 32 + lane;
     const int32_t v = (int32_t)x;
@@ -279,7 +281,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
           if (f) {
             acc |= f;
             const int32_t uc = a.old_id ? __ldg(a.old_id + u) : (int32_t)u;
-            record_claim(a, v, f, uc, L, nev, s_par, s_lvl, s_start);
+            rec |= record_claim(a, v, f, uc, L, nev, s_par, s_lvl, s_start);
             if (!single_bit(f)) ++nev;
           }
         }
@@ -306,6 +308,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
   __syncwarp();
   if (nc > 0) batch_warp_flush<OffT, P>(a, nxt, q3n, wbuf, nc);
   if (mine) atomicOr(s_alive, mine);
+  if (rec) *s_rec = 1;
 }
 
 // The top-down step of a wave with warp-sized tiles (the batched form of the single-source
@@ -320,7 +323,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
 template <typename OffT, int E, int WCAP>
 __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt, int q3, int q3n, int64_t nf,
                               OffT r, int2* wbuf, int32_t* const* s_par, int32_t* const* s_lvl,
-                              const int32_t* s_start, unsigned long long* s_alive) {
+                              const int32_t* s_start, unsigned long long* s_alive, int* s_rec) {
   constexpr int TW = 32 * E;
   static_assert(TW % kChunk == 0, "warp tiles must start on chunk-index boundaries");
   static_assert(WCAP >= TW && WCAP % 32 == 0, "claim buffer must hold one full tile");
@@ -338,6 +341,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
   const int64_t wpb = blockDim.x >> 5;
   int nc = 0;  // warp-uniform
   unsigned long long mine = 0ull;
+  bool rec = false;  // this thread wrote a claim record
   for (int64_t tile = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles; tile += (int64_t)gridDim.x * wpb) {
     const OffT e0 = (OffT)(tile * TW);
     const int cnt = (int)min((OffT)TW, r - e0);
@@ -436,7 +440,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
       if (claimed[j]) {
         mine |= claimed[j];
         // parent record: the outputs are written after the wave (or the level) from it
-        record_claim(a, v, claimed[j], uu[j], L, slot[j], s_par, s_lvl, s_start);
+        rec |= record_claim(a, v, claimed[j], uu[j], L, slot[j], s_par, s_lvl, s_start);
       }
     }
     if (nc + tot > WCAP) {
@@ -456,6 +460,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
   // OR of the lanes' claimed bits, one shared atomic per warp
   unsigned lo = __reduce_or_sync(full, (unsigned)mine), hi = __reduce_or_sync(full, (unsigned)(mine >> 32));
   if (lane == 0 && (lo | hi)) atomicOr(s_alive, ((unsigned long long)hi << 32) | lo);
+  if (rec) *s_rec = 1;
 }
 
 // TPS: resident threads per SM the registers are sized for (0: the compiler's choice).
@@ -476,7 +481,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
   __shared__ int32_t s_start[kMaxWave];
   __shared__ OffT s_warp[33];
   __shared__ unsigned long long s_resv, s_alive;
-  __shared__ int s_nclaim, s_klo, s_kend;
+  __shared__ int s_nclaim, s_klo, s_kend, s_rec;
 
   BatchCtl* ctl = a.ctl;
   const int L = *(volatile int*)&ctl->level;
@@ -495,6 +500,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
   if (threadIdx.x == 0) {
     s_nclaim = 0;
     s_alive = 0ull;
+    s_rec = 0;
   }
   // Frontier t - 1 is no longer read by anyone: clear its masks so that the buffer can
   // collect frontier t + 2.
@@ -516,12 +522,13 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
   if (bu) {
     __syncthreads();  // slot pointers staged
     batch_bu_level<OffT, WCAP>(a, F, Fn, *(volatile unsigned long long*)&ctl->alive[cur], nxt, q3n,
-                               s_claim + warp * WCAP, s_par, s_lvl, s_start, L, &s_alive);
+                               s_claim + warp * WCAP, s_par, s_lvl, s_start, L, &s_alive, &s_rec);
   } else if constexpr (WT) {
     __syncthreads();  // slot pointers staged
     batch_td_warp<OffT, E, WCAP>(a, L, cur, nxt, q3, q3n, nf, r, s_claim + warp * WCAP, s_par, s_lvl, s_start,
-                                 &s_alive);
+                                 &s_alive, &s_rec);
   }
+  bool rec = false;  // this thread wrote a claim record (CTA tiles)
   for (int64_t tile = (bu || WT) ? ntiles : (int64_t)blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const OffT e0 = (OffT)(tile * T);
     const int cnt = (int)min((OffT)T, r - e0);
@@ -622,7 +629,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
       if (claimed[j]) {
         mine |= claimed[j];
         // parent record: the outputs are written after the wave (or the level) from it
-        record_claim(a, v, claimed[j], uu[j], L, slot[j], s_par, s_lvl, s_start);
+        rec |= record_claim(a, v, claimed[j], uu[j], L, slot[j], s_par, s_lvl, s_start);
       }
     }
     if (mine) atomicOr(&s_alive, mine);
@@ -645,12 +652,14 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
       if (threadIdx.x == 0) s_nclaim = 0;
     }
   }
+  if (rec) s_rec = 1;
   __syncthreads();
   const int nc = bu ? 0 : s_nclaim;
   if (nc > 0) batch_flush<OffT, BLOCK, CLAIM>(a, nxt, q3n, s_claim, nc, s_warp, &s_resv);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_alive) atomicOr(&ctl->alive[nxt], s_alive);
+    if (s_rec) *(volatile unsigned*)&ctl->recorded = 1u;
     __threadfence();
     const unsigned tdone = atomicAdd(&ctl->done[cur], 1u);
     if (tdone == gridDim.x - 1) {
@@ -697,6 +706,12 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
   __shared__ int32_t s_start[kMaxWave];
   __shared__ unsigned long long s_cnt[kMaxWave];
   BatchCtl* ctl = a.ctl;
+  // Nothing to write when the level's claims were all written at claim time (single root
+  // bits, the rule on grids) and there is no direction choice to make: every CTA sees the
+  // same words, so the whole grid leaves.
+  if (!COUNT_ONLY && !a.allow_bu && !*(volatile unsigned*)&ctl->recorded &&
+      !*(volatile unsigned long long*)&ctl->ovf_count)
+    return;
   const int Lnext = *(volatile int*)&ctl->level;  // already advanced by the expansion
   const int L = Lnext - 1;
   const int t = L - 1;
@@ -796,7 +811,10 @@ __global__ void __launch_bounds__(256) k_batch_emit(BatchArgs<OffT> a) {
     __threadfence();
     if (atomicAdd(&ctl->emit_done, 1u) == gridDim.x - 1) {
       __threadfence();
-      if (!COUNT_ONLY) ctl->ovf_count = 0;  // with deferred outputs the overflow list lasts the wave
+      if (!COUNT_ONLY) {
+        ctl->ovf_count = 0;  // with deferred outputs the overflow list lasts the wave
+        ctl->recorded = 0;
+      }
       ctl->emit_done = 0;
       if (a.allow_bu) {
         // A bottom-up level makes every vertex look for the bits of every active root, so a
@@ -864,8 +882,8 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
       const int32_t v = a.new_id ? __ldg(a.new_id + vc) : vc;
       vis = a.visited[v];
       const int ne = vis ? min(a.evc[v], K) : 0;
-      if (ne == K && a.dense_idx) {  // claims past the slots went to the vertex's dense row
-        drow = a.dense_idx[v];
+      if (ne == K && (a.dense_idx || a.dense_ident)) {  // claims past the slots: the vertex's dense row
+        drow = a.dense_ident ? v : a.dense_idx[v];
         if (drow >= 0) dm = a.dense_mask[drow];
       }
       for (int k = 0; k < ne; ++k) {

@@ -637,7 +637,7 @@ GBFS_API bfs_status bfs_graph_set_option(bfs_graph_t G, int option, int64_t valu
       if (G->dense_rows != value) {
         if (G->last_done) cudaEventSynchronize(G->last_done);
         G->dense_rows = value;
-        set_batch_shape(G, G->batch_shape);  // the captured wave loop holds the old arguments
+        destroy_batch_state(G);  // the pool is sized when the wave state is next allocated
       }
       return BFS_OK;
     case BFS_OPT_FRONTIER:

@@ -178,15 +178,16 @@ def test_waves_with_bottom_up_levels(torch_cuda, oracle_mod, graphs_mod, policy,
             capi.bfs_graph_destroy(h)
 
 
-@pytest.mark.parametrize("dense_rows", [-1, 1, 0])
+@pytest.mark.parametrize("dense_rows", [-1, 1, 0, 1 << 20])
 @pytest.mark.parametrize("bottom_up", [0, 1])
 def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, bottom_up, dense_rows):
-    """Hub vertices claimed by many frontier vertices with disjoint root bits: 64 roots at
-    the leaves of a star (every leaf's edge claims its own bit of the centre, 64 parent
-    events at one vertex in one level), and a second hub joined to every leaf, so that the
-    claims of a wave spill past the per-vertex slots: into dense rows (all the pool, one row,
-    none), then the overflow list. Every root still gets the oracle's levels and a valid
-    tree."""
+    """Hub vertices claimed by many frontier vertices with disjoint root bits: roots at the
+    leaves of a star (every leaf's edge claims its own bits of the centre, up to 64 claims at
+    one vertex in one level), and a second hub joined to every leaf. Claims of one root bit
+    are written at once; with each leaf holding two roots (repeated roots), every claim
+    carries two bits and the wave's records spill past the per-vertex slots: into dense rows
+    (the default pool, one row, none, a row per vertex), then the overflow list. Every root
+    still gets the oracle's levels and a valid tree."""
     from paper_1408_1605_gb300 import capi
 
     leaves = np.arange(1, 65, dtype=np.int32)
@@ -199,6 +200,7 @@ def test_claims_beyond_the_event_slots(torch_cuda, oracle_mod, graphs_mod, botto
             capi.bfs_graph_set_option(h, capi.BFS_OPT_BOTTOM_UP, bottom_up)
             capi.bfs_graph_set_option(h, capi.BFS_OPT_WAVE_DENSE_ROWS, dense_rows)
             check_wave(capi, oracle_mod, torch_cuda, h, g, leaves)
+            check_wave(capi, oracle_mod, torch_cuda, h, g, np.repeat(leaves[:32], 2))
             check_wave(capi, oracle_mod, torch_cuda, h, g, np.concatenate([leaves[:32], [0, 65] * 16]))
             check_wave(capi, oracle_mod, torch_cuda, h, g, leaves[::-1].copy(), host_out=True)
         finally:
