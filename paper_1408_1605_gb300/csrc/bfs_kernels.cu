@@ -1191,14 +1191,46 @@ void launch_scan_frontier(const GraphDev& g, const int32_t* front, int64_t nf, i
                                             ws.ctl);
 }
 
+// Sets a kernel's dynamic shared memory size and the smallest shared-memory carveout that
+// keeps the CTAs per SM its registers and warps allow, so that the rest of the SM's 256 KB
+// is L1 for the visited-bitmap probes (the driver otherwise picks a larger carveout than the
+// warp tiles' small claim buffers need). Returns the CTAs per SM.
+template <typename K>
+static int fit_carveout(K kern, int block, size_t dyn_bytes) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int full = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full, kern, block, dyn_bytes) != cudaSuccess || full < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  cudaFuncAttributes fa{};
+  int dev = 0, smem_sm = 0;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      smem_sm <= 0) {
+    cudaGetLastError();
+    return full;
+  }
+  const size_t need = (size_t)full * (dyn_bytes + fa.sharedSizeBytes + 1024);  // 1 KB reserved per CTA
+  const int pct = (int)std::min<size_t>(100, std::max<size_t>(1, (need * 100 + smem_sm - 1) / smem_sm));
+  int got = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, kern, block, dyn_bytes) != cudaSuccess || got < full) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return full;
+  }
+  return got;
+}
+
 template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static cudaError_t launch_expand_t(const ExpandArgs<OffT>& a, int grid, cudaStream_t st) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
   auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT, TPS>;
   static bool attr_set = false;  // per template instance; set once per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
+    fit_carveout(kern, BLOCK, bytes);
     attr_set = true;
   }
   kern<<<grid, BLOCK, bytes, st>>>(a);
@@ -1208,11 +1240,7 @@ static cudaError_t launch_expand_t(const ExpandArgs<OffT>& a, int grid, cudaStre
 template <typename OffT, int BLOCK, int E, int CLAIM, bool WT, int TPS>
 static int occupancy_t(int num_sms) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
-  auto kern = k_expand<OffT, BLOCK, E, CLAIM, WT, TPS>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
-  return std::max(1, per_sm) * num_sms;
+  return fit_carveout(k_expand<OffT, BLOCK, E, CLAIM, WT, TPS>, BLOCK, bytes) * num_sms;
 }
 
 // Table of compiled shapes (BLOCK, E, CLAIM, tiles, TPS): tiles 0 = one tile of BLOCK x E
@@ -1244,8 +1272,7 @@ static cudaError_t launch_persistent_t(const PersistArgs<OffT>& a, int grid, cud
                                 : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT, TPS>;
   static bool attr_set[2] = {false, false};
   if (!attr_set[a.allow_bottom_up ? 1 : 0]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
+    fit_carveout(kern, BLOCK, bytes);  // the same settings the grid size was computed under
     attr_set[a.allow_bottom_up ? 1 : 0] = true;
   }
   PersistArgs<OffT> copy = a;
@@ -1259,10 +1286,7 @@ static int persistent_grid_t(int num_sms, bool with_bu) {
   constexpr size_t bytes = ShapeSmem<OffT, BLOCK, E, CLAIM, WT>::bytes;
   auto kern = with_bu ? k_bfs_persistent<OffT, BLOCK, E, CLAIM, true, WT, TPS>
                       : k_bfs_persistent<OffT, BLOCK, E, CLAIM, false, WT, TPS>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, bytes) != cudaSuccess) per_sm = 1;
-  return std::max(1, per_sm) * num_sms;
+  return fit_carveout(kern, BLOCK, bytes) * num_sms;
 }
 
 template <typename OffT>
