@@ -886,11 +886,24 @@ def run_serve(args) -> int:
             capi.bfs_serve_wait(srv, tk, 600000)
         offered = time.perf_counter() - t0
         rep = capi.bfs_serve_stats(srv)
+        # per graph: latency (submission to completion) and service time (admission to completion)
+        lat = [[] for _ in gs]
+        svc = [[] for _ in gs]
+        for i, tk in enumerate(tickets):
+            st = capi.bfs_serve_result(srv, tk)
+            lat[int(gsel[i])].append(st.expand_ms)
+            svc[int(gsel[i])].append(st.device_ms)
         capi.bfs_serve_destroy(srv)
+        per_graph = {names[gi]: {"queries": len(lat[gi]),
+                                 "p50_ms": round(float(np.percentile(lat[gi], 50)), 2),
+                                 "p99_ms": round(float(np.percentile(lat[gi], 99)), 2),
+                                 "service_mean_ms": round(float(np.mean(svc[gi])), 2)}
+                     for gi in range(len(gs)) if lat[gi]}
         results.append({"offered_qps": rate, "queries": nq, "achieved_qps": round(nq / offered, 1),
                         "p50_ms": round(rep["latency_p50_ms"], 3), "p99_ms": round(rep["latency_p99_ms"], 3),
                         "mean_ms": round(rep["latency_mean_ms"], 3), "gteps": round(rep["gteps"], 3),
-                        "max_concurrent": rep["max_concurrent"], "levels": rep["levels"]})
+                        "max_concurrent": rep["max_concurrent"], "levels": rep["levels"],
+                        "per_graph": per_graph})
         log(f"[serve] rate {rate:.0f}: {results[-1]}")
     for h in hs:
         capi.bfs_graph_destroy(h)

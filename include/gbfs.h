@@ -369,8 +369,9 @@ GBFS_API bfs_status bfs_serve_wait(bfs_server_t srv, uint64_t ticket, int timeou
 GBFS_API bfs_status bfs_serve_cancel(bfs_server_t srv, uint64_t ticket);
 
 /* Statistics of a completed query (depth, vertices reached, m_c; device_ms = time from
- * admission to completion) and release of its ticket. Returns the query's status;
- * BFS_ERR_BUSY if it is not done yet. */
+ * admission to completion, expand_ms = time from submission to completion, i.e. the query's
+ * latency) and release of its ticket. Returns the query's status; BFS_ERR_BUSY if it is not
+ * done yet. */
 GBFS_API bfs_status bfs_serve_result(bfs_server_t srv, uint64_t ticket, bfs_stats *stats);
 
 /* Latency percentiles, throughput and counters since creation. */

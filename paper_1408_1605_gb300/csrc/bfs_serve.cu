@@ -402,8 +402,9 @@ static void wave_round(bfs_server_s* S, Wave* w) {
       r->stats.edges_traversed = w->stats_host[3 * b + 0] / 2;
       r->stats.vertices_reached = w->stats_host[3 * b + 1];
       r->stats.depth = (int32_t)w->stats_host[3 * b + 2];
-      r->stats.device_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_admit).count();
-      r->stats.expand_ms = r->stats.device_ms;
+      const Clock::time_point now = Clock::now();
+      r->stats.device_ms = std::chrono::duration<double, std::milli>(now - r->t_admit).count();
+      r->stats.expand_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
       finish_req(S, r, BFS_OK, "");
       w->sg->depth_sum += r->stats.depth;
       ++w->sg->depth_n;

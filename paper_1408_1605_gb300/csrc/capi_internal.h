@@ -13,7 +13,7 @@ namespace gbfs {
 
 struct BatchState;  // multi-source work buffers, see bfs_batch.cu
 
-// Expansion shape used unless the autotuner or GBFS_SHAPE picks another.
+// Expansion shape used unless the autotuner or bfs_graph_set_shape picks another.
 constexpr int kDefaultShape = 7;  // warp tiles of 128 edges, 48 registers (fastest on R-MAT)
 
 bfs_status fail(bfs_status s, const std::string& msg);
