@@ -71,6 +71,8 @@ struct Ctl {
 constexpr int kMaxLevelTimes = 64;
 struct PCtl {
   unsigned long long counter[3];
+  unsigned int pfx[3];             // by level % 3: first bitmap word not full (visited prefix scan)
+  unsigned int pad_pfx;
   unsigned int bar_count;
   unsigned int bar_gen;
   unsigned int error;
