@@ -97,6 +97,9 @@ struct BatchArgs {
   unsigned long long* dense_mask; // [dense_cap]
   long long dense_cap;
   int dense_ident;                // the pool holds a row per vertex: row v is v's (no dense_idx)
+  // Waves whose roots all start at level 0 (bfs_run_batch): bit v set once V[v] holds every
+  // root still searching, so no edge into v can claim again (NULL: not kept).
+  uint32_t* done;
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -124,6 +127,7 @@ struct BatchBufs {
   unsigned long long* dense_mask = nullptr;
   long long dense_cap = 0;
   bool dense_ident = false;
+  uint32_t* done = nullptr;         // [n / 32] (waves with deferred outputs only)
 };
 
 struct RootSeed {
@@ -167,6 +171,7 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.dense_mask = b.dense_mask;
   a.dense_cap = b.dense_cap;
   a.dense_ident = b.dense_ident ? 1 : 0;
+  a.done = b.done;
   return a;
 }
 

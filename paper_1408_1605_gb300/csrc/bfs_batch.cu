@@ -82,6 +82,7 @@ void free_batch_bufs(BatchBufs& b) {
   cudaFree(b.ev);
   cudaFree(b.ovf);
   cudaFree(b.dense_idx);
+  cudaFree(b.done);
   cudaFree(b.dense_par);
   cudaFree(b.dense_lvl);
   cudaFree(b.dense_mask);
@@ -122,6 +123,7 @@ size_t batch_bufs_bytes(const GraphDev& g, int ev_slots, long long dense_rows) {
   const size_t ovf_cap = (size_t)overflow_cap(g, ev_slots);
   const size_t dense = (size_t)dense_rows_cap(g, ev_slots, dense_rows);
   return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots + (dense ? 4 : 0)) +
+         (ev_slots == kEventSlotsWave ? (size_t)(g.n + 31) / 32 * 4 : 0) +
          ovf_cap * sizeof(OvfEvent) + 2 * 16 * (size_t)(g.nnz / kChunk + 2) + dense * (8 * kMaxWave + 8) +
          64 * 1024;
 }
@@ -156,6 +158,7 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots, long
     if (e == cudaSuccess) e = dalloc(&b.dense_lvl, (size_t)b.dense_cap * kMaxWave);
     if (e == cudaSuccess) e = dalloc(&b.dense_mask, (size_t)b.dense_cap);
   }
+  if (ev_slots == kEventSlotsWave && e == cudaSuccess) e = dalloc(&b.done, (size_t)(g.n + 31) / 32);
   if (e == cudaSuccess) e = cudaMemset(b.evc, 0, sizeof(int32_t) * (size_t)g.n);
   if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
   if (e != cudaSuccess) {
@@ -196,6 +199,12 @@ BatchArgs<OffT> batch_args(const bfs_graph_s* G) {
   a.alpha = G->alpha;
   a.beta = G->beta;
   a.defer = 1;  // every event kept until the wave ends; the outputs are written once, after it
+  // Done marks only for graphs in input order: there a vertex's 64-bit visited mask is a
+  // DRAM-random read that a mark spares (uniform s26 waves 415 vs 469 ms). On graphs
+  // relabelled by degree the masks most edges read are the hubs', few and L2-resident, and
+  // the extra mark read cost more than it saved (R-MAT s26 waves 80 vs 71 ms, s22 6.9 vs
+  // 4.0 ms).
+  if (G->g.old_id) a.done = nullptr;
   if (a.dense_cap <= 0) {  // no dense rows: overflow list, then direct writes
     a.dense_idx = nullptr;
     a.dense_ident = 0;

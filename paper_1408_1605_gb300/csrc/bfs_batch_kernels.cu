@@ -51,6 +51,8 @@ __global__ void k_batch_clear(BatchArgs<OffT> a) {
   }
   if (a.dense_idx || a.dense_ident)
     for (int64_t r = tid; r < a.dense_cap; r += stride) a.dense_mask[r] = 0ull;
+  if (a.done)
+    for (int64_t w = tid; w < (a.n + 31) / 32; w += stride) a.done[w] = 0u;
   if (tid == 0) {
     a.ctl->ovf_count = 0;
     a.ctl->emit_done = 0;
@@ -320,7 +322,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
 // searches the scan. Per edge (u, v): new = F_t[u] & ~V[v], claimed = new & ~atomicOr(V[v],
 // new); each claim records a parent event, and the first claim of v in this level appends v
 // to frontier t + 1 through the warp's claim buffer.
-template <typename OffT, int E, int WCAP>
+template <typename OffT, int E, int WCAP, bool DONE>
 __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt, int q3, int q3n, int64_t nf,
                               OffT r, int2* wbuf, int32_t* const* s_par, int32_t* const* s_lvl,
                               const int32_t* s_start, unsigned long long* s_alive, int* s_rec) {
@@ -342,6 +344,11 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
   int nc = 0;  // warp-uniform
   unsigned long long mine = 0ull;
   bool rec = false;  // this thread wrote a claim record
+  // Done marks (waves whose roots all start at level 0): the roots still searching are those
+  // of frontier t; a vertex whose visited mask holds all of them can never be claimed again
+  // (the set only shrinks), so its mask is not read. A missing mark only costs the read.
+  uint32_t* done = DONE ? a.done : nullptr;
+  const unsigned long long act = DONE ? *(volatile unsigned long long*)&ctl->alive[cur] : 0ull;
   for (int64_t tile = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles; tile += (int64_t)gridDim.x * wpb) {
     const OffT e0 = (OffT)(tile * TW);
     const int cnt = (int)min((OffT)TW, r - e0);
@@ -407,11 +414,28 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
         atomicOr(&ctl->error, kErrColumnRange);
         ok[j] = false;
       }
-      nb[j] = ok[j] ? (ff[j] & ~a.visited[vv[j]]) : 0ull;
+      if constexpr (DONE) {
+        // a vertex marked done holds every searching root's bit: no 64-bit visited-mask read
+        // (the marks are read from L2, so that one set during the level is seen at once)
+        if (ok[j] && ((__ldcg(done + ((uint32_t)vv[j] >> 5)) >> (vv[j] & 31)) & 1u)) ok[j] = false;
+        const unsigned long long vm = ok[j] ? a.visited[vv[j]] : ~0ull;
+        nb[j] = ff[j] & ~vm;
+        // complete but not yet marked (its last bit came at an earlier level): mark it
+        if (ok[j] && (vm & act) == act) atomicOr(done + ((uint32_t)vv[j] >> 5), 1u << (vv[j] & 31));
+      } else {
+        nb[j] = ok[j] ? (ff[j] & ~a.visited[vv[j]]) : 0ull;
+      }
     }
     unsigned long long claimed[E];
 #pragma unroll
-    for (int j = 0; j < E; ++j) claimed[j] = nb[j] ? nb[j] & ~atomicOr(a.visited + vv[j], nb[j]) : 0ull;
+    for (int j = 0; j < E; ++j) {
+      claimed[j] = 0ull;
+      if (nb[j]) {
+        const unsigned long long old = atomicOr(a.visited + vv[j], nb[j]);
+        claimed[j] = nb[j] & ~old;
+        if (DONE && ((old | nb[j]) & act) == act) atomicOr(done + ((uint32_t)vv[j] >> 5), 1u << (vv[j] & 31));
+      }
+    }
     unsigned wc = 0;  // bit j: some lane of the warp claimed with edge j (warp-uniform)
 #pragma unroll
     for (int j = 0; j < E; ++j)
@@ -525,8 +549,12 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
                                s_claim + warp * WCAP, s_par, s_lvl, s_start, L, &s_alive, &s_rec);
   } else if constexpr (WT) {
     __syncthreads();  // slot pointers staged
-    batch_td_warp<OffT, E, WCAP>(a, L, cur, nxt, q3, q3n, nf, r, s_claim + warp * WCAP, s_par, s_lvl, s_start,
-                                 &s_alive, &s_rec);
+    if (a.done)  // grid-uniform
+      batch_td_warp<OffT, E, WCAP, true>(a, L, cur, nxt, q3, q3n, nf, r, s_claim + warp * WCAP, s_par, s_lvl,
+                                         s_start, &s_alive, &s_rec);
+    else
+      batch_td_warp<OffT, E, WCAP, false>(a, L, cur, nxt, q3, q3n, nf, r, s_claim + warp * WCAP, s_par, s_lvl,
+                                          s_start, &s_alive, &s_rec);
   }
   bool rec = false;  // this thread wrote a claim record (CTA tiles)
   for (int64_t tile = (bu || WT) ? ntiles : (int64_t)blockIdx.x; tile < ntiles; tile += gridDim.x) {
