@@ -409,10 +409,11 @@ GBFS_API bfs_status bfs_graph_get_shape(bfs_graph_t g, int kind, int *shape);
  *   BFS_KERNEL_SINGLE: candidates c = loop x shape: c < count uses BFS_LOOP_GRAPH with shape
  *     c, count <= c < 2 count BFS_LOOP_PERSISTENT with shape c - count and as many CTAs as
  *     fit, 2 count <= c < 3 count BFS_LOOP_PERSISTENT with shape c - 2 count and 2 CTAs per
- *     SM (BFS_OPT_PERSIST_CTAS; with BFS_OPT_BOTTOM_UP set, only the persistent ones; the
- *     others report -1). One warm-up search, then one bfs_run per root; ms_per_shape[c] =
- *     mean device ms per root. The winner's loop mode, CTAs per SM and shape are set on the
- *     graph. ms_per_shape: NULL or double[3 * count].
+ *     SM, 3 count <= c < 4 count the same with 1 CTA per SM (BFS_OPT_PERSIST_CTAS; with
+ *     BFS_OPT_BOTTOM_UP set, only the persistent ones; the others report -1). One warm-up
+ *     search, then one bfs_run per root; ms_per_shape[c] = mean device ms per root. The
+ *     winner's loop mode, CTAs per SM and shape are set on the graph. ms_per_shape: NULL or
+ *     double[4 * count].
  *   BFS_KERNEL_BATCH: candidates = shapes; n_roots <= 64; one warm-up wave and one timed
  *     wave per shape; ms_per_shape[s] = device ms per wave (double[count]).
  * count = bfs_shape_count(kind); best_shape: NULL or the winning candidate index.

@@ -387,7 +387,7 @@ def bfs_graph_get_shape(graph: int, kind: int) -> int:
 def bfs_tune(graph: int, kind: int, roots, levels, parents, stream=None):
     """Returns (best candidate, [ms per candidate]); single-source candidates are
     (graph loop, shape 0..count-1), (persistent loop, shape 0..count-1), then (persistent
-    loop with 2 CTAs per SM, shape 0..count-1)."""
+    loop with 2 CTAs per SM, shape 0..count-1), then (with 1 CTA per SM, shape 0..count-1)."""
     import numpy as np
 
     r = np.ascontiguousarray(roots, dtype=np.int32)
@@ -398,7 +398,7 @@ def bfs_tune(graph: int, kind: int, roots, levels, parents, stream=None):
         need = bfs_graph_info(graph)[0] * (1 if single else r.size)
         _check_int32_out("levels", levels, need)
         _check_int32_out("parents", parents, need)
-    n = bfs_shape_count(kind) * (3 if kind == BFS_KERNEL_SINGLE else 1)
+    n = bfs_shape_count(kind) * (4 if kind == BFS_KERNEL_SINGLE else 1)
     ms = (ctypes.c_double * max(n, 1))()
     best = ctypes.c_int(-1)
     check(lib().bfs_tune(graph, int(kind), r.ctypes.data, int(r.size), ptr(levels), ptr(parents),

@@ -1323,7 +1323,8 @@ static int occupancy_t(int num_sms) {
   X(5, 128, 4, 128, 1, 1024)   \
   X(6, 128, 8, 256, 1, 1024)   \
   X(7, 128, 4, 128, 1, 1280)   \
-  X(8, 128, 4, 256, 1, 1280)
+  X(8, 128, 4, 256, 1, 1280)   \
+  X(9, 512, 4, 128, 1, 1024)
 
 const ExpandShape kExpandShapes[] = {
 #define X(id, b, e, c, w, t) {id, b, e, c, w},

@@ -64,10 +64,11 @@ GBFS_API bfs_status bfs_tune(bfs_graph_t G, int kind, const int32_t* roots, int 
   if (kind == BFS_KERNEL_BATCH && n_roots > kMaxWave) return fail(BFS_ERR_INVALID_ARG, "n_roots outside [1, 64]");
   const int count = bfs_shape_count(kind);
   // Single-source candidates: every shape under the CUDA-graph loop, then every shape under
-  // the persistent loop with as many CTAs as fit, then with 2 CTAs per SM (only the
-  // persistent ones when bottom-up levels are enabled).
-  const int n_cand = kind == BFS_KERNEL_SINGLE ? 3 * count : count;
-  constexpr int kFewCtas = 2;
+  // the persistent loop with as many CTAs as fit, then with 2 CTAs per SM, then with 1 (only
+  // the persistent ones when bottom-up levels are enabled). Fewer CTAs make the grid barrier
+  // cheaper, which pays on graphs of hundreds of small levels.
+  const int n_cand = kind == BFS_KERNEL_SINGLE ? 4 * count : count;
+  auto persist_ctas = [count](int c) { return c >= 3 * count ? 1 : c >= 2 * count ? 2 : 0; };
   const bool bu = G->bottom_up != 0;
   int best = -1;
   double best_ms = std::numeric_limits<double>::infinity();
@@ -83,7 +84,7 @@ GBFS_API bfs_status bfs_tune(bfs_graph_t G, int kind, const int32_t* roots, int 
         continue;
       }
       if ((r = bfs_graph_set_option(G, BFS_OPT_LOOP, loop)) != BFS_OK) return r;
-      if ((r = bfs_graph_set_option(G, BFS_OPT_PERSIST_CTAS, c >= 2 * count ? kFewCtas : 0)) != BFS_OK) return r;
+      if ((r = bfs_graph_set_option(G, BFS_OPT_PERSIST_CTAS, persist_ctas(c))) != BFS_OK) return r;
       if ((r = bfs_graph_set_shape(G, kind, s)) != BFS_OK) return r;
       if ((r = bfs_run(G, roots[0], levels, parents, stream, st.data())) != BFS_OK) return r;  // warm-up
       for (int i = 0; i < n_roots; ++i) {
@@ -107,7 +108,7 @@ GBFS_API bfs_status bfs_tune(bfs_graph_t G, int kind, const int32_t* roots, int 
   if (kind == BFS_KERNEL_SINGLE) {
     if ((r = bfs_graph_set_option(G, BFS_OPT_LOOP, best < count ? BFS_LOOP_GRAPH : BFS_LOOP_PERSISTENT)) != BFS_OK)
       return r;
-    if ((r = bfs_graph_set_option(G, BFS_OPT_PERSIST_CTAS, best >= 2 * count ? kFewCtas : 0)) != BFS_OK) return r;
+    if ((r = bfs_graph_set_option(G, BFS_OPT_PERSIST_CTAS, persist_ctas(best))) != BFS_OK) return r;
   }
   if ((r = bfs_graph_set_shape(G, kind, best % count)) != BFS_OK) return r;
   if (best_shape) *best_shape = best;

@@ -115,7 +115,7 @@ def test_shape_tables(capi):
             assert info["warp_tiles"] in (0, 1)
     assert capi.bfs_shape_count(7) == 0
     # tests/test_gpu_bfs.py runs every single-source shape: keep its list in step
-    assert capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE) == 9
+    assert capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE) == 10
     with pytest.raises(capi.BfsError):
         capi.bfs_shape_info(0, 99)
 

@@ -106,7 +106,7 @@ def test_grid3d_manhattan(torch_cuda, oracle_mod, graphs_mod):
         capi.bfs_graph_destroy(h)
 
 
-@pytest.mark.parametrize("shape", list(range(9)))
+@pytest.mark.parametrize("shape", list(range(10)))
 @pytest.mark.parametrize("force64", [False, True])
 def test_rmat16_all_shapes(torch_cuda, oracle_mod, graphs_mod, shape, force64):
     """R-MAT scale 16, edge factor 16 (the small configuration): 16 seeded roots, every

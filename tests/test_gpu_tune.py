@@ -29,12 +29,13 @@ def test_tune_single_and_batch_then_exact(torch_cuda, oracle_mod, graphs_mod):
         pr = torch.empty(g.n, dtype=torch.int32, device="cuda")
         best, ms = capi.bfs_tune(h, capi.BFS_KERNEL_SINGLE, roots[:3], lv, pr)
         count = capi.bfs_shape_count(capi.BFS_KERNEL_SINGLE)
-        assert len(ms) == 3 * count and all(x > 0 for x in ms)
+        assert len(ms) == 4 * count and all(x > 0 for x in ms)
         assert best == int(np.argmin(ms))
         assert capi.bfs_graph_get_shape(h, capi.BFS_KERNEL_SINGLE) == best % count
         assert capi.bfs_graph_get_option(h, capi.BFS_OPT_LOOP) == (capi.BFS_LOOP_GRAPH if best < count
                                                                   else capi.BFS_LOOP_PERSISTENT)
-        assert capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS) == (2 if best >= 2 * count else 0)
+        assert capi.bfs_graph_get_option(h, capi.BFS_OPT_PERSIST_CTAS) == (
+            1 if best >= 3 * count else 2 if best >= 2 * count else 0)
         bl = torch.empty((24, g.n), dtype=torch.int32, device="cuda")
         bp = torch.empty((24, g.n), dtype=torch.int32, device="cuda")
         bbest, bms = capi.bfs_tune(h, capi.BFS_KERNEL_BATCH, roots, bl, bp)
