@@ -38,6 +38,8 @@ def _check(oracle, capi, srv, g, q, host):
     assert code == 0, (oracle.TREE_CODES[code], bad)
     assert st.edges_traversed == oracle.component_edges(g.offsets, ref)
     assert st.depth == int(ref.max()) + 1
+    # latency (submission to completion) covers the service time (admission to completion)
+    assert st.expand_ms >= st.device_ms >= 0.0
 
 
 @pytest.mark.parametrize("host,lpr", [(False, 1), (False, 0), (True, 3)])
