@@ -849,11 +849,28 @@ def run_serve(args) -> int:
     torch.cuda.set_device(local_rank)
     names = ["rmat-s20-ef16", "rmat-s24-ef16", "grid3d-192", "uniform-n8M-deg8"]
     gs, hs = [], []
+    batch_shapes = {}
     for nm in names:
         t = time.perf_counter()
-        g = WORKLOADS[nm].make()
+        wl = WORKLOADS[nm]
+        g = wl.make()
         gs.append(g)
-        hs.append(create_graph(capi, g, use_relabel(WORKLOADS[nm].kind, args.relabel)))
+        relabel = use_relabel(wl.kind, args.relabel)
+        h = create_graph(capi, g, relabel)
+        hs.append(h)
+        if not args.no_autotune:
+            # the waves take the graph's batch shape when the graph is added to a server:
+            # tune it first (one 64-root wave per shape, cached per graph class and scale)
+            from paper_1408_1605_gb300 import autotune
+
+            roots = np.asarray(wl.pick_roots(g, 64), dtype=np.int32)
+            lv = torch.empty((roots.size, g.n), dtype=torch.int32, device="cuda")
+            pr = torch.empty((roots.size, g.n), dtype=torch.int32, device="cuda")
+            rec = autotune.apply_or_tune(h, capi.BFS_KERNEL_BATCH, wl.kind + ("-relabel" if relabel else ""), g.n,
+                                         roots, lv, pr)
+            batch_shapes[nm] = rec["shape"]
+            del lv, pr
+            torch.cuda.empty_cache()
         log(f"[serve] {nm}: n={g.n} nnz={g.nnz} ({time.perf_counter() - t:.1f}s)")
     n_buf = 96  # output buffers per graph, reused once their query completes
     pools = [[(torch.empty(g.n, dtype=torch.int32, device="cuda"), torch.empty(g.n, dtype=torch.int32, device="cuda"))
@@ -917,7 +934,7 @@ def run_serve(args) -> int:
                                      "levels_per_round": args.serve_levels_per_round or 8,
                                      "cohort_wait_us": args.serve_cohort_wait_us or "mean cohort duration",
                                      "memory_cap_bytes": 64 << 30,
-                                     "relabel": args.relabel},
+                                     "relabel": args.relabel, "batch_shapes": batch_shapes},
                           "rates": results}), flush=True)
     return 0
 
