@@ -89,6 +89,7 @@ struct BatchArgs {
   int ev_slots;                   // event slots per vertex (kEventSlots or kEventSlotsWave)
   int defer;                      // 1: events kept for the whole wave, outputs written once at its end
   int n_slots;                    // slots (roots) of the wave whose outputs the final pass writes
+  int allow_ordered;              // large frontiers may be rebuilt in vertex order (no bottom-up levels)
   // Waves with deferred outputs: a vertex whose claims outgrow its event slots gets a dense
   // row (parent and wave level per root bit, and the mask of bits set there) from a pool.
   int32_t* dense_idx;             // [n]: the vertex's row, -1 if none (NULL: no dense rows)
@@ -165,6 +166,7 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.ev_slots = b.ev_slots;
   a.defer = 0;
   a.n_slots = kMaxWave;
+  a.allow_ordered = 1;
   a.dense_idx = b.dense_idx;
   a.dense_par = b.dense_par;
   a.dense_lvl = b.dense_lvl;
@@ -212,6 +214,17 @@ __device__ __forceinline__ void dense_write(const BatchArgs<OffT>& a, int32_t ro
     a.dense_lvl[(size_t)row * kMaxWave + b] = L;
   }
   atomicOr(a.dense_mask + row, bits);
+}
+
+// Vertex-ordered frontiers: when the frontier being expanded holds at least n / kOrderedDiv
+// vertices, the expansion only marks the next frontier's masks (no appends) and
+// k_batch_order rebuilds the list from them in vertex order, so that the next expansion
+// reads its frontier's masks, rows and neighbours' masks in address order. Decided from the
+// current frontier's size, which every kernel of the level reads alike.
+constexpr long long kOrderedDiv = 16;
+template <typename OffT>
+__device__ __forceinline__ bool wave_ordered(const BatchArgs<OffT>& a, long long nf) {
+  return a.allow_ordered && !a.allow_bu && nf * kOrderedDiv >= a.n;
 }
 
 // True when a claim carries a single root bit: it is written out at once (that root's level
@@ -303,6 +316,10 @@ template <typename OffT>
 void launch_batch_count(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_final(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
+// After every expansion: rebuilds the next frontier in vertex order if the expansion was an
+// ordered one (wave_ordered), else returns at once.
+template <typename OffT>
+void launch_batch_order(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st);
 template <typename OffT>
 void launch_batch_stats(const OffT* off, const int32_t* new_id, int64_t n, const WaveSlots* slots, int n_slots,
                         long long* stats, int num_sms, cudaStream_t st);

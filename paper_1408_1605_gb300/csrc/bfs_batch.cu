@@ -245,6 +245,7 @@ static bfs_status build_batch_graph(bfs_graph_s* G) {
   {
     cudaError_t le = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, cs);
     if (a.allow_bu) launch_batch_count<OffT>(a, G->g.num_sms, cs);
+    launch_batch_order<OffT>(a, G->g.num_sms, cs);
     e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
     if (le != cudaSuccess) e = le;
@@ -323,6 +324,7 @@ static bfs_status run_batch(bfs_graph_s* G, const int32_t* roots, int n_roots, i
       if ((e = launch_batch_expand<OffT>(G->batch_shape, a, S->grid, st)) != cudaSuccess)
         return cuda_fail(e, "batch expand");
       if (a.allow_bu) launch_batch_count<OffT>(a, g.num_sms, st);
+      launch_batch_order<OffT>(a, g.num_sms, st);
       if ((e = cudaMemcpyAsync(S->ctl_host, S->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "batch level sync");

@@ -347,6 +347,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
   // Done marks (waves whose roots all start at level 0): the roots still searching are those
   // of frontier t; a vertex whose visited mask holds all of them can never be claimed again
   // (the set only shrinks), so its mask is not read. A missing mark only costs the read.
+  const bool ordered = wave_ordered(a, nf);  // no appends: the next frontier is rebuilt in vertex order
   uint32_t* done = DONE ? a.done : nullptr;
   const unsigned long long act = DONE ? *(volatile unsigned long long*)&ctl->alive[cur] : 0ull;
   for (int64_t tile = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles; tile += (int64_t)gridDim.x * wpb) {
@@ -458,7 +459,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int32_t v = vv[j];
-      first[j] = claimed[j] && fold[j] == 0ull;
+      first[j] = !ordered && claimed[j] && fold[j] == 0ull;  // ordered: k_batch_order lists it
       deg[j] = first[j] ? (int32_t)(a.off[v + 1] - a.off[v]) : 0;
       tot += __popc(__ballot_sync(full, first[j]));
       if (claimed[j]) {
@@ -515,6 +516,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
   const int64_t nf = a.pk.count(pc);
   const OffT r = (OffT)a.pk.edges(pc);
   const long long prev = *(volatile long long*)&ctl->prev_count;
+  const bool ordered = wave_ordered(a, nf);  // no appends: the next frontier is rebuilt in vertex order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < kMaxWave) {
     s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
@@ -647,7 +649,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int32_t v = vv[j];
-      first[j] = claimed[j] && fold[j] == 0ull;
+      first[j] = !ordered && claimed[j] && fold[j] == 0ull;  // ordered: k_batch_order lists it
       o0[j] = 0;
       o1[j] = 0;
       if (first[j]) {
@@ -711,8 +713,10 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
       ctl->done[cur] = 0;
       ctl->alive[cur] = 0;
       ctl->level = L + 1;
-      ctl->cont = nn > 0;
-      if (a.use_cond) cudaGraphSetConditional(a.cond, nn > 0 ? 1u : 0u);
+      // an ordered expansion appended nothing: the next frontier exists if some root claimed
+      const bool more = ordered ? *(volatile unsigned long long*)&ctl->alive[nxt] != 0ull : nn > 0;
+      ctl->cont = more;
+      if (a.use_cond) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
     }
   }
 }
@@ -963,6 +967,54 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
   }
 }
 
+// The next frontier of an ordered expansion (wave_ordered on the expanded frontier's size),
+// rebuilt from its masks F_{t+1} in vertex order: rounds of blockDim.x consecutive vertices
+// per CTA, a block scan of the marked vertices' counts and degrees, one 64-bit reservation
+// per round on the packed (count, edges) counter the appends use otherwise, then each marked
+// vertex writes its list entry, scan value, column base and tile descriptors. Entries are in
+// vertex order within a round; rounds land in any order.
+template <typename OffT>
+__global__ void __launch_bounds__(256) k_batch_order(BatchArgs<OffT> a) {
+  BatchCtl* ctl = a.ctl;
+  if (!wave_ordered(a, *(volatile long long*)&ctl->prev_count)) return;  // grid-uniform
+  const int t = *(volatile int*)&ctl->level - 2;  // the expansion that just closed
+  const int nxt = (t & 1) ^ 1, q3n = (t + 1) % 3;
+  const unsigned long long* Fn = a.fmask[q3n];
+  __shared__ OffT s_warp[33];
+  __shared__ unsigned long long s_resv;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < a.n; r0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = r0 + threadIdx.x;
+    const bool in = v < a.n && Fn[v] != 0ull;
+    OffT o0 = 0, d = 0;
+    if (in) {
+      o0 = a.off[v];
+      d = a.off[v + 1] - o0;
+    }
+    OffT tot_cnt, tot_deg;
+    const OffT ex_cnt = block_exclusive_scan((OffT)(in ? 1 : 0), s_warp, &tot_cnt);
+    const OffT ex_deg = block_exclusive_scan(d, s_warp, &tot_deg);
+    if (tot_cnt == 0) continue;  // block-uniform
+    if (threadIdx.x == 0) s_resv = atomicAdd(&ctl->counter[nxt], a.pk.make((long long)tot_cnt, (long long)tot_deg));
+    __syncthreads();
+    const unsigned long long resv = s_resv;
+    __syncthreads();
+    const int64_t slot = a.pk.count(resv) + (int64_t)ex_cnt;
+    const OffT run = (OffT)a.pk.edges(resv) + ex_deg;
+    const OffT b = o0 - run;
+    if (in) {
+      a.qv[q3n][slot] = (int32_t)v;
+      a.cum[nxt][slot] = run;
+      a.base[nxt][slot] = b;
+    }
+    write_descs_warp(a.chunk[nxt], in, run, d, (int32_t)slot, (int32_t)v, b);
+  }
+}
+
+template <typename OffT>
+void launch_batch_order(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
+  k_batch_order<OffT><<<num_sms * 8, 256, 0, st>>>(a);
+}
+
 template <typename OffT>
 void launch_batch_final(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
   k_batch_final<OffT><<<num_sms * 8, 256, 0, st>>>(a);
@@ -1145,6 +1197,7 @@ void launch_level_stats(const OffT* off, const int32_t* new_id, int64_t n, const
   template void launch_batch_emit<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                        \
   template void launch_batch_count<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
   template void launch_batch_final<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
+  template void launch_batch_order<OffT>(const BatchArgs<OffT>&, int, cudaStream_t);                       \
   template void launch_batch_seed<OffT>(const BatchArgs<OffT>&, const RootSeed*, int, int, bool, cudaStream_t); \
   template cudaError_t launch_batch_expand<OffT>(int, const BatchArgs<OffT>&, int, cudaStream_t);           \
   template int batch_expand_grid<OffT>(int, int);                                                           \

@@ -136,6 +136,7 @@ template <typename OffT>
 static void wave_launch_level(Wave* w) {
   BatchArgs<OffT> a = make_batch_args<OffT>(w->g, w->b);
   launch_batch_expand<OffT>(w->shape, a, w->grid, w->stream);
+  launch_batch_order<OffT>(a, w->g.num_sms, w->stream);  // before the emit, which reads the list
   launch_batch_emit<OffT>(a, w->g.num_sms, w->stream);
 }
 
