@@ -101,6 +101,10 @@ struct BatchArgs {
   // Waves whose roots all start at level 0 (bfs_run_batch): bit v set once V[v] holds every
   // root still searching, so no edge into v can claim again (NULL: not kept).
   uint32_t* done;
+  // [n rounded up to 16]: byte v is 1 once an ordered expansion put v into the next frontier
+  // (the claim whose OR found F_{t+1}[v] empty stores it); k_batch_order reads and clears it.
+  uint8_t* fmark;
+  int order_marks;                // ordered levels keep byte marks (graphs not relabelled by degree)
 };
 
 // Work buffers of multi-source searches on one graph.
@@ -129,6 +133,7 @@ struct BatchBufs {
   long long dense_cap = 0;
   bool dense_ident = false;
   uint32_t* done = nullptr;         // [n / 32] (waves with deferred outputs only)
+  uint8_t* fmark = nullptr;         // [n rounded up to 16], zero between ordered levels
 };
 
 struct RootSeed {
@@ -174,6 +179,8 @@ BatchArgs<OffT> make_batch_args(const GraphDev& g, const BatchBufs& b) {
   a.dense_cap = b.dense_cap;
   a.dense_ident = b.dense_ident ? 1 : 0;
   a.done = b.done;
+  a.fmark = b.fmark;
+  a.order_marks = g.old_id ? 0 : 1;
   return a;
 }
 

@@ -83,6 +83,7 @@ void free_batch_bufs(BatchBufs& b) {
   cudaFree(b.ovf);
   cudaFree(b.dense_idx);
   cudaFree(b.done);
+  cudaFree(b.fmark);
   cudaFree(b.dense_par);
   cudaFree(b.dense_lvl);
   cudaFree(b.dense_mask);
@@ -123,7 +124,7 @@ size_t batch_bufs_bytes(const GraphDev& g, int ev_slots, long long dense_rows) {
   const size_t ovf_cap = (size_t)overflow_cap(g, ev_slots);
   const size_t dense = (size_t)dense_rows_cap(g, ev_slots, dense_rows);
   return (size_t)g.n * (8 * 4 + 4 * 3 + 2 * 2 * osz + 4 + sizeof(ClaimEvent) * ev_slots + (dense ? 4 : 0)) +
-         (ev_slots == kEventSlotsWave ? (size_t)(g.n + 31) / 32 * 4 : 0) +
+         (ev_slots == kEventSlotsWave ? (size_t)(g.n + 31) / 32 * 4 : 0) + (size_t)(g.n + 15) / 16 * 16 +
          ovf_cap * sizeof(OvfEvent) + 2 * 16 * (size_t)(g.nnz / kChunk + 2) + dense * (8 * kMaxWave + 8) +
          64 * 1024;
 }
@@ -159,6 +160,9 @@ cudaError_t alloc_batch_bufs(const GraphDev& g, BatchBufs& b, int ev_slots, long
     if (e == cudaSuccess) e = dalloc(&b.dense_mask, (size_t)b.dense_cap);
   }
   if (ev_slots == kEventSlotsWave && e == cudaSuccess) e = dalloc(&b.done, (size_t)(g.n + 31) / 32);
+  const size_t fmark_bytes = (size_t)(g.n + 15) / 16 * 16;  // whole 16-byte words: the padding stays 0
+  if (e == cudaSuccess) e = dalloc(&b.fmark, fmark_bytes);
+  if (e == cudaSuccess) e = cudaMemset(b.fmark, 0, fmark_bytes);
   if (e == cudaSuccess) e = cudaMemset(b.evc, 0, sizeof(int32_t) * (size_t)g.n);
   if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(BatchCtl));
   if (e != cudaSuccess) {

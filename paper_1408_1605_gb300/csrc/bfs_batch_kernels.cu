@@ -47,6 +47,7 @@ __global__ void k_batch_clear(BatchArgs<OffT> a) {
     a.fmask[1][v] = 0ull;
     a.fmask[2][v] = 0ull;
     a.evc[v] = 0;
+    a.fmark[v] = 0;
     if (a.dense_idx) a.dense_idx[v] = -1;
   }
   if (a.dense_idx || a.dense_ident)
@@ -348,6 +349,7 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
   // of frontier t; a vertex whose visited mask holds all of them can never be claimed again
   // (the set only shrinks), so its mask is not read. A missing mark only costs the read.
   const bool ordered = wave_ordered(a, nf);  // no appends: the next frontier is rebuilt in vertex order
+  const bool marks = ordered && a.order_marks;  // ... from byte marks
   uint32_t* done = DONE ? a.done : nullptr;
   const unsigned long long act = DONE ? *(volatile unsigned long long*)&ctl->alive[cur] : 0ull;
   for (int64_t tile = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles; tile += (int64_t)gridDim.x * wpb) {
@@ -459,7 +461,9 @@ __device__ void batch_td_warp(const BatchArgs<OffT>& a, int L, int cur, int nxt,
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int32_t v = vv[j];
-      first[j] = !ordered && claimed[j] && fold[j] == 0ull;  // ordered: k_batch_order lists it
+      const bool fresh = claimed[j] && fold[j] == 0ull;  // v enters the next frontier with this claim
+      if (fresh && marks) a.fmark[v] = 1;
+      first[j] = fresh && !ordered;  // ordered: k_batch_order lists it
       deg[j] = first[j] ? (int32_t)(a.off[v + 1] - a.off[v]) : 0;
       tot += __popc(__ballot_sync(full, first[j]));
       if (claimed[j]) {
@@ -517,6 +521,7 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
   const OffT r = (OffT)a.pk.edges(pc);
   const long long prev = *(volatile long long*)&ctl->prev_count;
   const bool ordered = wave_ordered(a, nf);  // no appends: the next frontier is rebuilt in vertex order
+  const bool marks = ordered && a.order_marks;  // ... from byte marks
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < kMaxWave) {
     s_lvl[threadIdx.x] = a.slots->lvl[threadIdx.x];
@@ -649,7 +654,9 @@ __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) k_expand_batch(BatchArgs<O
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int32_t v = vv[j];
-      first[j] = !ordered && claimed[j] && fold[j] == 0ull;  // ordered: k_batch_order lists it
+      const bool fresh = claimed[j] && fold[j] == 0ull;  // v enters the next frontier with this claim
+      if (fresh && marks) a.fmark[v] = 1;
+      first[j] = fresh && !ordered;  // ordered: k_batch_order lists it
       o0[j] = 0;
       o1[j] = 0;
       if (first[j]) {
@@ -967,21 +974,21 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
   }
 }
 
-// The next frontier of an ordered expansion (wave_ordered on the expanded frontier's size),
-// rebuilt from its masks F_{t+1} in vertex order: rounds of blockDim.x consecutive vertices
-// per CTA, a block scan of the marked vertices' counts and degrees, one 64-bit reservation
-// per round on the packed (count, edges) counter the appends use otherwise, then each marked
-// vertex writes its list entry, scan value, column base and tile descriptors. Entries are in
-// vertex order within a round; rounds land in any order.
+// Bit j set when byte j of x is nonzero; frontier marks are 0 or 1.
+__device__ __forceinline__ unsigned mark_bits(unsigned x) {
+  return (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
+}
+
+// k_batch_order on a degree-relabelled graph: one vertex per thread, read from the 64-bit
+// masks F_{t+1}, rounds of blockDim.x consecutive vertices per CTA (the hubs, at the lowest
+// ids, spread over many CTAs), a block scan of the marked vertices' counts and degrees, one
+// reservation per round, then each marked vertex writes its list entry, scan value, column
+// base and tile descriptors.
 template <typename OffT>
-__global__ void __launch_bounds__(256) k_batch_order(BatchArgs<OffT> a) {
-  BatchCtl* ctl = a.ctl;
-  if (!wave_ordered(a, *(volatile long long*)&ctl->prev_count)) return;  // grid-uniform
-  const int t = *(volatile int*)&ctl->level - 2;  // the expansion that just closed
-  const int nxt = (t & 1) ^ 1, q3n = (t + 1) % 3;
+__device__ __forceinline__ void order_from_masks(const BatchArgs<OffT>& a, BatchCtl* ctl, int nxt, int q3n,
+                                                 OffT* s_warp, unsigned long long* s_resv_p) {
+  unsigned long long& s_resv = *s_resv_p;
   const unsigned long long* Fn = a.fmask[q3n];
-  __shared__ OffT s_warp[33];
-  __shared__ unsigned long long s_resv;
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < a.n; r0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = r0 + threadIdx.x;
     const bool in = v < a.n && Fn[v] != 0ull;
@@ -1010,9 +1017,99 @@ __global__ void __launch_bounds__(256) k_batch_order(BatchArgs<OffT> a) {
   }
 }
 
+// k_batch_order on any other graph: from the byte marks the expansion left (1 / 8 of the
+// bytes of the masks). Each thread takes 16 consecutive vertices with one 16-byte load of
+// their marks and clears the marks it found; a block scan of the threads' marked counts and
+// degree sums, one reservation per round of 16 x blockDim.x vertices, then each thread writes
+// its marked vertices' list entries, scan values, column bases and tile descriptors in vertex
+// order, the warp's lanes stepping through their marked vertices together.
+template <typename OffT>
+__device__ __forceinline__ void order_from_marks(const BatchArgs<OffT>& a, BatchCtl* ctl, int nxt, int q3n,
+                                                 OffT* s_warp, unsigned long long* s_resv_p) {
+  constexpr int V = 16;  // vertices per thread: one uint4 of marks
+  constexpr unsigned kFull = 0xffffffffu;
+  unsigned long long& s_resv = *s_resv_p;
+  uint4* marks = reinterpret_cast<uint4*>(a.fmark);
+  const int64_t groups = (a.n + V - 1) / V;  // the marks array holds whole 16-byte groups
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < groups; g0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = g0 + threadIdx.x;
+    const int64_t v0 = gi * V;
+    unsigned sel = 0;  // bit i: vertex v0 + i is in the next frontier
+    if (gi < groups) {
+      const uint4 m = marks[gi];
+      if (m.x | m.y | m.z | m.w) {
+        sel = mark_bits(m.x) | (mark_bits(m.y) << 4) | (mark_bits(m.z) << 8) | (mark_bits(m.w) << 12);
+        marks[gi] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    OffT deg = 0;
+    for (unsigned s = sel; s; s &= s - 1) {
+      const int64_t v = v0 + __ffs(s) - 1;
+      deg += a.off[v + 1] - a.off[v];
+    }
+    OffT tot_cnt, tot_deg;
+    const OffT ex_cnt = block_exclusive_scan((OffT)__popc(sel), s_warp, &tot_cnt);
+    const OffT ex_deg = block_exclusive_scan(deg, s_warp, &tot_deg);
+    if (tot_cnt == 0) continue;  // block-uniform
+    if (threadIdx.x == 0) s_resv = atomicAdd(&ctl->counter[nxt], a.pk.make((long long)tot_cnt, (long long)tot_deg));
+    __syncthreads();
+    const unsigned long long resv = s_resv;
+    __syncthreads();
+    int64_t slot = a.pk.count(resv) + (int64_t)ex_cnt;
+    OffT run = (OffT)a.pk.edges(resv) + ex_deg;
+    unsigned rem = sel;
+    while (__any_sync(kFull, rem != 0u)) {  // warp-uniform: the descriptor writes are warp-collective
+      const bool in = rem != 0u;
+      int64_t v = 0;
+      OffT o0 = 0, d = 0;
+      if (in) {
+        v = v0 + __ffs(rem) - 1;
+        rem &= rem - 1u;
+        o0 = a.off[v];
+        d = a.off[v + 1] - o0;
+      }
+      const OffT b = o0 - run;
+      if (in) {
+        a.qv[q3n][slot] = (int32_t)v;
+        a.cum[nxt][slot] = run;
+        a.base[nxt][slot] = b;
+      }
+      write_descs_warp(a.chunk[nxt], in, run, d, (int32_t)slot, (int32_t)v, b);
+      if (in) {
+        ++slot;
+        run += d;
+      }
+    }
+  }
+}
+
+// The next frontier of an ordered expansion (wave_ordered on the expanded frontier's size),
+// rebuilt in vertex order: entries are in vertex order within a round; rounds land in any
+// order. Where the rounds are cut depends on the graph (MARKS = BatchArgs::order_marks): a
+// degree-relabelled graph puts its hubs at the lowest ids, so rounds of 16 x blockDim.x
+// vertices there would leave the hubs' tile descriptors (22 % of the edges of R-MAT s22 in
+// the first 4096 vertices) to one CTA. Two kernels, so that each keeps its own register count
+// (the mask variant 32, for 8 resident CTAs per SM).
+template <typename OffT, bool MARKS>
+__global__ void __launch_bounds__(256) k_batch_order(BatchArgs<OffT> a) {
+  BatchCtl* ctl = a.ctl;
+  if (!wave_ordered(a, *(volatile long long*)&ctl->prev_count)) return;  // grid-uniform
+  const int t = *(volatile int*)&ctl->level - 2;  // the expansion that just closed
+  const int nxt = (t & 1) ^ 1, q3n = (t + 1) % 3;
+  __shared__ OffT s_warp[33];
+  __shared__ unsigned long long s_resv;
+  if constexpr (MARKS)
+    order_from_marks(a, ctl, nxt, q3n, s_warp, &s_resv);
+  else
+    order_from_masks(a, ctl, nxt, q3n, s_warp, &s_resv);
+}
+
 template <typename OffT>
 void launch_batch_order(const BatchArgs<OffT>& a, int num_sms, cudaStream_t st) {
-  k_batch_order<OffT><<<num_sms * 8, 256, 0, st>>>(a);
+  if (a.order_marks)
+    k_batch_order<OffT, true><<<num_sms * 8, 256, 0, st>>>(a);
+  else
+    k_batch_order<OffT, false><<<num_sms * 8, 256, 0, st>>>(a);
 }
 
 template <typename OffT>
