@@ -16,7 +16,7 @@
  *    holding neighbour ids in [0, n_vertices). Rows need not be sorted. Self-loops and
  *    repeated entries are harmless. A non-symmetric CSR is searched along its stored
  *    (out-)edges.
- *  - Outputs (Sec. 3.1; Algorithm 2 lines 1-10): level[v] = hop distance from the root,
+ *  - Outputs (Sec. 3.1; the initialisation of Algorithm 2): level[v] = hop distance from the root,
  *    pred[v] = a neighbour of v one level closer to the root, level[root] = 0 and
  *    pred[root] = root; vertices not reached get level = pred = -1. When several parents
  *    are valid, which one is written depends on which atomic wins (Sec. 3.4).
@@ -87,7 +87,7 @@ typedef struct bfs_stats {
  *   BFS_RELABEL_DEGREE: the library stores the graph with its vertices renumbered by
  *     non-increasing degree (ties in input order) and every row sorted, so that in skewed
  *     graphs the visited bits of the few vertices that end most edges share a small part of
- *     the bitmap (the per-edge pre-check of Algorithm 3 line 6 then hits the L1 cache).
+ *     the bitmap (Algorithm 3's per-edge non-atomic pre-check then hits the L1 cache).
  *     Done once here, on the device (two extra int32[n] maps; peak extra memory about
  *     2 x n_entries x 4 bytes during the call). It is invisible to callers: roots, levels
  *     and parents stay in the caller's numbering, and results are the same BFS (levels
@@ -217,8 +217,8 @@ GBFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *levels, int32_
 GBFS_API bfs_status bfs_run_batch(bfs_graph_t g, const int32_t *roots, int n_roots, int32_t *levels,
                                   int32_t *parents, void *stream, bfs_stats *per_root_stats);
 
-/* One top-down level on caller-held state: the frontier expansion routine of Algorithm 2
- * line 14 (Algorithm 3) with R = C = 1, including the degree gather and exclusive scan
+/* One top-down level on caller-held state: the frontier expansion step of Algorithm 2
+ * (Algorithm 3) with R = C = 1, including the degree gather and exclusive scan
  * (Sec. 3.4). All pointers are device memory:
  *   frontier int32[n_frontier]: the current frontier (any order, repeats and
  *     zero-degree vertices allowed);

@@ -8,9 +8,9 @@ code: only the seeded input generators in ``paper_1408_1605_gb300.graphs`` serve
 
 Definitions followed (see ``bfs_oracle.c`` for the per-function citations):
   * level[v]: hop distance from the root, -1 if unreachable; pred[root] = root (Sec. 2.2,
-    Algorithm 1; Sec. 3.2, Algorithm 2 lines 1-10).
+    Algorithm 1; Sec. 3.2, the initialisation of Algorithm 2).
   * m_c: undirected edges inside the traversed component, the TEPS numerator (Sec. 4).
-  * one top-down level (Algorithm 2 line 14 with R = C = 1).
+  * one top-down level (the expansion step of Algorithm 2 with R = C = 1).
 
 Parity status: levels and m_c pinned (closed forms, brute force); parents checked by
 invariants only, because ties between parents are decided by atomics (Sec. 3.4).

@@ -140,7 +140,7 @@ int oracle_check_edges(int64_t n, const int64_t *offsets, const int32_t *cols,
     return 0;
 }
 
-/* One top-down level (the frontier expansion of Algorithm 2, line 14, with the R = C = 1
+/* One top-down level (the expansion step of Algorithm 2, with the R = C = 1
  * identities: every destination is local, so dst_verts has one block). For each u in
  * front[0..n_front) in order and each neighbour v of u: if v's visited bit is clear, set
  * it, pred[v] = u, level[v] = lvl and append v to next. bitmap: uint32[ceil(n/32)], bit

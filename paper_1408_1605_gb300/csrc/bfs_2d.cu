@@ -117,7 +117,7 @@ __global__ void k_2d_init(Part P) {
 
 __global__ void k_2d_seed(Part P, int32_t root) {
   const Geo& g = P.geo;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // Algorithm 2 lines 5-10: the owner of the root
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // Algorithm 2's root placement: the owner of the root
     const int i = g.owner_i(root), j = g.owner_j(root);
     const int64_t p = (int64_t)i * g.C + j, row = g.local_row(root);
     P.level[p * g.NR + row] = 0;
@@ -128,7 +128,7 @@ __global__ void k_2d_seed(Part P, int32_t root) {
   }
 }
 
-// expand_comm (Algorithm 2 line 13): every processor of grid column j receives the
+// expand_comm (Algorithm 2's expand_comm step): every processor of grid column j receives the
 // frontiers of all of them, concatenated in processor-row order.
 __global__ void k_2d_expand_comm(Part P) {
   const Geo& g = P.geo;
@@ -174,10 +174,11 @@ __global__ void k_2d_totals(Part P) {
 }
 
 // expand_frontier (Algorithm 3): thread -> edge of the combined edge space; binary searches
-// give the processor (pcum) and the frontier entry (its scan, Algorithm 3 line 2). A newly
-// visited row v goes to the dst_verts block of its owner's processor column tgt = v / B
-// (lines 9-14): as a row id for another column, as the owner's local column for this one,
-// whose level is set here (line 15); pred[v] = u either way (line 17).
+// give the processor (pcum) and the frontier entry (its scan: the binary search of
+// Algorithm 3). A newly visited row v goes to the dst_verts block of its owner's processor
+// column tgt = v / B (Algorithm 3's frontier append): as a row id for another column, as the
+// owner's local column for this one, whose level is set here; pred[v] = u either way
+// (Algorithm 3's output writes).
 __global__ void k_2d_expand(Part P, int32_t lvl) {
   const Geo& g = P.geo;
   const int64_t RC = (int64_t)g.R * g.C;
@@ -219,7 +220,7 @@ __global__ void k_2d_expand(Part P, int32_t lvl) {
   }
 }
 
-// Lines 15-17 and fold_comm: the local block becomes the processor's frontier; every other
+// Algorithm 3's output writes and fold_comm: the local block becomes the processor's frontier; every other
 // block goes to the processor of the same grid row that owns it (receiver column tgt),
 // recorded per sender column.
 __global__ void k_2d_fold(Part P) {

@@ -3,8 +3,8 @@
 // list of vertices with F_t[v] != 0; each of their rows is read once per level and serves
 // every root that has the vertex in its frontier. Per edge (u, v):
 //     new = F_t[u] & ~V[v];  old = atomicOr(&V[v], new);  claimed = new & ~old
-// (the visited-bitmap claim of Algorithm 3 lines 5-8, one bit per root); for every claimed
-// bit b the level and parent of (b, v) are written (lines 15, 17), and v joins frontier
+// (Algorithm 3's visited test and claim, one bit per root); for every claimed bit b the
+// level and parent of (b, v) are written (Algorithm 3's output writes), and v joins frontier
 // t + 1 when atomicOr(&F_{t+1}[v], claimed) returns 0 (first touch), through the same
 // buffered append with the fused degree scan as the single-source kernel. Thread-to-edge
 // mapping is the single-source one (Sec. 3.4 and 3.4.1). The paper has no batched form;
@@ -317,7 +317,7 @@ __device__ void batch_bu_level(const BatchArgs<OffT>& a, const unsigned long lon
 // The top-down step of a wave with warp-sized tiles (the batched form of the single-source
 // warp tiles): warp w expands tiles w, w + W, ... of 32 E edges on its own, so no CTA-wide
 // barrier is needed inside a level. Edge e's frontier entry k = max{k : cum[k] <= e}
-// (Algorithm 3 line 2): a tile inside one row takes it from its tile descriptor; a tile
+// (the binary search of Algorithm 3): a tile inside one row takes it from its tile descriptor; a tile
 // over at most 32 entries holds them one per lane (row start in the tile, column base,
 // caller id, frontier mask) and searches them with shuffles; a tile over more entries
 // searches the scan. Per edge (u, v): new = F_t[u] & ~V[v], claimed = new & ~atomicOr(V[v],

@@ -1,7 +1,7 @@
 // C ABI of the gbfs library: graph upload and checks, single-source search, one-level
 // expansion. The level loop of a search stays on the device: one CUDA graph per graph
 // handle holds a conditional WHILE node whose body is the expansion kernel; the kernel's
-// last CTA sets the condition to "next frontier non-empty" (Algorithm 2 lines 19-21,
+// last CTA sets the condition to "next frontier non-empty" (the termination test of Algorithm 2,
 // without the per-level host round trip of the original design, Sec. 3.4).
 #include <cuda_runtime.h>
 

@@ -4,7 +4,7 @@
 //
 // Level structure (Algorithm 2 with R = C = 1). The frontier of a level is held as
 // (v[k], cum[k], base[k]) plus a chunk index of tile descriptors: descriptor c holds
-// k = max{k : cum[k] <= c * kChunk}, the binary-search answer (Algorithm 3 line 2) for
+// k = max{k : cum[k] <= c * kChunk}, the answer of Algorithm 3's binary search for
 // every kChunk-th edge, with that entry's parent id and the column entry of edge
 // c * kChunk; it is written when the frontier is built. One expansion processes the
 // level's edge space [0, r) in tiles, of BLOCK * E edges per CTA (CTA tiles) or of 32 * E
@@ -16,12 +16,12 @@
 //      (Sec. 3.4.1: advance k while e >= cum[k + 1]);
 //   3. lane l takes edges l, l + 32, ... of its warp's 32 * E (coalesced column reads), and
 //      all E column loads are issued before any is used (the interleaving of Sec. 3.4.1);
-//   4. bitmap pre-check, then atomicOr claim (Algorithm 3 lines 5-8); the winner writes
-//      level and parent (lines 15, 17) and reads the claimed vertex's degree;
+//   4. bitmap pre-check, then atomicOr claim (Algorithm 3's visited test and claim); the winner writes
+//      level and parent (Algorithm 3's output writes) and reads the claimed vertex's degree;
 //   5. claimed vertices are appended to a warp (or CTA) buffer with one shared atomic or
 //      ballot per warp; the buffer is flushed with ONE global 64-bit atomicAdd that reserves
 //      both the queue slots and the edge range (the exclusive scan of the next frontier's
-//      degrees, Sec. 3.4, fused into the append of lines 9-14).
+//      degrees, Sec. 3.4, fused into Algorithm 3's frontier append).
 // The last CTA to finish closes the level (no spin-waits in the per-level kernels; the
 // persistent kernel's grid barrier waits are bounded).
 #include <cuda_runtime.h>
@@ -504,7 +504,7 @@ struct WarpTileSmem {
 
 // The top-down step with warp-sized tiles: warp w expands tiles w, w + W, ... of 32 E
 // edges on its own, so no CTA-wide barrier is needed inside a level. The mapping of edge e
-// to the frontier entry k = max{k : cum[k] <= e} (Algorithm 3 line 2): a tile inside one row
+// to the frontier entry k = max{k : cum[k] <= e} (the binary search of Algorithm 3): a tile inside one row
 // takes it from its descriptor; a tile over at most 32 entries holds them one per lane and
 // finds k with a five-step binary search over the lanes (shuffles, no shared memory); a tile
 // over more entries searches the global scan. The rest (column reads, pre-check, atomicOr

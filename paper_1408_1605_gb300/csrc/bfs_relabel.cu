@@ -6,7 +6,7 @@
 // is rebuilt in the new numbering and sorted. In a skewed graph (R-MAT) a few percent of
 // the vertices are the endpoints of most edges; after relabelling their visited bits share
 // a few hundred KB of the bitmap that stay in each SM's L1 cache, so the per-edge bitmap
-// pre-check of Algorithm 3 line 6 mostly hits L1 instead of going to L2. Searches keep
+// non-atomic pre-check of Algorithm 3 mostly hits L1 instead of going to L2. Searches keep
 // taking and returning the caller's vertex ids: the kernels map the root through new_id
 // and write levels and parents at old_id[v].
 #include <cuda_runtime.h>

@@ -13,7 +13,7 @@ enum : unsigned { kErrColumnRange = 1u, kErrFrontierRange = 2u, kErrCounterOverf
 
 // The next frontier's size and edge total are reserved together by one 64-bit atomicAdd
 // on a packed word (count << shift) | edges, so the slot order and the exclusive degree
-// scan agree (the scan of Sec. 3.4, fused into the append of Algorithm 3 lines 9-14).
+// scan agree (the scan of Sec. 3.4, fused into Algorithm 3's frontier append).
 struct Packed {
   int shift;                 // bits for the edge total
   unsigned long long mask;   // (1 << shift) - 1
@@ -37,8 +37,8 @@ struct FrontierBuf {
 };
 
 // Tile descriptor of the chunk index: for every kChunk-th edge c * kChunk of a level's
-// edge space, k = max{k : cum[k] <= c * kChunk} (the binary-search answer of Algorithm 3
-// line 2), plus what a tile that lies inside row k alone needs: the parent to write (the
+// edge space, k = max{k : cum[k] <= c * kChunk} (the answer of Algorithm 3's binary
+// search), plus what a tile that lies inside row k alone needs: the parent to write (the
 // caller id u of entry k) and col = base[k] + c * kChunk, the column entry of that edge.
 // Written by whoever appends entry k to the frontier.
 template <typename OffT>
@@ -109,7 +109,7 @@ __device__ __forceinline__ int32_t ld_nc(const int32_t* p) {
   return v;
 }
 
-// Visited-bitmap pre-check load (Algorithm 3 line 6). Mode 0: through L1, kept there with
+// Visited-bitmap pre-check load (Algorithm 3's non-atomic pre-check). Mode 0: through L1, kept there with
 // priority (a stale copy is harmless: the atomicOr decides). Mode 1: L2 only
 // (ld.global.cg), so words filled during the level are seen and fewer futile atomics are
 // issued.
@@ -130,8 +130,8 @@ __device__ __forceinline__ T warp_inclusive_scan(T x) {
   return x;
 }
 
-// Largest k in [lo, hi) with a[k] <= x, given a[lo] <= x (binsearch_maxle of Algorithm 3
-// line 2). a is non-decreasing.
+// Largest k in [lo, hi) with a[k] <= x, given a[lo] <= x (binsearch_maxle, the binary search of
+// Algorithm 3). a is non-decreasing.
 template <typename T, typename I>
 __device__ __forceinline__ I binsearch_maxle(const T* a, I lo, I hi, T x) {
   while (hi - lo > 1) {

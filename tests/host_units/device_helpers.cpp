@@ -1,5 +1,5 @@
 // CPU unit tests of the scalar device helpers of the CUDA library, compiled as host code:
-//  * binsearch_maxle (the thread -> edge map of Algorithm 3 line 2) against
+//  * binsearch_maxle (the thread -> edge binary search of Algorithm 3) against
 //    std::upper_bound - 1 on random and adversarial non-decreasing sequences (runs of equal
 //    values = zero-degree frontier entries), int32 and int64, whole and partial ranges,
 //    and the monotonicity of the map in the searched value (Sec. 3.4.1);

@@ -1,5 +1,5 @@
 """Device helpers of the CUDA library compiled as plain host C++ (CPU only):
-  * the scalar ones (the thread -> edge binary search of Algorithm 3 line 2, the chunk-index
+  * the scalar ones (the thread -> edge binary search of Algorithm 3, the chunk-index
     and tile-descriptor writers, the packed append counter) against the C++ standard
     library on random and adversarial degree sequences (tests/host_units/device_helpers.cpp);
   * the warp- and block-collective ones (warp and block scans, the warp-cooperative
