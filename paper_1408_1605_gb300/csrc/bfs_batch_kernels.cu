@@ -974,11 +974,6 @@ __global__ void __launch_bounds__(256) k_batch_final(BatchArgs<OffT> a) {
   }
 }
 
-// Bit j set when byte j of x is nonzero; frontier marks are 0 or 1.
-__device__ __forceinline__ unsigned mark_bits(unsigned x) {
-  return (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
-}
-
 // k_batch_order on a degree-relabelled graph: one vertex per thread, read from the 64-bit
 // masks F_{t+1}, rounds of blockDim.x consecutive vertices per CTA (the hubs, at the lowest
 // ids, spread over many CTAs), a block scan of the marked vertices' counts and degrees, one

@@ -73,6 +73,12 @@ __device__ __forceinline__ void write_descs_warp(TileDesc<OffT>* desc, bool vali
   }
 }
 
+// Frontier marks of ordered wave levels, one byte per vertex holding 0 or 1: bit j of the
+// result is set when byte j of the 32-bit word x is 1 (four vertices' marks per word).
+__host__ __device__ __forceinline__ unsigned mark_bits(unsigned x) {
+  return (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
+}
+
 // Exclusive scan of one value per thread across the block; *total receives the sum.
 // s_warp needs 33 entries. Every thread of the block must call it.
 template <typename OffT>

@@ -7,7 +7,8 @@
 //    range [cum, cum + deg) gets that entry (and its parent and column entry), nothing
 //    else is touched; over a whole frontier the chunk index equals the binary-search answer
 //    at every boundary;
-//  * Packed: the (count, edges) word of the fused append adds component-wise.
+//  * Packed: the (count, edges) word of the fused append adds component-wise;
+//  * mark_bits: every pattern of four 0/1 byte marks maps to its 4-bit vertex mask.
 // Prints "ok" and returns 0, or reports the first failure and returns 1.
 #include <algorithm>
 #include <cstdint>
@@ -127,6 +128,15 @@ static void check_packed() {
   }
 }
 
+static void check_mark_bits() {
+  for (unsigned m = 0; m < 16; ++m) {
+    unsigned x = 0;  // byte j = 1 for each bit j of m
+    for (int j = 0; j < 4; ++j)
+      if ((m >> j) & 1u) x |= 1u << (8 * j);
+    CHECK(gbfs::mark_bits(x) == m, "mark_bits(0x%08x) = %u, want %u", x, gbfs::mark_bits(x), m);
+  }
+}
+
 int main() {
   for (int t = 0; t < 300; ++t) {
     check_binsearch<int32_t>(1 + below(300), 1 + below(5000));
@@ -138,6 +148,7 @@ int main() {
     check_chunks<int64_t>(1 + below(400), 1 + below(1ll << 16), (int64_t)below(1ll << 33));
   }
   check_packed();
+  check_mark_bits();
   if (failures) {
     std::printf("%d failures\n", failures);
     return 1;
