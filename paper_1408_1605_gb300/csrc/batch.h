@@ -224,10 +224,11 @@ __device__ __forceinline__ void dense_write(const BatchArgs<OffT>& a, int32_t ro
 }
 
 // Vertex-ordered frontiers: when the frontier being expanded holds at least n / kOrderedDiv
-// vertices, the expansion only marks the next frontier's masks (no appends) and
-// k_batch_order rebuilds the list from them in vertex order, so that the next expansion
-// reads its frontier's masks, rows and neighbours' masks in address order. Decided from the
-// current frontier's size, which every kernel of the level reads alike.
+// vertices, the expansion only marks the next frontier's masks (no appends; on graphs not
+// relabelled by degree also a byte mark per vertex, BatchArgs::fmark) and k_batch_order
+// rebuilds the list from them in vertex order, so that the next expansion reads its
+// frontier's masks, rows and neighbours' masks in address order. Decided from the current
+// frontier's size, which every kernel of the level reads alike.
 constexpr long long kOrderedDiv = 16;
 template <typename OffT>
 __device__ __forceinline__ bool wave_ordered(const BatchArgs<OffT>& a, long long nf) {
