@@ -56,7 +56,8 @@ def build_bfs(verbose: bool = False, force: bool = False, extra: list[str] | Non
     """nvcc each translation unit in parallel to an object, then link one shared library
     (static cudart, so the library loads on a machine without a GPU)."""
     srcs = _bfs_sources()
-    deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    deps = (srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+            glob.glob(os.path.join(INCLUDE, "*.h")))
     if not (force or _stale(LIB_BFS, deps)):
         return LIB_BFS
     objdir = os.path.join(HERE, "_build")

@@ -1,7 +1,8 @@
 // A small SIMT emulator for CPU unit tests of the library's warp- and block-collective
 // helpers: every emulated GPU thread is an OS thread; the warp intrinsics the helpers use
-// (__ballot_sync, __shfl_sync, __shfl_up_sync, full-warp masks only) exchange values through
-// a per-warp slot array between two barriers, and __syncthreads is a block barrier. The
+// (__ballot_sync, __any_sync, __shfl_sync, __shfl_up_sync, full-warp masks only) exchange
+// values through a per-warp slot array between two barriers, __syncthreads is a block
+// barrier, and the device atomics the headers use act on host memory. The
 // intrinsic semantics follow the CUDA programming guide's definitions. Included ahead of the
 // library headers (g++ -include), in place of their CUDA device environment.
 #pragma once
@@ -123,7 +124,23 @@ T __shfl_up_sync(unsigned mask, T v, unsigned d) {
   return lane >= d ? simt::from_bits<T>(all[lane - d]) : v;
 }
 
+inline int __any_sync(unsigned mask, int pred) { return __ballot_sync(mask, pred) != 0u; }
+
 inline int __ffs(unsigned x) { return __builtin_ffs((int)x); }
+inline int __ffsll(long long x) { return __builtin_ffsll(x); }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
 inline void __syncthreads() { simt::t_block->bar.wait(); }
+
+// Device atomics on host memory (sequentially consistent; each returns the old value).
+inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
+  return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST);
+}
+inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned long long atomicOr(unsigned long long* p, unsigned long long v) {
+  return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST);
+}
+inline int atomicCAS(int* p, int cmp, int val) {
+  __atomic_compare_exchange_n(p, &cmp, val, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST);
+  return cmp;
+}
 unsigned __ldcg(const unsigned*);  // declared for the headers; not used by these tests

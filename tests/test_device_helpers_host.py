@@ -4,7 +4,11 @@
     library on random and adversarial degree sequences (tests/host_units/device_helpers.cpp);
   * the warp- and block-collective ones (warp and block scans, the warp-cooperative
     descriptor writers for hub rows) on a small SIMT emulator, one OS thread per GPU thread,
-    against the standard library and the scalar writers (tests/host_units/warp_helpers.cpp)."""
+    against the standard library and the scalar writers (tests/host_units/warp_helpers.cpp);
+  * the two block-level passes that rebuild an ordered wave level's frontier in vertex order
+    (over the 64-bit root masks, over the byte marks) on the same emulator, against the
+    marked set, the degree scan and the binary search of Algorithm 3 written out in the
+    test (tests/host_units/batch_order.cpp)."""
 import os
 import shutil
 import subprocess
@@ -15,7 +19,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
 
 
-@pytest.mark.parametrize("unit,prelude", [("device_helpers", "cuda_shim.h"), ("warp_helpers", "simt_emu.h")])
+@pytest.mark.parametrize("unit,prelude", [("device_helpers", "cuda_shim.h"), ("warp_helpers", "simt_emu.h"),
+                                          ("batch_order", "simt_emu.h")])
 def test_device_helpers_on_host(tmp_path, unit, prelude):
     cxx = shutil.which("g++")
     if not cxx or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
