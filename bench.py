@@ -885,6 +885,10 @@ def run_serve(args) -> int:
         in_use = [[None] * n_buf for _ in gs]
         nxt = [0] * len(gs)
         tickets = []
+        sampler = ClockSampler(gpu_smi_id())  # SM clocks and throttle reasons while this rate runs
+        sampler.start()
+        time.sleep(0.3)
+        w0 = time.time()
         t0 = time.perf_counter()
         for i in range(nq):
             target = t0 + arrivals[i]
@@ -902,6 +906,9 @@ def run_serve(args) -> int:
         for tk in tickets:
             capi.bfs_serve_wait(srv, tk, 600000)
         offered = time.perf_counter() - t0
+        w1 = time.time()
+        time.sleep(0.2)
+        sampler.stop()
         rep = capi.bfs_serve_stats(srv)
         # per graph: latency (submission to completion) and service time (admission to completion)
         lat = [[] for _ in gs]
@@ -920,7 +927,7 @@ def run_serve(args) -> int:
                         "p50_ms": round(rep["latency_p50_ms"], 3), "p99_ms": round(rep["latency_p99_ms"], 3),
                         "mean_ms": round(rep["latency_mean_ms"], 3), "gteps": round(rep["gteps"], 3),
                         "max_concurrent": rep["max_concurrent"], "levels": rep["levels"],
-                        "per_graph": per_graph})
+                        "per_graph": per_graph, "clocks": sampler.summary(w0, w1)})
         log(f"[serve] rate {rate:.0f}: {results[-1]}")
     for h in hs:
         capi.bfs_graph_destroy(h)
