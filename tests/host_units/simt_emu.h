@@ -144,3 +144,7 @@ inline int atomicCAS(int* p, int cmp, int val) {
   return cmp;
 }
 unsigned __ldcg(const unsigned*);  // declared for the headers; not used by these tests
+template <class T>
+T __ldg(const T* p) {  // read-only load: a plain load on the host
+  return *p;
+}

@@ -8,7 +8,10 @@
   * the two block-level passes that rebuild an ordered wave level's frontier in vertex order
     (over the 64-bit root masks, over the byte marks) on the same emulator, against the
     marked set, the degree scan and the binary search of Algorithm 3 written out in the
-    test (tests/host_units/batch_order.cpp)."""
+    test (tests/host_units/batch_order.cpp);
+  * where a batched wave's claims go (record_claim: at once, event slot, dense row, overflow
+    list), on one thread and on racing emulated threads: every claimed (root, vertex) pair
+    found exactly once with its parent and level (tests/host_units/claim_records.cpp)."""
 import os
 import shutil
 import subprocess
@@ -20,7 +23,7 @@ CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include
 
 
 @pytest.mark.parametrize("unit,prelude", [("device_helpers", "cuda_shim.h"), ("warp_helpers", "simt_emu.h"),
-                                          ("batch_order", "simt_emu.h")])
+                                          ("batch_order", "simt_emu.h"), ("claim_records", "simt_emu.h")])
 def test_device_helpers_on_host(tmp_path, unit, prelude):
     cxx = shutil.which("g++")
     if not cxx or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
