@@ -1,8 +1,8 @@
 // A small SIMT emulator for CPU unit tests of the library's warp- and block-collective
 // helpers: every emulated GPU thread is an OS thread; the warp intrinsics the helpers use
 // (__ballot_sync, __any_sync, __shfl_sync, __shfl_up_sync, full-warp masks only) exchange
-// values through a per-warp slot array between two barriers, __syncthreads is a block
-// barrier, and the device atomics the headers use act on host memory. The
+// values through a per-warp slot array between two barriers, __syncwarp and __syncthreads
+// are warp and block barriers, and the device atomics the headers use act on host memory. The
 // intrinsic semantics follow the CUDA programming guide's definitions. Included ahead of the
 // library headers (g++ -include), in place of their CUDA device environment.
 #pragma once
@@ -130,6 +130,11 @@ inline int __ffs(unsigned x) { return __builtin_ffs((int)x); }
 inline int __ffsll(long long x) { return __builtin_ffsll(x); }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
 inline void __syncthreads() { simt::t_block->bar.wait(); }
+inline void __syncwarp(unsigned mask = 0xffffffffu) {
+  assert(mask == 0xffffffffu);
+  simt::t_block->warps[threadIdx.x / 32].bar.wait();
+}
+inline int min(int x, int y) { return x < y ? x : y; }  // the device integer min
 
 // Device atomics on host memory (sequentially consistent; each returns the old value).
 inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {

@@ -9,6 +9,10 @@
     (over the 64-bit root masks, over the byte marks) on the same emulator, against the
     marked set, the degree scan and the binary search of Algorithm 3 written out in the
     test (tests/host_units/batch_order.cpp);
+  * the warp and CTA appends of a wave's next frontier (batch_warp_flush, batch_flush) on the
+    emulator, several flushes on top of an earlier reservation: contiguous in-order ranges,
+    the degree scan carried on, column bases and tile descriptors
+    (tests/host_units/batch_append.cpp);
   * where a batched wave's claims go (record_claim: at once, event slot, dense row, overflow
     list), on one thread and on racing emulated threads: every claimed (root, vertex) pair
     found exactly once with its parent and level (tests/host_units/claim_records.cpp)."""
@@ -23,7 +27,8 @@ CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include
 
 
 @pytest.mark.parametrize("unit,prelude", [("device_helpers", "cuda_shim.h"), ("warp_helpers", "simt_emu.h"),
-                                          ("batch_order", "simt_emu.h"), ("claim_records", "simt_emu.h")])
+                                          ("batch_order", "simt_emu.h"), ("batch_append", "simt_emu.h"),
+                                          ("claim_records", "simt_emu.h")])
 def test_device_helpers_on_host(tmp_path, unit, prelude):
     cxx = shutil.which("g++")
     if not cxx or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
